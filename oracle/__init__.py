@@ -1,0 +1,25 @@
+"""FP64 CPU oracle for the GP marginal log-likelihood (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline legs of
+``bench.py`` may import this package.  The product path never does.
+"""
+from .gp_oracle import (  # noqa: F401
+    build,
+    cov_fill,
+    dcov_dlogrho,
+    cholesky,
+    forward,
+    backward,
+    lower_matvec,
+    lower_inverse,
+    inverse_from_chol,
+    logdet,
+    loglik,
+    loglik_grad,
+    kernel,
+    kernel_dlogrho,
+    num_threads,
+    set_threads,
+    OracleNotPD,
+    KERNELS,
+)

@@ -1,0 +1,356 @@
+/*
+ * gp_oracle.c -- plain, slow FP64 CPU oracle for the Gaussian-process
+ * marginal log-likelihood of Paciorek et al., "Parallelizing Gaussian
+ * Process Calculations in R" (arXiv:1305.4886).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may call this
+ * code: only the tests, the package's smoke check and the benchmark's
+ * CPU-baseline leg load it.  It shares no code, header, table or helper
+ * with the CUDA library; the two meet only through seeded inputs.
+ *
+ * What it computes, step by step, is the definition in Section 1 of the
+ * paper, written out with unblocked loops:
+ *
+ *   marginal model      Y | theta ~ N(mu, C),  C = C_y + C_g      (Sec. 1)
+ *   covariance entries  C_ij = s2 * k(d_ij / rho)   (i != j)
+ *                       C_ii = s2 + tau2            (nugget, diagonal C_y)
+ *   Cholesky            L L^T = C, no pivoting; a pivot <= 0 fails (Sec. 5)
+ *   forward solve       v = L^{-1} (y - mu)          ("backsolve", Sec. 1)
+ *   sum of squares      q = v^T v                    (Sec. 2.2.2)
+ *   log-determinant     logdet = 2 sum_i log L_ii    (Sec. 2.2.2)
+ *   log-density         l = -logdet/2 - q/2 - (n/2) log(2 pi)
+ *
+ * The paper writes the density only up to proportionality; the oracle keeps
+ * the Gaussian normalising constant so that l is the full log-density.
+ *
+ * The gradient is not in the paper.  It is the standard Gaussian identity
+ *   dl/dtheta_j = 1/2 alpha^T (dC/dtheta_j) alpha - 1/2 tr(C^{-1} dC/dtheta_j),
+ *   alpha = C^{-1}(y - mu),
+ * with theta = (log s2, log rho, log tau2), C^{-1} formed explicitly from the
+ * inverse of L, and every trace / quadratic form summed over all (i, j).
+ *
+ * Kernels (Matern in the Rasmussen & Williams parameterisation, the paper's
+ * GP reference; u = d / rho):
+ *   exponential  k(u) = exp(-u)
+ *   Matern 3/2   k(u) = (1 + a) exp(-a),            a = sqrt(3) u
+ *   Matern 5/2   k(u) = (1 + a + a^2/3) exp(-a),    a = sqrt(5) u
+ *
+ * Storage: every matrix here is a full n x n row-major array (A[i*n + j]).
+ * Locations are n points of 2 coordinates, interleaved (x_i1, x_i2).
+ * Sums that feed the reported scalars use Neumaier compensation.
+ * OpenMP parallelises independent rows only; each row's arithmetic is
+ * sequential and rows are combined in index order, so results do not depend
+ * on the thread count.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_OK 0
+#define ORC_NOT_PD 1
+#define ORC_INVALID 2
+
+typedef struct {
+    double s, c;
+} nsum_t; /* Neumaier running sum */
+
+static void ns_init(nsum_t *a) { a->s = 0.0; a->c = 0.0; }
+static void ns_add(nsum_t *a, double x) {
+    double t = a->s + x;
+    if (fabs(a->s) >= fabs(x)) a->c += (a->s - t) + x;
+    else a->c += (x - t) + a->s;
+    a->s = t;
+}
+static double ns_get(const nsum_t *a) { return a->s + a->c; }
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void orc_set_threads(int t) {
+#ifdef _OPENMP
+    if (t > 0) omp_set_num_threads(t);
+#else
+    (void)t;
+#endif
+}
+
+/* correlation k(u) for u = d/rho >= 0 (Sec. 1 covariance; kernels above) */
+double orc_kernel(int kind, double u) {
+    if (kind == 0) return exp(-u);
+    if (kind == 1) {
+        double a = sqrt(3.0) * u;
+        return (1.0 + a) * exp(-a);
+    }
+    if (kind == 2) {
+        double a = sqrt(5.0) * u;
+        return (1.0 + a + a * a / 3.0) * exp(-a);
+    }
+    return NAN;
+}
+
+/* -u k'(u): derivative of k(d/rho) with respect to log rho */
+double orc_kernel_dlogrho(int kind, double u) {
+    if (kind == 0) return u * exp(-u);
+    if (kind == 1) {
+        double a = sqrt(3.0) * u;
+        return a * a * exp(-a);
+    }
+    if (kind == 2) {
+        double a = sqrt(5.0) * u;
+        return a * a * (1.0 + a) / 3.0 * exp(-a);
+    }
+    return NAN;
+}
+
+static double dist2d(const double *x, int64_t i, int64_t j) {
+    double dx = x[2 * i] - x[2 * j];
+    double dy = x[2 * i + 1] - x[2 * j + 1];
+    return sqrt(dx * dx + dy * dy);
+}
+
+/* C(theta): full symmetric n x n (Sec. 1: C = C_g + C_y, C_y = tau2 I) */
+void orc_cov_fill(const double *x, int64_t n, int kind, double s2, double rho,
+                  double tau2, double *C) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t j = 0; j < n; ++j) {
+            if (i == j) C[i * n + j] = s2 + tau2;
+            else C[i * n + j] = s2 * orc_kernel(kind, dist2d(x, i, j) / rho);
+        }
+    }
+}
+
+/* dC/dlog(rho): full symmetric, zero diagonal */
+void orc_dcov_dlogrho(const double *x, int64_t n, int kind, double s2, double rho,
+                      double *D) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t j = 0; j < n; ++j) {
+            if (i == j) D[i * n + j] = 0.0;
+            else D[i * n + j] = s2 * orc_kernel_dlogrho(kind, dist2d(x, i, j) / rho);
+        }
+    }
+}
+
+/* Unblocked column Cholesky, in place; lower triangle of A becomes L, the
+ * strict upper triangle is zeroed.  No pivoting: returns j+1 for the first
+ * column j whose pivot is not > 0 (the failure mode noted in Sec. 5). */
+int64_t orc_cholesky(double *A, int64_t n) {
+    for (int64_t j = 0; j < n; ++j) {
+        double s = A[j * n + j];
+        for (int64_t k = 0; k < j; ++k) s -= A[j * n + k] * A[j * n + k];
+        if (!(s > 0.0)) return j + 1;
+        double ljj = sqrt(s);
+        A[j * n + j] = ljj;
+#pragma omp parallel for schedule(static)
+        for (int64_t i = j + 1; i < n; ++i) {
+            double t = A[i * n + j];
+            const double *li = A + i * n, *lj = A + j * n;
+            for (int64_t k = 0; k < j; ++k) t -= li[k] * lj[k];
+            A[i * n + j] = t / ljj;
+        }
+    }
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = i + 1; j < n; ++j) A[i * n + j] = 0.0;
+    return 0;
+}
+
+/* v = L^{-1} b (forward substitution) */
+void orc_forward(const double *L, int64_t n, const double *b, double *v) {
+    for (int64_t i = 0; i < n; ++i) {
+        double t = b[i];
+        for (int64_t k = 0; k < i; ++k) t -= L[i * n + k] * v[k];
+        v[i] = t / L[i * n + i];
+    }
+}
+
+/* a = L^{-T} v (back substitution, column-oriented) */
+void orc_backward(const double *L, int64_t n, const double *v, double *a) {
+    double *w = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    memcpy(w, v, sizeof(double) * (size_t)n);
+    for (int64_t i = n - 1; i >= 0; --i) {
+        a[i] = w[i] / L[i * n + i];
+        for (int64_t k = 0; k < i; ++k) w[k] -= L[i * n + k] * a[i];
+    }
+    free(w);
+}
+
+/* L * z (lower triangular times vector), used to draw y = L z */
+void orc_lower_matvec(const double *L, int64_t n, const double *z, double *y) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double t = 0.0;
+        for (int64_t k = 0; k <= i; ++k) t += L[i * n + k] * z[k];
+        y[i] = t;
+    }
+}
+
+/* logdet = 2 sum log L_ii (Sec. 2.2.2), compensated */
+double orc_logdet(const double *L, int64_t n) {
+    nsum_t a;
+    ns_init(&a);
+    for (int64_t i = 0; i < n; ++i) ns_add(&a, log(L[i * n + i]));
+    return 2.0 * ns_get(&a);
+}
+
+/* compensated inner product */
+double orc_dot(const double *a, const double *b, int64_t n) {
+    nsum_t s;
+    ns_init(&s);
+    for (int64_t i = 0; i < n; ++i) ns_add(&s, a[i] * b[i]);
+    return ns_get(&s);
+}
+
+/* X = L^{-1}, by forward substitution on each unit vector; full row-major */
+void orc_lower_inverse(const double *L, int64_t n, double *X) {
+    memset(X, 0, sizeof(double) * (size_t)n * (size_t)n);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t c = 0; c < n; ++c) {
+        /* column c of X solves L x = e_c; x_i = 0 for i < c */
+        for (int64_t i = c; i < n; ++i) {
+            double t = (i == c) ? 1.0 : 0.0;
+            for (int64_t k = c; k < i; ++k) t -= L[i * n + k] * X[k * n + c];
+            X[i * n + c] = t / L[i * n + i];
+        }
+    }
+}
+
+/* W = C^{-1} = L^{-T} L^{-1}, full symmetric */
+void orc_inverse_from_chol(const double *L, int64_t n, double *W) {
+    double *X = (double *)malloc(sizeof(double) * (size_t)n * (size_t)n);
+    double *XT = (double *)malloc(sizeof(double) * (size_t)n * (size_t)n);
+    orc_lower_inverse(L, n, X);
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t k = 0; k < n; ++k) XT[i * n + k] = X[k * n + i];
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t j = 0; j <= i; ++j) {
+            /* W_ij = sum_k X_ki X_kj, nonzero only for k >= max(i, j) = i */
+            double t = 0.0;
+            for (int64_t k = i; k < n; ++k) t += XT[i * n + k] * XT[j * n + k];
+            W[i * n + j] = t;
+            W[j * n + i] = t;
+        }
+    }
+    free(X);
+    free(XT);
+}
+
+static int params_ok(int64_t n, int kind, double s2, double rho, double tau2) {
+    if (n < 1) return 0;
+    if (kind < 0 || kind > 2) return 0;
+    if (!(s2 > 0.0) || !(rho > 0.0) || !(tau2 >= 0.0)) return 0;
+    if (!isfinite(s2) || !isfinite(rho) || !isfinite(tau2)) return 0;
+    return 1;
+}
+
+/*
+ * Log-likelihood (Sec. 1 / Sec. 2.2.2).  mu may be NULL (zero mean).
+ * out[0] = loglik, out[1] = logdet, out[2] = q.  alpha (n, may be NULL)
+ * receives C^{-1}(y - mu).  L (n*n, may be NULL) receives the factor.
+ * Returns ORC_OK, ORC_INVALID, or ORC_NOT_PD (then *info = failing col + 1).
+ */
+int orc_loglik(const double *x, const double *y, const double *mu, int64_t n,
+               int kind, double s2, double rho, double tau2, double *out,
+               double *alpha, double *Lout, int64_t *info) {
+    if (info) *info = 0;
+    if (!params_ok(n, kind, s2, rho, tau2)) return ORC_INVALID;
+    for (int64_t i = 0; i < 2 * n; ++i)
+        if (!isfinite(x[i])) return ORC_INVALID;
+    size_t nn = (size_t)n * (size_t)n;
+    double *C = (double *)malloc(sizeof(double) * nn);
+    double *r = (double *)malloc(sizeof(double) * (size_t)n);
+    double *v = (double *)malloc(sizeof(double) * (size_t)n);
+    orc_cov_fill(x, n, kind, s2, rho, tau2, C);
+    int64_t f = orc_cholesky(C, n);
+    if (f != 0) {
+        if (info) *info = f;
+        out[0] = out[1] = out[2] = NAN;
+        free(C); free(r); free(v);
+        return ORC_NOT_PD;
+    }
+    for (int64_t i = 0; i < n; ++i) r[i] = y[i] - (mu ? mu[i] : 0.0);
+    orc_forward(C, n, r, v);
+    double logdet = orc_logdet(C, n);
+    double q = orc_dot(v, v, n);
+    out[0] = -0.5 * logdet - 0.5 * q - 0.5 * (double)n * log(2.0 * M_PI);
+    out[1] = logdet;
+    out[2] = q;
+    if (alpha) orc_backward(C, n, v, alpha);
+    if (Lout) memcpy(Lout, C, sizeof(double) * nn);
+    free(C); free(r); free(v);
+    return ORC_OK;
+}
+
+/*
+ * Log-likelihood and its gradient with respect to
+ * theta = (log s2, log rho, log tau2):
+ *   dC/dlog s2  = C - tau2 I
+ *   dC/dlog rho = s2 * (-u k'(u)),  u = d/rho  (zero on the diagonal)
+ *   dC/dlog tau2 = tau2 I
+ *   g_j = 1/2 alpha^T dC_j alpha - 1/2 sum_{i,k} W_ik (dC_j)_ik,  W = C^{-1}
+ * Every sum runs over the full square with Neumaier compensation.
+ */
+int orc_loglik_grad(const double *x, const double *y, const double *mu, int64_t n,
+                    int kind, double s2, double rho, double tau2, double *out,
+                    double *alpha, double *grad, int64_t *info) {
+    size_t nn = (size_t)n * (size_t)n;
+    double *L, *W, *C, *D, *a;
+    int st;
+    if (!params_ok(n, kind, s2, rho, tau2)) return ORC_INVALID;
+    L = (double *)malloc(sizeof(double) * nn);
+    a = (double *)malloc(sizeof(double) * (size_t)n);
+    st = orc_loglik(x, y, mu, n, kind, s2, rho, tau2, out, a, L, info);
+    if (st != ORC_OK) {
+        grad[0] = grad[1] = grad[2] = NAN;
+        free(L); free(a);
+        return st;
+    }
+    W = (double *)malloc(sizeof(double) * nn);
+    C = (double *)malloc(sizeof(double) * nn);
+    D = (double *)malloc(sizeof(double) * nn);
+    orc_inverse_from_chol(L, n, W);
+    orc_cov_fill(x, n, kind, s2, rho, tau2, C);
+    orc_dcov_dlogrho(x, n, kind, s2, rho, D);
+
+    /* per-row compensated partial sums, combined in row order */
+    double *part = (double *)calloc((size_t)n * 6, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+        nsum_t q0, q1, t0, t1;
+        ns_init(&q0); ns_init(&q1); ns_init(&t0); ns_init(&t1);
+        for (int64_t k = 0; k < n; ++k) {
+            double dc0 = C[i * n + k] - (i == k ? tau2 : 0.0);
+            double dc1 = D[i * n + k];
+            ns_add(&q0, a[i] * dc0 * a[k]);
+            ns_add(&q1, a[i] * dc1 * a[k]);
+            ns_add(&t0, W[i * n + k] * dc0);
+            ns_add(&t1, W[i * n + k] * dc1);
+        }
+        part[6 * i + 0] = ns_get(&q0);
+        part[6 * i + 1] = ns_get(&q1);
+        part[6 * i + 2] = ns_get(&t0);
+        part[6 * i + 3] = ns_get(&t1);
+        part[6 * i + 4] = a[i] * a[i];      /* alpha^T alpha term */
+        part[6 * i + 5] = W[i * n + i];     /* tr W term */
+    }
+    nsum_t s[6];
+    for (int c = 0; c < 6; ++c) ns_init(&s[c]);
+    for (int64_t i = 0; i < n; ++i)
+        for (int c = 0; c < 6; ++c) ns_add(&s[c], part[6 * i + c]);
+    grad[0] = 0.5 * ns_get(&s[0]) - 0.5 * ns_get(&s[2]);
+    grad[1] = 0.5 * ns_get(&s[1]) - 0.5 * ns_get(&s[3]);
+    grad[2] = 0.5 * tau2 * ns_get(&s[4]) - 0.5 * tau2 * ns_get(&s[5]);
+    if (alpha) memcpy(alpha, a, sizeof(double) * (size_t)n);
+    free(part); free(L); free(W); free(C); free(D); free(a);
+    return ORC_OK;
+}
