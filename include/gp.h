@@ -1,0 +1,144 @@
+/*
+ * gp.h -- C ABI of libgp, a GB300 (sm_103a) library for the Gaussian-process
+ * marginal log-likelihood of Paciorek et al., "Parallelizing Gaussian Process
+ * Calculations in R" (arXiv:1305.4886).
+ *
+ * The operation (Sec. 1): for locations x_1..x_n, data y and mean mu,
+ *     C(theta) = C_g(theta) + C_y(theta)            (covariance + nugget)
+ *     L L^T    = C(theta)                           (Cholesky, no pivoting)
+ *     v        = L^{-1} (y - mu)                    (forward solve)
+ *     logdet   = 2 sum_i log L_ii,  q = v^T v        (Sec. 2.2.2)
+ *     loglik   = -logdet/2 - q/2 - (n/2) log(2 pi)
+ *
+ * Conventions shared by every entry point
+ *   - Pointers prefixed d_ are device pointers; h_ are host pointers.  The
+ *     caller owns every buffer, including workspaces; the library never
+ *     allocates device memory in these calls and keeps no hidden state
+ *     between them.
+ *   - Matrices are FP64, column-major, lower triangle referenced, leading
+ *     dimension ld >= gp_padded_order(n).  The padded order n_p rounds n up
+ *     to a multiple of GP_PAD (the block padding of Sec. 2.2); rows/columns
+ *     n..n_p-1 are owned by the library and hold the identity, so they add
+ *     log 1 = 0 to logdet and 0 to q.  Entries above the diagonal are never
+ *     read and may be overwritten inside diagonal tiles.
+ *   - Locations are n points x 2 coordinates, interleaved (x_i1, x_i2).
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call
+ *     is asynchronous on it: the host return code reports argument checks
+ *     and launch errors only.  Failures found on the device go to the
+ *     caller's int64 *d_info, which the caller reads after its own sync:
+ *        0      success
+ *        k + 1  the unpivoted Cholesky met a pivot <= 0 (or NaN) at global
+ *               column k -- the failure mode of Sec. 5
+ *        -1     a bounded device-side wait gave up (timeout)
+ *        -2     non-finite input (location, data or mean)
+ *     When *d_info != 0 the scalar outputs are NaN.
+ *   - Kernel parameters are on the natural scale: sigma2 > 0, rho > 0,
+ *     tau2 >= 0, all finite.  Gradients are with respect to
+ *     theta = (log sigma2, log rho, log tau2).
+ */
+#ifndef GP_H
+#define GP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GP_ABI_VERSION 1
+#define GP_PAD 128 /* padding granularity of n (rows/columns of one tile) */
+
+typedef enum {
+    GP_OK = 0,
+    GP_ERR_NOT_PD = 1,    /* reserved: device-side detection goes to d_info */
+    GP_ERR_INVALID = 2,   /* bad argument (sizes, parameters, NULL pointers) */
+    GP_ERR_CUDA = 3,      /* a CUDA launch or runtime call failed */
+    GP_ERR_TIMEOUT = 4,   /* reserved: device-side detection goes to d_info */
+    GP_ERR_WORKSPACE = 5  /* workspace missing or smaller than required */
+} gp_status;
+
+/* Covariance functions k(u), u = d / rho, d Euclidean distance (Sec. 1;
+ * Matern in the Rasmussen & Williams parameterisation):
+ *   EXP       exp(-u)
+ *   MATERN32  (1 + a) exp(-a),           a = sqrt(3) u
+ *   MATERN52  (1 + a + a^2/3) exp(-a),   a = sqrt(5) u                     */
+typedef enum { GP_KERNEL_EXP = 0, GP_KERNEL_MATERN32 = 1, GP_KERNEL_MATERN52 = 2 } gp_kernel;
+
+/* Arithmetic of the factorisation.
+ *   GP_FP64        every step in FP64 on the CUDA cores.
+ *   GP_MIXED_BF16  FP64 diagonal blocks, pivots, log-determinant and
+ *                  residuals; the off-diagonal panel solve and the trailing
+ *                  SYRK/GEMM updates run on the tcgen05 tensor cores on
+ *                  BF16 slices of the FP64 operands (a 3-slice split,
+ *                  FP32 accumulation), followed by iterative refinement of
+ *                  alpha against a matrix-free FP64 residual.            */
+typedef enum { GP_FP64 = 0, GP_MIXED_BF16 = 1 } gp_precision;
+
+typedef struct {
+    int32_t kernel; /* gp_kernel */
+    double sigma2;  /* marginal variance of the latent process, > 0 */
+    double rho;     /* range, > 0 */
+    double tau2;    /* nugget (diagonal of C_y), >= 0 */
+} gp_params;
+
+/* ---- queries (pure host functions) ------------------------------------ */
+
+int gp_abi_version(void);
+const char *gp_status_string(int status);
+
+/* n rounded up to a multiple of GP_PAD; 0 for n < 1. */
+int64_t gp_padded_order(int64_t n);
+
+/* Bytes of device workspace that gp_loglik (want_grad = 0) or
+ * gp_loglik_grad (want_grad = 1) needs for this n and precision; 0 for an
+ * invalid request.  The first gp_padded_order(n)^2 doubles of the workspace
+ * hold the matrix (column-major, ld = n_p): after gp_loglik they hold the
+ * Cholesky factor L, after gp_loglik_grad the lower triangle of C^{-1}.   */
+size_t gp_workspace_bytes(int64_t n, int precision, int want_grad);
+
+/* Bytes of workspace gp_chol needs for this n and precision. */
+size_t gp_chol_workspace_bytes(int64_t n, int precision);
+
+/* ---- the steps of the path ------------------------------------------- */
+
+/* Covariance fill (Sec. 1: C = C_g + C_y; Sec. 2.3.5: entries built from a
+ * covariance function at given indices).  Writes the lower tiles of the
+ * n_p x n_p matrix d_C (ld = ldc): C_ij = sigma2 k(d_ij/rho) for i != j,
+ * C_ii = sigma2 + tau2, identity in the padding.                           */
+int gp_cov_fill(const double *d_x, int64_t n, const gp_params *prm, double *d_C,
+                int64_t ldc, void *stream);
+
+/* Cholesky factorisation L L^T = C in place (Sec. 1; block algorithm of
+ * Sec. 2.1): d_C holds the n_p x n_p matrix from gp_cov_fill on entry and
+ * L on exit (lower triangle; padding stays identity).  No pivoting: a pivot
+ * <= 0 sets *d_info = column + 1 (Sec. 5).  d_ws: gp_chol_workspace_bytes. */
+int gp_chol(double *d_C, int64_t n, int64_t ldc, int precision, void *d_ws,
+            size_t ws_bytes, int64_t *d_info, void *stream);
+
+/* Triangular solve with the factor (Sec. 1 "backsolve"; the paper's
+ * forwardsolve/backsolve pair, Sec. 2.3.2):
+ *   trans = 0: d_out = L^{-1} d_b      trans = 1: d_out = L^{-T} d_b.
+ * d_b and d_out hold n values; they may alias.                            */
+int gp_backsolve(const double *d_L, int64_t n, int64_t ldc, int trans, const double *d_b,
+                 double *d_out, void *stream);
+
+/* d_out = L d_z (n values; the paper's multiplication by the Cholesky factor
+ * used for simulation, Sec. 2.3.2).  d_z and d_out must not alias.         */
+int gp_mult_chol(const double *d_L, int64_t n, int64_t ldc, const double *d_z, double *d_out,
+                 void *stream);
+
+/* Log-likelihood (Sec. 1, Sec. 2.2.2).  d_mu: n values or NULL (zero mean).
+ * d_out[0..3] = {loglik, logdet, q, refinement residual}; the last is
+ * ||r - C alpha||_2 / ||r||_2 after refinement in GP_MIXED_BF16, and 0 in
+ * GP_FP64.  d_alpha: n values or NULL; receives C^{-1}(y - mu).  d_ws:
+ * gp_workspace_bytes(n, precision, 0); on return its first n_p^2 doubles
+ * hold L.                                                                  */
+int gp_loglik(const double *d_x, const double *d_y, const double *d_mu, int64_t n,
+              const gp_params *prm, int precision, void *d_ws, size_t ws_bytes,
+              double *d_out, double *d_alpha, int64_t *d_info, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GP_H */

@@ -1,0 +1,48 @@
+// common.cuh -- shared definitions of the libgp CUDA sources (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gp.h"
+
+namespace gp {
+
+constexpr int TB = 64;        // FP64 CUDA-core tile (diagonal POTRF / TRSM / TRSV)
+constexpr int PAD = GP_PAD;   // padding granularity of n
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
+
+// The first device-side failure wins: d_info is only written while it is 0.
+__device__ __forceinline__ void set_info(int64_t *info, int64_t v) {
+    atomicCAS(reinterpret_cast<unsigned long long *>(info), 0ull,
+              static_cast<unsigned long long>(v));
+}
+
+__device__ __forceinline__ bool failed(const int64_t *info) {
+    return *reinterpret_cast<const volatile int64_t *>(info) != 0;
+}
+
+// Map a linear index over the lower-triangular tile grid to (ti, tj), ti >= tj.
+__device__ __forceinline__ void lower_tile_coords(int64_t t, int64_t &ti, int64_t &tj) {
+    int64_t i = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while ((i + 1) * (i + 2) / 2 <= t) ++i;
+    while (i * (i + 1) / 2 > t) --i;
+    ti = i;
+    tj = t - i * (i + 1) / 2;
+}
+
+}  // namespace gp
+
+#define GP_LAUNCH_CHECK()                                   \
+    do {                                                    \
+        cudaError_t e_ = cudaGetLastError();                \
+        if (e_ != cudaSuccess) return GP_ERR_CUDA;          \
+    } while (0)
+
+#define GP_TRY(expr)                                        \
+    do {                                                    \
+        int s_ = (expr);                                    \
+        if (s_ != GP_OK) return s_;                         \
+    } while (0)

@@ -1,0 +1,300 @@
+// dense_f64.cu -- FP64 CUDA-core building blocks of the tiled Cholesky
+// (Sec. 2.1: factor the diagonal block, forward-solve the blocks below it,
+// update the trailing blocks by multiply-and-subtract; repeat per block
+// column).
+//
+//   potrf_tile   Cholesky of one 64 x 64 diagonal tile in shared memory.
+//   trsm_tiles   panel solve  B <- B L_kk^{-T}  for the tiles below it.
+//   trtri_tiles  inverse of each 64 x 64 diagonal tile of a lower block.
+//   gemm_f64     C = alpha op(A) op(B) + beta C, 64 x 64 register-tiled.
+//
+// GB300 executes FP64 at a small fraction of its tensor rate, so these
+// kernels are bounded by the FP64 pipe, not by memory: a 4 x 4 register tile
+// per thread keeps shared-memory traffic far below the DFMA issue rate.
+#include "internal.h"
+
+namespace gp {
+
+// ---------------------------------------------------------------------------
+// Cholesky of the 64 x 64 tile at A (column-major, ld), right-looking in
+// shared memory.  col_base is the global column of the tile's first column
+// (for the d_info convention).  Pivots <= 0 or NaN stop the factorisation.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) potrf_tile_kernel(double *A, int64_t ld, int64_t col_base,
+                                                         int64_t *info) {
+    __shared__ double S[TB * (TB + 1)];
+    __shared__ int bad;
+    if (failed(info)) return;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < TB * TB; e += blockDim.x) {
+        int r = e & (TB - 1), c = e >> 6;
+        S[c * (TB + 1) + r] = (r >= c) ? A[r + (int64_t)c * ld] : 0.0;
+    }
+    if (tid == 0) bad = 0;
+    __syncthreads();
+    for (int j = 0; j < TB; ++j) {
+        double d = S[j * (TB + 1) + j];
+        if (!(d > 0.0)) {  // uniform: every thread read the same value
+            if (tid == 0) {
+                bad = 1;
+                set_info(info, col_base + j + 1);
+            }
+            break;
+        }
+        double ljj = sqrt(d);
+        __syncthreads();
+        if (tid >= j && tid < TB) S[j * (TB + 1) + tid] = (tid == j) ? ljj : S[j * (TB + 1) + tid] / ljj;
+        __syncthreads();
+        // rank-1 update of the trailing lower triangle, columns j+1..63
+        const int w = TB - 1 - j;
+        for (int e = tid; e < w * TB; e += blockDim.x) {
+            int c = j + 1 + e / TB;
+            int r = e & (TB - 1);
+            if (r >= c) S[c * (TB + 1) + r] -= S[j * (TB + 1) + r] * S[j * (TB + 1) + c];
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    if (bad) return;
+    for (int e = tid; e < TB * TB; e += blockDim.x) {
+        int r = e & (TB - 1), c = e >> 6;
+        if (r >= c) A[r + (int64_t)c * ld] = S[c * (TB + 1) + r];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// B <- B L^{-T} for the 64-row tiles below the diagonal tile L (the panel
+// forward-solve of Sec. 2.1).  B tile t starts at B0 + 64 t.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) trsm_tiles_kernel(const double *L, double *B0, int64_t ld,
+                                                         const int64_t *info) {
+    __shared__ double Ls[TB * (TB + 1)];
+    __shared__ double Bs[TB * (TB + 1)];
+    if (failed(info)) return;
+    const int tid = threadIdx.x;
+    double *B = B0 + (int64_t)blockIdx.x * TB;
+    for (int e = tid; e < TB * TB; e += blockDim.x) {
+        int r = e & (TB - 1), c = e >> 6;
+        Ls[c * (TB + 1) + r] = (r >= c) ? L[r + (int64_t)c * ld] : 0.0;
+        Bs[c * (TB + 1) + r] = B[r + (int64_t)c * ld];
+    }
+    __syncthreads();
+    // X L^T = B: column c of X = (B_c - sum_{l<c} X_l L_cl) / L_cc
+    for (int c = 0; c < TB; ++c) {
+        if (tid < TB) Bs[c * (TB + 1) + tid] /= Ls[c * (TB + 1) + c];
+        __syncthreads();
+        const int w = TB - 1 - c;
+        for (int e = tid; e < w * TB; e += blockDim.x) {
+            int c2 = c + 1 + e / TB;
+            int r = e & (TB - 1);
+            Bs[c2 * (TB + 1) + r] -= Bs[c * (TB + 1) + r] * Ls[c * (TB + 1) + c2];
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < TB * TB; e += blockDim.x) {
+        int r = e & (TB - 1), c = e >> 6;
+        B[r + (int64_t)c * ld] = Bs[c * (TB + 1) + r];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// X_tt = L_tt^{-1} for every 64 x 64 diagonal tile t of the lower block L
+// (ld_l); X (ld_x) receives full tiles with zeros above the diagonal.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) trtri_tiles_kernel(const double *L, int64_t ld_l, double *X,
+                                                          int64_t ld_x, const int64_t *info) {
+    __shared__ double Ls[TB * (TB + 1)];
+    __shared__ double Bs[TB * (TB + 1)];
+    if (failed(info)) return;
+    const int tid = threadIdx.x;
+    const int64_t off = (int64_t)blockIdx.x * TB;
+    const double *Lt = L + off + off * ld_l;
+    double *Xt = X + off + off * ld_x;
+    for (int e = tid; e < TB * TB; e += blockDim.x) {
+        int r = e & (TB - 1), c = e >> 6;
+        Ls[c * (TB + 1) + r] = (r >= c) ? Lt[r + (int64_t)c * ld_l] : 0.0;
+        Bs[c * (TB + 1) + r] = (r == c) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    // X L = I: column c of X (descending) = (B_c - sum_{l>c} X_l L_lc) / L_cc
+    for (int c = TB - 1; c >= 0; --c) {
+        if (tid < TB) Bs[c * (TB + 1) + tid] /= Ls[c * (TB + 1) + c];
+        __syncthreads();
+        for (int e = tid; e < c * TB; e += blockDim.x) {
+            int c2 = e / TB;
+            int r = e & (TB - 1);
+            Bs[c2 * (TB + 1) + r] -= Bs[c * (TB + 1) + r] * Ls[c2 * (TB + 1) + c];
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < TB * TB; e += blockDim.x) {
+        int r = e & (TB - 1), c = e >> 6;
+        Xt[r + (int64_t)c * ld_x] = (r >= c) ? Bs[c * (TB + 1) + r] : 0.0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// C (M x N) = alpha op(A) op(B) + beta C, column-major.
+//   opA = 0: op(A)(r,k) = A[r + k lda]    opA = 1: A[k + r lda]
+//   opB = 0: op(B)(k,c) = B[k + c ldb]    opB = 1: B[c + k ldb]
+// lower != 0: M == N and only 64 x 64 tiles with tile row >= tile column are
+// computed (grid is the triangular tile count).
+// ---------------------------------------------------------------------------
+constexpr int GBK = 16;
+
+__global__ void __launch_bounds__(256) gemm_f64_kernel(int64_t M, int64_t N, int64_t K, double alpha,
+                                                       const double *__restrict__ A, int64_t lda,
+                                                       int opA, const double *__restrict__ B,
+                                                       int64_t ldb, int opB, double beta,
+                                                       double *C, int64_t ldc, int lower,
+                                                       const int64_t *info) {
+    __shared__ double As[GBK][TB + 1];
+    __shared__ double Bs[GBK][TB + 1];
+    if (info && failed(info)) return;
+    int64_t bi, bj;
+    if (lower) {
+        lower_tile_coords(blockIdx.x, bi, bj);
+    } else {
+        bi = blockIdx.x;
+        bj = blockIdx.y;
+    }
+    const int64_t r0 = bi * TB, c0 = bj * TB;
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+
+    for (int64_t k0 = 0; k0 < K; k0 += GBK) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int idx = tid + 256 * q;
+            int r, k;
+            double v = 0.0;
+            if (opA == 0) {
+                r = idx & 63;
+                k = idx >> 6;
+                int64_t gr = r0 + r, gk = k0 + k;
+                if (gr < M && gk < K) v = A[gr + gk * lda];
+            } else {
+                k = idx & 15;
+                r = idx >> 4;
+                int64_t gr = r0 + r, gk = k0 + k;
+                if (gr < M && gk < K) v = A[gk + gr * lda];
+            }
+            As[k][r] = v;
+            double w = 0.0;
+            int c, kb;
+            if (opB == 0) {
+                kb = idx & 15;
+                c = idx >> 4;
+                int64_t gc = c0 + c, gk = k0 + kb;
+                if (gc < N && gk < K) w = B[gk + gc * ldb];
+            } else {
+                c = idx & 63;
+                kb = idx >> 6;
+                int64_t gc = c0 + c, gk = k0 + kb;
+                if (gc < N && gk < K) w = B[gc + gk * ldb];
+            }
+            Bs[kb][c] = w;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < GBK; ++k) {
+            double av[4], bv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) av[a] = As[k][tx + 16 * a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) bv[b] = Bs[k][ty + 16 * b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        int64_t gc = c0 + ty + 16 * b;
+        if (gc >= N) continue;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            int64_t gr = r0 + tx + 16 * a;
+            if (gr >= M) continue;
+            double *p = C + gr + gc * ldc;
+            double v = alpha * acc[a][b];
+            if (beta != 0.0) v = fma(beta, *p, v);
+            *p = v;
+        }
+    }
+}
+
+int gemm_f64(int64_t M, int64_t N, int64_t K, double alpha, const double *A, int64_t lda, int opA,
+             const double *B, int64_t ldb, int opB, double beta, double *C, int64_t ldc, int lower,
+             const int64_t *info, cudaStream_t s) {
+    if (M <= 0 || N <= 0) return GP_OK;
+    if (lower) {
+        if (M != N) return GP_ERR_INVALID;
+        int64_t T = ceil_div(M, TB);
+        gemm_f64_kernel<<<(unsigned)(T * (T + 1) / 2), 256, 0, s>>>(M, N, K, alpha, A, lda, opA, B,
+                                                                    ldb, opB, beta, C, ldc, 1, info);
+    } else {
+        dim3 g((unsigned)ceil_div(M, TB), (unsigned)ceil_div(N, TB));
+        gemm_f64_kernel<<<g, 256, 0, s>>>(M, N, K, alpha, A, lda, opA, B, ldb, opB, beta, C, ldc, 0,
+                                          info);
+    }
+    GP_LAUNCH_CHECK();
+    return GP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Right-looking tiled Cholesky in FP64 of the m x m block at A (m a multiple
+// of 64): per tile column k, POTRF of the diagonal tile, TRSM of the tiles
+// below, SYRK/GEMM of the trailing lower triangle (Sec. 2.1).
+// ---------------------------------------------------------------------------
+int chol_fp64_tiled(double *A, int64_t ld, int64_t m, int64_t col_base, int64_t *info,
+                    cudaStream_t s) {
+    const int64_t T = m / TB;
+    for (int64_t k = 0; k < T; ++k) {
+        const int64_t k0 = k * TB;
+        double *Akk = A + k0 + k0 * ld;
+        potrf_tile_kernel<<<1, 256, 0, s>>>(Akk, ld, col_base + k0, info);
+        GP_LAUNCH_CHECK();
+        const int64_t rest = m - k0 - TB;
+        if (rest <= 0) continue;
+        double *P = Akk + TB;  // rows below the diagonal tile
+        trsm_tiles_kernel<<<(unsigned)(rest / TB), 256, 0, s>>>(Akk, P, ld, info);
+        GP_LAUNCH_CHECK();
+        double *C = P + TB * ld;  // trailing block
+        GP_TRY(gemm_f64(rest, rest, TB, -1.0, P, ld, 0, P, ld, 1, 1.0, C, ld, 1, info, s));
+    }
+    return GP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// X = L^{-1} for the lower m x m block L (m a multiple of 64), FP64, written
+// to X (ld_x; full block, zeros above the diagonal).  Block forward
+// substitution over 64-row tiles: X_ii = L_ii^{-1};
+// X_{i,0:i} = -X_ii (L_{i,0:i} X_{0:i,0:i}).  tmp: 64 x m doubles.
+// ---------------------------------------------------------------------------
+int trtri_fp64_blocked(const double *L, int64_t ld_l, int64_t m, double *X, int64_t ld_x,
+                       double *tmp, const int64_t *info, cudaStream_t s) {
+    const int64_t T = m / TB;
+    if (cudaMemset2DAsync(X, ld_x * sizeof(double), 0, m * sizeof(double), m, s) != cudaSuccess)
+        return GP_ERR_CUDA;
+    trtri_tiles_kernel<<<(unsigned)T, 256, 0, s>>>(L, ld_l, X, ld_x, info);
+    GP_LAUNCH_CHECK();
+    for (int64_t i = 1; i < T; ++i) {
+        const int64_t i0 = i * TB;
+        // tmp (64 x i0) = L[i0:i0+64, 0:i0] * X[0:i0, 0:i0]
+        GP_TRY(gemm_f64(TB, i0, i0, 1.0, L + i0, ld_l, 0, X, ld_x, 0, 0.0, tmp, TB, 0, info, s));
+        // X[i0:i0+64, 0:i0] = -X_ii * tmp
+        GP_TRY(gemm_f64(TB, i0, TB, -1.0, X + i0 + i0 * ld_x, ld_x, 0, tmp, TB, 0, 0.0, X + i0,
+                        ld_x, 0, info, s));
+    }
+    return GP_OK;
+}
+
+}  // namespace gp

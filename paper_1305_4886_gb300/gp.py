@@ -1,0 +1,226 @@
+"""Thin ctypes binding of libgp (include/gp.h), same names as the C ABI.
+
+The binding only marshals arguments: torch tensors become device pointers,
+the current torch stream becomes the cudaStream_t, and every step of the
+computation runs in libgp's CUDA kernels.  There is no CPU fallback: if
+libgp.so is missing or CUDA is unavailable, calls raise.
+"""
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgp.so")
+
+GP_OK, GP_ERR_NOT_PD, GP_ERR_INVALID, GP_ERR_CUDA, GP_ERR_TIMEOUT, GP_ERR_WORKSPACE = range(6)
+KERNELS = {"exp": 0, "matern32": 1, "matern52": 2}
+PRECISIONS = {"fp64": 0, "mixed_bf16": 1}
+
+# Exported symbols, in the order include/gp.h declares them.
+SYMBOLS = [
+    "gp_abi_version",
+    "gp_status_string",
+    "gp_padded_order",
+    "gp_workspace_bytes",
+    "gp_chol_workspace_bytes",
+    "gp_cov_fill",
+    "gp_chol",
+    "gp_backsolve",
+    "gp_mult_chol",
+    "gp_loglik",
+]
+
+
+class GpParams(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int32), ("sigma2", ctypes.c_double),
+                ("rho", ctypes.c_double), ("tau2", ctypes.c_double)]
+
+
+class GpError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = lib().gp_status_string(status).decode() if status >= 0 else "?"
+        super().__init__(f"{where}: status {status} ({msg})")
+
+
+class GpDeviceError(RuntimeError):
+    """A device-side failure reported through d_info."""
+
+    def __init__(self, info):
+        self.info = int(info)
+        if self.info > 0:
+            msg = f"covariance not positive definite at column {self.info - 1}"
+        elif self.info == -1:
+            msg = "bounded device wait timed out"
+        elif self.info == -2:
+            msg = "non-finite input"
+        else:
+            msg = f"device failure {self.info}"
+        super().__init__(msg)
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load libgp.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libgp.so not built ({LIB_PATH}); run "
+                                   "`python -m paper_1305_4886_gb300.build`")
+            L = ctypes.CDLL(LIB_PATH)
+            p, i64, ci, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_size_t
+            PP = ctypes.POINTER(GpParams)
+            L.gp_abi_version.restype = ci
+            L.gp_status_string.argtypes = [ci]
+            L.gp_status_string.restype = ctypes.c_char_p
+            L.gp_padded_order.argtypes = [i64]
+            L.gp_padded_order.restype = i64
+            L.gp_workspace_bytes.argtypes = [i64, ci, ci]
+            L.gp_workspace_bytes.restype = sz
+            L.gp_chol_workspace_bytes.argtypes = [i64, ci]
+            L.gp_chol_workspace_bytes.restype = sz
+            L.gp_cov_fill.argtypes = [p, i64, PP, p, i64, p]
+            L.gp_chol.argtypes = [p, i64, i64, ci, p, sz, p, p]
+            L.gp_backsolve.argtypes = [p, i64, i64, ci, p, p, p]
+            L.gp_mult_chol.argtypes = [p, i64, i64, p, p, p]
+            L.gp_loglik.argtypes = [p, p, p, i64, PP, ci, p, sz, p, p, p, p]
+            for name in ["gp_cov_fill", "gp_chol", "gp_backsolve", "gp_mult_chol", "gp_loglik"]:
+                getattr(L, name).restype = ci
+            _lib = L
+    return _lib
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("libgp takes device tensors")
+    if not t.is_contiguous():
+        raise ValueError("libgp takes contiguous tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _f64(t):
+    if t is not None and t.dtype != torch.float64:
+        raise ValueError("libgp takes float64 tensors")
+    return _ptr(t)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def params(kernel, sigma2, rho, tau2):
+    k = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+    return GpParams(k, float(sigma2), float(rho), float(tau2))
+
+
+def _prec(p):
+    return PRECISIONS[p] if isinstance(p, str) else int(p)
+
+
+def _check(st, where):
+    if st != GP_OK:
+        raise GpError(st, where)
+
+
+# ---------------------------------------------------------------------------
+# the C ABI, one function per entry point
+# ---------------------------------------------------------------------------
+def gp_abi_version():
+    return lib().gp_abi_version()
+
+
+def gp_padded_order(n):
+    return lib().gp_padded_order(int(n))
+
+
+def gp_workspace_bytes(n, precision="fp64", want_grad=False):
+    return lib().gp_workspace_bytes(int(n), _prec(precision), int(bool(want_grad)))
+
+
+def gp_chol_workspace_bytes(n, precision="fp64"):
+    return lib().gp_chol_workspace_bytes(int(n), _prec(precision))
+
+
+def gp_cov_fill(x, prm, C, ldc=None, stream=None):
+    n = x.shape[0]
+    ldc = ldc if ldc is not None else C.shape[-1]
+    _check(lib().gp_cov_fill(_f64(x), n, ctypes.byref(prm), _f64(C), int(ldc), _stream(stream)),
+           "gp_cov_fill")
+
+
+def gp_chol(C, n, ldc, precision, ws, info, stream=None):
+    wsb = 0 if ws is None else ws.numel() * ws.element_size()
+    _check(lib().gp_chol(_f64(C), int(n), int(ldc), _prec(precision), _ptr(ws), wsb, _ptr(info),
+                         _stream(stream)), "gp_chol")
+
+
+def gp_backsolve(L, n, ldc, trans, b, out, stream=None):
+    _check(lib().gp_backsolve(_f64(L), int(n), int(ldc), int(trans), _f64(b), _f64(out),
+                              _stream(stream)), "gp_backsolve")
+
+
+def gp_mult_chol(L, n, ldc, z, out, stream=None):
+    _check(lib().gp_mult_chol(_f64(L), int(n), int(ldc), _f64(z), _f64(out), _stream(stream)),
+           "gp_mult_chol")
+
+
+def gp_loglik(x, y, mu, n, prm, precision, ws, out, alpha, info, stream=None):
+    wsb = ws.numel() * ws.element_size()
+    _check(lib().gp_loglik(_f64(x), _f64(y), _f64(mu), int(n), ctypes.byref(prm), _prec(precision),
+                           _ptr(ws), wsb, _f64(out), _f64(alpha), _ptr(info), _stream(stream)),
+           "gp_loglik")
+
+
+# ---------------------------------------------------------------------------
+# convenience wrappers that allocate with torch (device memory only)
+# ---------------------------------------------------------------------------
+def workspace(n, precision="fp64", want_grad=False, device="cuda"):
+    nbytes = gp_workspace_bytes(n, precision, want_grad)
+    if nbytes == 0:
+        raise GpError(GP_ERR_INVALID, "gp_workspace_bytes")
+    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+def factor_view(ws, n):
+    """The n_p x n_p matrix region at the start of a loglik workspace, as a
+    column-major view: element (i, j) is view[j, i]."""
+    np_ = gp_padded_order(n)
+    return ws[: np_ * np_ * 8].view(torch.float64).view(np_, np_)
+
+
+def loglik(x, y, kernel, sigma2, rho, tau2, mu=None, precision="fp64", ws=None,
+           want_alpha=True, check=True):
+    """Evaluate the log-likelihood on the device.  Returns a dict of device
+    tensors {out: [loglik, logdet, q, resid], alpha, info} (synchronises and
+    raises on a device failure when check=True)."""
+    n = x.shape[0]
+    dev = x.device
+    if ws is None:
+        ws = workspace(n, precision, False, dev)
+    out = torch.empty(4, dtype=torch.float64, device=dev)
+    alpha = torch.empty(n, dtype=torch.float64, device=dev) if want_alpha else None
+    info = torch.zeros(1, dtype=torch.int64, device=dev)
+    mu_t = None
+    if mu is not None:
+        mu_t = mu if torch.is_tensor(mu) else torch.full((n,), float(mu), dtype=torch.float64,
+                                                         device=dev)
+    gp_loglik(x, y, mu_t, n, params(kernel, sigma2, rho, tau2), precision, ws, out, alpha, info)
+    if check:
+        iv = int(info.item())
+        if iv != 0:
+            raise GpDeviceError(iv)
+    return dict(out=out, alpha=alpha, info=info, ws=ws)

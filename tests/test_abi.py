@@ -1,0 +1,82 @@
+"""The C-ABI library: it builds, loads without a GPU, exports every symbol
+include/gp.h declares, and its host-side queries and argument checks behave
+as documented.  No compute call is made here (no GPU in this suite)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER_DIR = os.path.join(ROOT, "include")
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(HEADER_DIR):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(HEADER_DIR, fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for m in re.finditer(r"\b(gp_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def libgp():
+    from paper_1305_4886_gb300 import build, gp
+    build.build()
+    return gp
+
+
+def test_header_declares_the_path(libgp):
+    names = declared_symbols()
+    for must in ["gp_cov_fill", "gp_chol", "gp_backsolve", "gp_loglik"]:
+        assert must in names
+
+
+def test_exports_every_declared_symbol(libgp):
+    L = ctypes.CDLL(libgp.LIB_PATH)
+    missing = [s for s in sorted(declared_symbols()) if not hasattr(L, s)]
+    assert not missing, missing
+    assert sorted(declared_symbols()) == sorted(libgp.SYMBOLS)
+
+
+def test_host_queries(libgp):
+    L = libgp.lib()
+    assert L.gp_abi_version() == 1
+    assert libgp.gp_padded_order(1) == 128
+    assert libgp.gp_padded_order(128) == 128
+    assert libgp.gp_padded_order(129) == 256
+    assert libgp.gp_padded_order(67275) == 67328
+    assert libgp.gp_padded_order(0) == 0
+    for p in ["fp64", "mixed_bf16"]:
+        b = libgp.gp_workspace_bytes(1024, p)
+        assert b >= 1024 * 1024 * 8
+        assert libgp.gp_workspace_bytes(0, p) == 0
+    assert libgp.gp_workspace_bytes(100, 7) == 0
+    for s in range(6):
+        assert isinstance(L.gp_status_string(s), bytes)
+
+
+def test_invalid_arguments_rejected_before_any_device_work(libgp):
+    L = libgp.lib()
+    P = libgp.params
+    dummy = ctypes.c_void_p(16)
+    bad = [P("exp", 0.0, 0.1, 0.1), P("exp", 1.0, -1.0, 0.1), P("exp", 1.0, 0.1, -0.1),
+           P("exp", float("nan"), 0.1, 0.1), P(7, 1.0, 0.1, 0.1)]
+    for prm in bad:
+        st = L.gp_loglik(dummy, dummy, None, 10, ctypes.byref(prm), 0, dummy, 1 << 30, dummy,
+                         None, dummy, None)
+        assert st == libgp.GP_ERR_INVALID
+    good = P("exp", 1.0, 0.1, 0.1)
+    assert L.gp_loglik(dummy, dummy, None, 0, ctypes.byref(good), 0, dummy, 1 << 30, dummy,
+                       None, dummy, None) == libgp.GP_ERR_INVALID
+    # workspace too small
+    assert L.gp_loglik(dummy, dummy, None, 1000, ctypes.byref(good), 0, dummy, 100, dummy,
+                       None, dummy, None) == libgp.GP_ERR_WORKSPACE
+    # leading dimension shorter than the padded order
+    assert L.gp_cov_fill(dummy, 200, ctypes.byref(good), dummy, 200, None) == libgp.GP_ERR_INVALID
+    assert L.gp_backsolve(dummy, 10, 128, 2, dummy, dummy, None) == libgp.GP_ERR_INVALID
