@@ -138,6 +138,30 @@ int gp_loglik(const double *d_x, const double *d_y, const double *d_mu, int64_t 
               const gp_params *prm, int precision, void *d_ws, size_t ws_bytes,
               double *d_out, double *d_alpha, int64_t *d_info, void *stream);
 
+/* Log-likelihood and its gradient (the gradient is not in the paper, whose
+ * optimiser uses none).  Same arguments as gp_loglik plus d_grad[3] =
+ * d loglik / d(log sigma2, log rho, log tau2), computed as
+ *   sum_{i,k} Cbar_ik (dC/dtheta_j)_ik,  Cbar = (alpha alpha^T - C^{-1}) / 2,
+ * with C^{-1} formed in place from the factor (blocked TRTRI + LAUUM) and
+ * dC/dtheta recomputed tile by tile from the locations.  In GP_MIXED_BF16
+ * the inverse's contractions use the tensor cores like the factorisation.
+ * d_ws: gp_workspace_bytes(n, precision, 1); on return its first n_p^2
+ * doubles hold the lower triangle of C^{-1}.                               */
+int gp_loglik_grad(const double *d_x, const double *d_y, const double *d_mu, int64_t n,
+                   const gp_params *prm, int precision, void *d_ws, size_t ws_bytes,
+                   double *d_out, double *d_alpha, double *d_grad, int64_t *d_info, void *stream);
+
+/* One trailing update of the block Cholesky (Sec. 2.1, the matrix
+ * multiplication and subtraction that carries most of the work), on its
+ * own:  C -= P P^T on the lower triangle of the m x m block d_C (ldc),
+ * with P the m x k block d_P (column-major, ldp).  GP_MIXED_BF16 runs it on
+ * the tcgen05 tensor cores over BF16 slices (FP32 accumulation); GP_FP64 on
+ * the CUDA cores.  d_ws: gp_syrk_workspace_bytes (0 for GP_FP64).  d_info
+ * (nullable) receives -1 if a bounded device wait gave up.                */
+size_t gp_syrk_workspace_bytes(int64_t m, int64_t k, int precision);
+int gp_syrk_lower(double *d_C, int64_t ldc, const double *d_P, int64_t ldp, int64_t m, int64_t k,
+                  int precision, void *d_ws, size_t ws_bytes, int64_t *d_info, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,44 +33,81 @@ static bool precision_ok(int p) { return p == GP_FP64 || p == GP_MIXED_BF16; }
 
 int64_t padded(int64_t n) { return n < 1 ? 0 : round_up(n, PAD); }
 
-// Workspace of the factorisation (beyond the matrix itself).
-struct CholWs {
-    size_t bytes = 0;
-};
+constexpr int MIXED_SLICES = 3;      // BF16 slices per FP64 operand (6 slice products)
+constexpr int REFINE_EVALS = 4;      // residual evaluations of the mixed refinement
+constexpr double REFINE_TOL = 1e-11; // ||r - C alpha|| / ||r|| target
 
-static size_t chol_ws_layout(int64_t np, int precision, Carve &c) {
-    (void)np;
-    (void)precision;
-    (void)c;
-    return c.off;
+// Workspace of the factorisation (beyond the matrix itself).
+static size_t chol_ws_bytes(int64_t np, int precision) {
+    if (precision == GP_FP64) return 0;
+    return chol_mixed_ws_bytes(np, MIXED_SLICES);
 }
 
 struct LoglikWs {
-    double *A = nullptr;
-    double *r = nullptr;
+    double *A = nullptr;      // n_p x n_p matrix (C, then L)
+    double *r = nullptr;      // y - mu (n_p)
+    double *v = nullptr;      // forward solve / alpha (n_p)
+    double *acc = nullptr;    // C alpha (n_p)
+    double *s = nullptr;      // refinement residual / correction (n_p)
+    double *stats = nullptr;  // [0] refinement residual ratio
+    int *conv = nullptr;      // refinement converged flag
     void *chol = nullptr;
     size_t bytes = 0;
 };
 
 static LoglikWs loglik_ws_layout(void *base, int64_t n, int precision, int want_grad) {
-    (void)want_grad;
     LoglikWs w;
     const int64_t np = padded(n);
     Carve c(base);
     w.A = c.take<double>((size_t)np * (size_t)np);
     w.r = c.take<double>((size_t)np);
-    Carve cc(nullptr);
-    size_t chol_bytes = chol_ws_layout(np, precision, cc);
-    w.chol = c.take<char>(chol_bytes);
-    w.bytes = c.off;
+    w.v = c.take<double>((size_t)np);
+    w.acc = c.take<double>((size_t)np);
+    w.s = c.take<double>((size_t)np);
+    w.stats = c.take<double>(4);
+    w.conv = c.take<int>(4);
+    size_t cb = chol_ws_bytes(np, precision);
+    if (want_grad) {  // the inverse and contraction reuse the factorisation's scratch
+        size_t gb = grad_ws_bytes(np, precision, MIXED_SLICES);
+        cb = cb > gb ? cb : gb;
+    }
+    w.chol = c.take<char>(cb);
+    w.bytes = (c.off + 255) & ~size_t(255);
     return w;
 }
 
 static int run_chol(double *A, int64_t np, int64_t ld, int precision, void *ws, int64_t *info,
                     cudaStream_t s) {
-    (void)ws;
     if (precision == GP_FP64) return chol_fp64_tiled(A, ld, np, 0, info, s);
+    if (precision == GP_MIXED_BF16) return chol_mixed(A, ld, np, MIXED_SLICES, ws, info, s);
     return GP_ERR_INVALID;
+}
+
+// fill -> Cholesky -> solves -> reductions; leaves alpha in w.v.
+static int loglik_core(const double *d_x, const double *d_y, const double *d_mu, int64_t n,
+                       const KernParams &kp, int precision, const LoglikWs &w, double *d_out,
+                       int64_t *d_info, cudaStream_t s) {
+    const int64_t np = padded(n);
+    if (cudaMemsetAsync(d_info, 0, sizeof(int64_t), s) != cudaSuccess) return GP_ERR_CUDA;
+    GP_TRY(launch_cov_fill(d_x, n, np, kp, w.A, np, d_info, s));
+    GP_TRY(run_chol(w.A, np, np, precision, w.chol, d_info, s));
+    GP_TRY(launch_residual(d_y, d_mu, n, np, w.r, d_info, s));
+    if (cudaMemcpyAsync(w.v, w.r, sizeof(double) * np, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return GP_ERR_CUDA;
+    GP_TRY(trsv_blocked(w.A, np, n, 0, w.v, d_info, s));
+    if (precision == GP_FP64) {
+        // q = v^T v with v = L^{-1} r (Sec. 2.2.2); then alpha = L^{-T} v
+        GP_TRY(launch_loglik_reduce(w.A, np, n, w.v, w.v, nullptr, d_out, d_info, s));
+        GP_TRY(trsv_blocked(w.A, np, n, 1, w.v, d_info, s));
+        return GP_OK;
+    }
+    // mixed: alpha from the low-precision factor, refined against the FP64
+    // matrix-free residual; q = r^T alpha with the refined alpha
+    GP_TRY(trsv_blocked(w.A, np, n, 1, w.v, d_info, s));
+    GP_TRY(refine_alpha(d_x, n, np, kp, w.A, np, w.r, w.v, w.acc, w.s, w.stats, w.conv,
+                        REFINE_EVALS, REFINE_TOL, d_info, s));
+    GP_TRY(launch_loglik_reduce(w.A, np, n, w.r, w.v, w.stats, d_out, d_info, s));
+    return GP_OK;
 }
 
 }  // namespace gp
@@ -97,8 +134,7 @@ int64_t gp_padded_order(int64_t n) { return padded(n); }
 
 size_t gp_chol_workspace_bytes(int64_t n, int precision) {
     if (n < 1 || !precision_ok(precision)) return 0;
-    Carve c(nullptr);
-    return chol_ws_layout(padded(n), precision, c);
+    return chol_ws_bytes(padded(n), precision);
 }
 
 size_t gp_workspace_bytes(int64_t n, int precision, int want_grad) {
@@ -149,21 +185,49 @@ int gp_loglik(const double *d_x, const double *d_y, const double *d_mu, int64_t 
     LoglikWs w = loglik_ws_layout(d_ws, n, precision, 0);
     if (!d_ws || ws_bytes < w.bytes) return GP_ERR_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
+    KernParams kp = make_kern(*prm);
+    GP_TRY(loglik_core(d_x, d_y, d_mu, n, kp, precision, w, d_out, d_info, s));
+    if (d_alpha &&
+        cudaMemcpyAsync(d_alpha, w.v, sizeof(double) * n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return GP_ERR_CUDA;
+    return GP_OK;
+}
+
+int gp_loglik_grad(const double *d_x, const double *d_y, const double *d_mu, int64_t n,
+                   const gp_params *prm, int precision, void *d_ws, size_t ws_bytes, double *d_out,
+                   double *d_alpha, double *d_grad, int64_t *d_info, void *stream) {
+    if (n < 1 || !d_x || !d_y || !d_out || !d_grad || !d_info || !params_ok(prm) ||
+        !precision_ok(precision))
+        return GP_ERR_INVALID;
+    LoglikWs w = loglik_ws_layout(d_ws, n, precision, 1);
+    if (!d_ws || ws_bytes < w.bytes) return GP_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
     const int64_t np = padded(n);
     KernParams kp = make_kern(*prm);
-    if (cudaMemsetAsync(d_info, 0, sizeof(int64_t), s) != cudaSuccess) return GP_ERR_CUDA;
-    GP_TRY(launch_cov_fill(d_x, n, np, kp, w.A, np, d_info, s));
-    GP_TRY(run_chol(w.A, np, np, precision, w.chol, d_info, s));
-    GP_TRY(launch_residual(d_y, d_mu, n, np, w.r, d_info, s));
-    GP_TRY(trsv_blocked(w.A, np, n, 0, w.r, d_info, s));
-    GP_TRY(launch_loglik_reduce(w.A, np, n, w.r, d_out, d_info, s));
-    if (d_alpha) {
-        if (cudaMemcpyAsync(d_alpha, w.r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s) !=
-            cudaSuccess)
-            return GP_ERR_CUDA;
-        GP_TRY(trsv_blocked(w.A, np, n, 1, d_alpha, d_info, s));
-    }
+    GP_TRY(loglik_core(d_x, d_y, d_mu, n, kp, precision, w, d_out, d_info, s));
+    GP_TRY(chol_inverse(w.A, np, np, precision, MIXED_SLICES, w.chol, d_info, s));
+    GP_TRY(grad_contract(d_x, n, np, kp, w.A, np, w.v, w.chol, precision, MIXED_SLICES, d_grad,
+                         d_info, s));
+    if (d_alpha &&
+        cudaMemcpyAsync(d_alpha, w.v, sizeof(double) * n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return GP_ERR_CUDA;
     return GP_OK;
+}
+
+size_t gp_syrk_workspace_bytes(int64_t m, int64_t k, int precision) {
+    if (m < 1 || k < 1 || !precision_ok(precision)) return 0;
+    return syrk_ws_bytes(m, k, precision, MIXED_SLICES);
+}
+
+int gp_syrk_lower(double *d_C, int64_t ldc, const double *d_P, int64_t ldp, int64_t m, int64_t k,
+                  int precision, void *d_ws, size_t ws_bytes, int64_t *d_info, void *stream) {
+    if (m < 1 || k < 1 || !d_C || !d_P || ldc < m || ldp < m || !precision_ok(precision))
+        return GP_ERR_INVALID;
+    size_t need = syrk_ws_bytes(m, k, precision, MIXED_SLICES);
+    if (need > 0 && (!d_ws || ws_bytes < need)) return GP_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (d_info && cudaMemsetAsync(d_info, 0, sizeof(int64_t), s) != cudaSuccess) return GP_ERR_CUDA;
+    return syrk_lower(d_C, ldc, d_P, ldp, m, k, precision, MIXED_SLICES, d_ws, d_info, s);
 }
 
 }  // extern "C"

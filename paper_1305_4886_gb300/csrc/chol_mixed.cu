@@ -1,17 +1,22 @@
-// chol_mixed.cu -- mixed-precision blocked Cholesky (Sec. 2.1 block
-// algorithm, two levels of blocking as in Sec. 2.2).
+// chol_mixed.cu -- mixed-precision blocked Cholesky (the block algorithm of
+// Sec. 2.1 with the two levels of blocking of Sec. 2.2).
 //
-// Outer blocks of NB = 512 columns.  Per outer block column k:
-//   1. FP64 tiled Cholesky of the NB x NB diagonal block (64-column tiles,
-//      diagonal POTRF in shared memory)                       -- FP64
-//   2. W = L_kk^{-1} by blocked FP64 triangular inversion       -- FP64
-//   3. panel solve L_ik = A_ik W^T as one tensor-core contraction over
-//      BF16 slices of A_ik and W (the forward-solves of Sec. 2.1)
-//   4. trailing update A_ij -= L_ik L_jk^T for the lower triangle, on the
-//      tensor cores over BF16 slices of the panel ("most of the total work
-//      is in the matrix multiplications", Sec. 2.1).
-// The diagonal pivots, hence the log-determinant, come from FP64
-// factorisations of blocks that carry FP32-accurate updates.
+// Outer blocks of NB = 512 columns.  The matrix stays FP64 (the fill's C);
+// trailing updates accumulate in a separate FP32 array D that is folded into
+// the FP64 matrix one block column at a time, just before that column is
+// factored, so the FP64 pipe touches each entry once instead of once per
+// outer step.  Per outer block column k:
+//   1. A[k:, k] += D[k:, k]   (FP64 += FP32, the block column only)
+//   2. FP64 tiled Cholesky of the NB x NB diagonal block      -- FP64
+//   3. W = L_kk^{-1}, blocked FP64 triangular inversion        -- FP64
+//   4. panel solve L_ik = A_ik W^T: one tensor-core contraction over row-
+//      scaled BF16 slices of A_ik and W (the forward-solves of Sec. 2.1),
+//      written to the FP64 matrix
+//   5. trailing update D_ij -= L_ik L_jk^T on the lower triangle, tensor
+//      cores, FP32 accumulation into D ("most of the total work is in the
+//      matrix multiplications", Sec. 2.1).
+// The pivots and hence the log-determinant come from FP64 factorisations of
+// blocks that carry FP32-accurate updates.
 #include "internal.h"
 #include "tc_gemm.h"
 
@@ -24,6 +29,7 @@ struct MixedWs {
     double *tmp = nullptr;          // 64 x NB
     __nv_bfloat16 *SA = nullptr;    // S x np x NB  panel slices
     __nv_bfloat16 *SB = nullptr;    // S x NB x NB  inverse slices
+    float *D = nullptr;             // np x np pending trailing updates
     size_t bytes = 0;
 };
 
@@ -43,37 +49,59 @@ static MixedWs mixed_layout(void *base, int64_t np, int S) {
     w.tmp = reinterpret_cast<double *>(take(sizeof(double) * TB * NB));
     w.SA = reinterpret_cast<__nv_bfloat16 *>(take(2ull * S * (size_t)np * NB));
     w.SB = reinterpret_cast<__nv_bfloat16 *>(take(2ull * S * NB * NB));
+    w.D = reinterpret_cast<float *>(take(sizeof(float) * (size_t)np * (size_t)np));
     w.bytes = align256(off);
     return w;
 }
 
 size_t chol_mixed_ws_bytes(int64_t np, int S) { return mixed_layout(nullptr, np, S).bytes; }
 
+// A[r, c] += D[r, c] for the lower part of a block column (rows >= c).
+__global__ void fold_delta_kernel(double *A, int64_t ld, const float *D, int64_t ldd, int64_t rows,
+                                  int64_t cols, const int64_t *info) {
+    if (failed(info)) return;
+    const int64_t c = blockIdx.y;
+    for (int64_t r = c + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows;
+         r += (int64_t)gridDim.x * blockDim.x)
+        A[r + c * ld] += static_cast<double>(D[r + c * ldd]);
+}
+
 int chol_mixed(double *A, int64_t ld, int64_t np, int S, void *ws, int64_t *info, cudaStream_t s) {
     MixedWs w = mixed_layout(ws, np, S);
+    if (cudaMemsetAsync(w.D, 0, sizeof(float) * (size_t)np * (size_t)np, s) != cudaSuccess)
+        return GP_ERR_CUDA;
     for (int64_t k0 = 0; k0 < np; k0 += NB) {
         const int64_t nb = (np - k0) < NB ? (np - k0) : NB;
         double *Akk = A + k0 + k0 * ld;
+        const int64_t rows = np - k0;
+        if (k0 > 0) {
+            dim3 g((unsigned)ceil_div(rows, 256 * 4) + 1, (unsigned)nb);
+            fold_delta_kernel<<<g, 256, 0, s>>>(Akk, ld, w.D + k0 + k0 * np, np, rows, nb, info);
+            GP_LAUNCH_CHECK();
+        }
         GP_TRY(chol_fp64_tiled(Akk, ld, nb, k0, info, s));
         const int64_t m = np - k0 - nb;
         if (m <= 0) break;
         double *P = Akk + nb;  // m x nb panel below the diagonal block
         GP_TRY(trtri_fp64_blocked(Akk, ld, nb, w.W, nb, w.tmp, info, s));
-        GP_TRY(split_bf16(w.W, nb, nb, nb, nb, 0, 0, 0, S, w.SB, s));
-        GP_TRY(split_bf16(P, ld, m, nb, nb, 0, 0, 0, S, w.SA, s));
-        TcOperand opA{w.SA, m, nb, S, 0};
-        TcOperand opW{w.SB, nb, nb, S, 0};
-        // L_ik = A_ik W^T
-        GP_TRY(tc_gemm(opA, opW, m, nb, nb, 1.0, 0.0, P, ld, 0, S, info, s));
-        GP_TRY(split_bf16(P, ld, m, nb, nb, 0, 0, 0, S, w.SA, s));
-        // A_22 -= L_ik L_ik^T (lower)
-        GP_TRY(tc_gemm(opA, opA, m, m, nb, -1.0, 1.0, P + nb * ld, ld, 1, S, info, s));
+        GP_TRY(split_rows(w.W, nb, nb, nb, nb, 0, 0, 1, S, w.SB, NB, NB, 0, 0, s));
+        GP_TRY(split_rows(P, ld, m, nb, nb, 0, 0, 0, S, w.SA, np, NB, 0, 0, s));
+        TcOperand opA{w.SA, np, NB, S, 0, 0};
+        TcOperand opW{w.SB, NB, NB, S, 0, 0};
+        // L_ik = A_ik W^T  (FP64 out)
+        TcOut o1{P, ld, 0, 1.0, 0.0, 0, 0};
+        GP_TRY(tc_gemm(opA, opW, m, nb, nb, o1, 0, 0, info, s));
+        GP_TRY(split_rows(P, ld, m, nb, nb, 0, 0, 0, S, w.SA, np, NB, 0, 0, s));
+        // D_22 -= L_ik L_ik^T (lower, FP32)
+        float *D22 = w.D + (k0 + nb) + (k0 + nb) * np;
+        TcOut o2{D22, np, 1, -1.0, 0.0, 1, 0};
+        GP_TRY(tc_gemm(opA, opA, m, m, nb, o2, 0, 0, info, s));
     }
     return GP_OK;
 }
 
 // ---------------------------------------------------------------------------
-// Standalone trailing update C (m x m, lower) -= P P^T, P m x k.
+// Standalone trailing update C (m x m, lower, FP64) -= P P^T, P m x k.
 // ---------------------------------------------------------------------------
 size_t syrk_ws_bytes(int64_t m, int64_t k, int precision, int S) {
     if (precision == GP_FP64) return 0;
@@ -86,9 +114,10 @@ int syrk_lower(double *C, int64_t ldc, const double *P, int64_t ldp, int64_t m, 
         return gemm_f64(m, m, k, -1.0, P, ldp, 0, P, ldp, 1, 1.0, C, ldc, 1, info, s);
     __nv_bfloat16 *SA = static_cast<__nv_bfloat16 *>(ws);
     const int64_t kp = round_up(k, 64);
-    GP_TRY(split_bf16(P, ldp, m, kp, k, 0, 0, 0, S, SA, s));
-    TcOperand op{SA, m, kp, S, 0};
-    return tc_gemm(op, op, m, m, kp, -1.0, 1.0, C, ldc, 1, S, info, s);
+    GP_TRY(split_rows(P, ldp, m, kp, k, 0, 0, 0, S, SA, m, kp, 0, 0, s));
+    TcOperand op{SA, m, kp, S, 0, 0};
+    TcOut o{C, ldc, 0, -1.0, 1.0, 1, 0};
+    return tc_gemm(op, op, m, m, kp, o, 0, 0, info, s);
 }
 
 }  // namespace gp

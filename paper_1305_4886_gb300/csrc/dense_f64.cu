@@ -139,6 +139,9 @@ __global__ void __launch_bounds__(256) trtri_tiles_kernel(const double *L, int64
 //   opB = 0: op(B)(k,c) = B[k + c ldb]    opB = 1: B[c + k ldb]
 // lower != 0: M == N and only 64 x 64 tiles with tile row >= tile column are
 // computed (grid is the triangular tile count).
+// mask.out_lower: write only entries with row + diag_off >= col.
+// mask.tri_k: op(B)(k, c) vanishes for k < c - tri_off; tiles start their K
+// loop there.
 // ---------------------------------------------------------------------------
 constexpr int GBK = 16;
 
@@ -147,7 +150,7 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(int64_t M, int64_t N, int
                                                        int opA, const double *__restrict__ B,
                                                        int64_t ldb, int opB, double beta,
                                                        double *C, int64_t ldc, int lower,
-                                                       const int64_t *info) {
+                                                       F64Mask mask, const int64_t *info) {
     __shared__ double As[GBK][TB + 1];
     __shared__ double Bs[GBK][TB + 1];
     if (info && failed(info)) return;
@@ -159,6 +162,9 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(int64_t M, int64_t N, int
         bj = blockIdx.y;
     }
     const int64_t r0 = bi * TB, c0 = bj * TB;
+    if (mask.out_lower && c0 > r0 + (TB - 1) + mask.diag_off) return;
+    int64_t kbeg = 0;
+    if (mask.tri_k && c0 - mask.tri_off > 0) kbeg = ((c0 - mask.tri_off) / GBK) * GBK;
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     double acc[4][4];
@@ -167,7 +173,7 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(int64_t M, int64_t N, int
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
 
-    for (int64_t k0 = 0; k0 < K; k0 += GBK) {
+    for (int64_t k0 = kbeg; k0 < K; k0 += GBK) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             int idx = tid + 256 * q;
@@ -223,6 +229,7 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(int64_t M, int64_t N, int
         for (int a = 0; a < 4; ++a) {
             int64_t gr = r0 + tx + 16 * a;
             if (gr >= M) continue;
+            if (mask.out_lower && gr + mask.diag_off < gc) continue;
             double *p = C + gr + gc * ldc;
             double v = alpha * acc[a][b];
             if (beta != 0.0) v = fma(beta, *p, v);
@@ -231,22 +238,29 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(int64_t M, int64_t N, int
     }
 }
 
-int gemm_f64(int64_t M, int64_t N, int64_t K, double alpha, const double *A, int64_t lda, int opA,
-             const double *B, int64_t ldb, int opB, double beta, double *C, int64_t ldc, int lower,
-             const int64_t *info, cudaStream_t s) {
+int gemm_f64_ex(int64_t M, int64_t N, int64_t K, double alpha, const double *A, int64_t lda,
+                int opA, const double *B, int64_t ldb, int opB, double beta, double *C, int64_t ldc,
+                int lower, const F64Mask &mask, const int64_t *info, cudaStream_t s) {
     if (M <= 0 || N <= 0) return GP_OK;
     if (lower) {
         if (M != N) return GP_ERR_INVALID;
         int64_t T = ceil_div(M, TB);
-        gemm_f64_kernel<<<(unsigned)(T * (T + 1) / 2), 256, 0, s>>>(M, N, K, alpha, A, lda, opA, B,
-                                                                    ldb, opB, beta, C, ldc, 1, info);
+        gemm_f64_kernel<<<(unsigned)(T * (T + 1) / 2), 256, 0, s>>>(
+            M, N, K, alpha, A, lda, opA, B, ldb, opB, beta, C, ldc, 1, mask, info);
     } else {
         dim3 g((unsigned)ceil_div(M, TB), (unsigned)ceil_div(N, TB));
         gemm_f64_kernel<<<g, 256, 0, s>>>(M, N, K, alpha, A, lda, opA, B, ldb, opB, beta, C, ldc, 0,
-                                          info);
+                                          mask, info);
     }
     GP_LAUNCH_CHECK();
     return GP_OK;
+}
+
+int gemm_f64(int64_t M, int64_t N, int64_t K, double alpha, const double *A, int64_t lda, int opA,
+             const double *B, int64_t ldb, int opB, double beta, double *C, int64_t ldc, int lower,
+             const int64_t *info, cudaStream_t s) {
+    F64Mask none{0, 0, 0, 0};
+    return gemm_f64_ex(M, N, K, alpha, A, lda, opA, B, ldb, opB, beta, C, ldc, lower, none, info, s);
 }
 
 // ---------------------------------------------------------------------------

@@ -12,6 +12,15 @@ int launch_cov_fill(const double *d_x, int64_t n, int64_t np, const KernParams &
                     int64_t ldc, int64_t *d_info, cudaStream_t s);
 
 // dense_f64.cu
+struct F64Mask {
+    int out_lower;
+    int64_t diag_off;
+    int tri_k;
+    int64_t tri_off;
+};
+int gemm_f64_ex(int64_t M, int64_t N, int64_t K, double alpha, const double *A, int64_t lda,
+                int opA, const double *B, int64_t ldb, int opB, double beta, double *C, int64_t ldc,
+                int lower, const F64Mask &mask, const int64_t *info, cudaStream_t s);
 int gemm_f64(int64_t M, int64_t N, int64_t K, double alpha, const double *A, int64_t lda, int opA,
              const double *B, int64_t ldb, int opB, double beta, double *C, int64_t ldc, int lower,
              const int64_t *info, cudaStream_t s);
@@ -27,7 +36,32 @@ int trsv_blocked(const double *L, int64_t ld, int64_t n, int trans, double *b,
                  const int64_t *info, cudaStream_t s);
 int lower_matvec(const double *L, int64_t ld, int64_t n, const double *z, double *y,
                  cudaStream_t s);
-int launch_loglik_reduce(const double *L, int64_t ld, int64_t n, const double *v, double *out,
-                         const int64_t *info, cudaStream_t s);
+int trsv_blocked_skip(const double *L, int64_t ld, int64_t n, int trans, double *b,
+                      const int64_t *info, const int *skip, cudaStream_t s);
+int launch_loglik_reduce(const double *L, int64_t ld, int64_t n, const double *u, const double *v,
+                         const double *resid, double *out, const int64_t *info, cudaStream_t s);
+
+// chol_mixed.cu
+size_t chol_mixed_ws_bytes(int64_t np, int S);
+int chol_mixed(double *A, int64_t ld, int64_t np, int S, void *ws, int64_t *info, cudaStream_t s);
+size_t syrk_ws_bytes(int64_t m, int64_t k, int precision, int S);
+int syrk_lower(double *C, int64_t ldc, const double *P, int64_t ldp, int64_t m, int64_t k,
+               int precision, int S, void *ws, int64_t *info, cudaStream_t s);
+
+// adjoint.cu
+size_t grad_ws_bytes(int64_t np, int precision, int S);
+int chol_inverse(double *A, int64_t ld, int64_t np, int precision, int S, void *ws, int64_t *info,
+                 cudaStream_t s);
+int grad_contract(const double *d_x, int64_t n, int64_t np, const KernParams &kp, const double *W,
+                  int64_t ld, const double *alpha, void *ws, int precision, int S, double *grad,
+                  const int64_t *info, cudaStream_t s);
+
+// refine.cu
+int cov_matvec(const double *d_x, int64_t n, int64_t np, const KernParams &kp, const double *a,
+               double *acc, const int *skip, const int64_t *info, cudaStream_t s);
+int refine_alpha(const double *d_x, int64_t n, int64_t np, const KernParams &kp, const double *L,
+                 int64_t ld, const double *r, double *alpha, double *acc, double *s,
+                 double *stats, int *conv, int max_evals, double tol, const int64_t *info,
+                 cudaStream_t st);
 
 }  // namespace gp

@@ -1,0 +1,142 @@
+// refine.cu -- iterative refinement of alpha = C^{-1} r for the mixed form,
+// against a matrix-free FP64 residual s = r - C(theta) alpha.
+//
+// C(theta) is never re-read from memory: every 64 x 64 lower tile is
+// recomputed from the locations (the same covariance routine as the fill),
+// and applied twice, C_IJ alpha_J to rows I and C_IJ^T alpha_I to rows J,
+// so each pair costs one kernel evaluation.  Row and column partial sums are
+// reduced in registers/warp shuffles and added to the accumulator with FP64
+// atomics.
+//
+// Refinement (not in the paper): with the mixed factor L~,
+//   repeat: s = r - C alpha; stop if ||s|| <= tol ||r||; alpha += L~^{-T} L~^{-1} s
+// A device flag records convergence so that later launches of a fixed-length
+// sequence return at once (no host round trip).
+#include "internal.h"
+#include "kern.cuh"
+
+namespace gp {
+
+__global__ void __launch_bounds__(256) cov_matvec_kernel(const double2 *__restrict__ x, int64_t n,
+                                                         KernParams kp,
+                                                         const double *__restrict__ a, double *acc,
+                                                         const int *skip, const int64_t *info) {
+    __shared__ double2 xc[TB];
+    __shared__ double ac[TB];
+    __shared__ double colsum[2][TB];
+    __shared__ double rowsum[4][TB];
+    if ((skip && *skip) || failed(info)) return;
+    int64_t ti, tj;
+    lower_tile_coords(blockIdx.x, ti, tj);
+    const int64_t row0 = ti * TB, col0 = tj * TB;
+    if (row0 >= n) return;
+    const int tid = threadIdx.x;
+    if (tid < TB) {
+        int64_t j = col0 + tid;
+        xc[tid] = (j < n) ? x[j] : make_double2(0.0, 0.0);
+        ac[tid] = (j < n) ? a[j] : 0.0;
+        colsum[0][tid] = 0.0;
+        colsum[1][tid] = 0.0;
+    }
+    __syncthreads();
+    const int r = tid & (TB - 1);
+    const int cg = tid >> 6;
+    const int half = (tid >> 5) & 1;
+    const int64_t i = row0 + r;
+    const bool diag = (ti == tj);
+    const bool row_ok = i < n;
+    const double2 xi = row_ok ? x[i] : make_double2(0.0, 0.0);
+    const double ai = row_ok ? a[i] : 0.0;
+    double rs = 0.0;
+    for (int c = cg; c < TB; c += 4) {
+        const int64_t j = col0 + c;
+        double v = 0.0;
+        if (row_ok && j < n) v = (i == j) ? kp.diag : cov_offdiag(kp, pair_dist(xi, xc[c]));
+        rs = fma(v, ac[c], rs);
+        if (!diag) {
+            double cs = v * ai;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
+            if ((tid & 31) == 0) colsum[half][c] += cs;  // one lane per (warp, column)
+        }
+    }
+    rowsum[cg][r] = rs;
+    __syncthreads();
+    if (tid < TB) {
+        const int64_t ii = row0 + tid;
+        if (ii < n) atomicAdd(acc + ii, rowsum[0][tid] + rowsum[1][tid] + rowsum[2][tid] + rowsum[3][tid]);
+        if (!diag) {
+            const int64_t jj = col0 + tid;
+            if (jj < n) atomicAdd(acc + jj, colsum[0][tid] + colsum[1][tid]);
+        }
+    }
+}
+
+// s = r - acc over i < n; ||s||, ||r|| reduced in one CTA (deterministic);
+// stats[0] = ||s|| / ||r||.  Sets *conv when the ratio is <= tol (or r = 0).
+__global__ void __launch_bounds__(1024) refine_resid_kernel(const double *r, const double *acc,
+                                                            int64_t n, double *s, double tol,
+                                                            double *stats, int *conv,
+                                                            const int64_t *info) {
+    __shared__ double ps[2][1024];
+    if (*conv || failed(info)) return;
+    double a = 0.0, b = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += 1024) {
+        double si = r[i] - acc[i];
+        s[i] = si;
+        a = fma(si, si, a);
+        b = fma(r[i], r[i], b);
+    }
+    ps[0][threadIdx.x] = a;
+    ps[1][threadIdx.x] = b;
+    __syncthreads();
+    for (int w = 512; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            ps[0][threadIdx.x] += ps[0][threadIdx.x + w];
+            ps[1][threadIdx.x] += ps[1][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double ratio = ps[1][0] > 0.0 ? sqrt(ps[0][0] / ps[1][0]) : 0.0;
+        stats[0] = ratio;
+        if (ratio <= tol) *conv = 1;
+    }
+}
+
+__global__ void axpy_kernel(int64_t n, const double *d, double *a, const int *skip,
+                            const int64_t *info) {
+    if (*skip || failed(info)) return;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) a[i] += d[i];
+}
+
+int cov_matvec(const double *d_x, int64_t n, int64_t np, const KernParams &kp, const double *a,
+               double *acc, const int *skip, const int64_t *info, cudaStream_t s) {
+    if (cudaMemsetAsync(acc, 0, sizeof(double) * n, s) != cudaSuccess) return GP_ERR_CUDA;
+    const int64_t T = np / TB;
+    cov_matvec_kernel<<<(unsigned)(T * (T + 1) / 2), 256, 0, s>>>(
+        reinterpret_cast<const double2 *>(d_x), n, kp, a, acc, skip, info);
+    GP_LAUNCH_CHECK();
+    return GP_OK;
+}
+
+int refine_alpha(const double *d_x, int64_t n, int64_t np, const KernParams &kp, const double *L,
+                 int64_t ld, const double *r, double *alpha, double *acc, double *s,
+                 double *stats, int *conv, int max_evals, double tol, const int64_t *info,
+                 cudaStream_t st) {
+    if (cudaMemsetAsync(conv, 0, sizeof(int), st) != cudaSuccess) return GP_ERR_CUDA;
+    for (int it = 0; it < max_evals; ++it) {
+        GP_TRY(cov_matvec(d_x, n, np, kp, alpha, acc, conv, info, st));
+        refine_resid_kernel<<<1, 1024, 0, st>>>(r, acc, n, s, tol, stats, conv, info);
+        GP_LAUNCH_CHECK();
+        if (it + 1 == max_evals) break;  // the last evaluation only reports
+        GP_TRY(trsv_blocked_skip(L, ld, n, 0, s, info, conv, st));
+        GP_TRY(trsv_blocked_skip(L, ld, n, 1, s, info, conv, st));
+        axpy_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(n, s, alpha, conv, info);
+        GP_LAUNCH_CHECK();
+    }
+    return GP_OK;
+}
+
+}  // namespace gp

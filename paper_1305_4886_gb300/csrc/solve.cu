@@ -40,8 +40,8 @@ int launch_residual(const double *y, const double *mu, int64_t n, int64_t np, do
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(32) trsv_diag_kernel(const double *L, int64_t ld, int64_t j0,
                                                        int bs, int trans, double *b,
-                                                       const int64_t *info) {
-    if (info && failed(info)) return;
+                                                       const int64_t *info, const int *skip) {
+    if ((info && failed(info)) || (skip && *skip)) return;
     const int l = threadIdx.x;
     const double *T = L + j0 + j0 * ld;
     double v0 = (l < bs) ? b[j0 + l] : 0.0;
@@ -79,9 +79,10 @@ __global__ void __launch_bounds__(32) trsv_diag_kernel(const double *L, int64_t 
 // forward update: b_i -= sum_{c < bs} L[i, j0 + c] x_c for j0+bs <= i < n
 __global__ void __launch_bounds__(256) trsv_fwd_update_kernel(const double *L, int64_t ld,
                                                               int64_t j0, int bs, int64_t n,
-                                                              double *b, const int64_t *info) {
+                                                              double *b, const int64_t *info,
+                                                              const int *skip) {
     __shared__ double xs[TB];
-    if (info && failed(info)) return;
+    if ((info && failed(info)) || (skip && *skip)) return;
     if (threadIdx.x < bs) xs[threadIdx.x] = b[j0 + threadIdx.x];
     __syncthreads();
     int64_t i = j0 + bs + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -95,8 +96,9 @@ __global__ void __launch_bounds__(256) trsv_fwd_update_kernel(const double *L, i
 // backward update: b_c -= sum_{r < bs} L[j0 + r, c] x_r for 0 <= c < j0
 __global__ void __launch_bounds__(256) trsv_bwd_update_kernel(const double *L, int64_t ld,
                                                               int64_t j0, int bs, double *b,
-                                                              const int64_t *info) {
-    if (info && failed(info)) return;
+                                                              const int64_t *info,
+                                                              const int *skip) {
+    if ((info && failed(info)) || (skip && *skip)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double x0 = (lane < bs) ? b[j0 + lane] : 0.0;
     double x1 = (lane + 32 < bs) ? b[j0 + lane + 32] : 0.0;
@@ -115,19 +117,20 @@ __global__ void __launch_bounds__(256) trsv_bwd_update_kernel(const double *L, i
 }
 
 // In-place solve on b (n values): trans = 0 -> L^{-1} b, trans = 1 -> L^{-T} b.
-int trsv_blocked(const double *L, int64_t ld, int64_t n, int trans, double *b,
-                 const int64_t *info, cudaStream_t s) {
+// skip (nullable): a device flag that turns every launch into a no-op.
+int trsv_blocked_skip(const double *L, int64_t ld, int64_t n, int trans, double *b,
+                      const int64_t *info, const int *skip, cudaStream_t s) {
     const int64_t T = ceil_div(n, TB);
     if (trans == 0) {
         for (int64_t t = 0; t < T; ++t) {
             const int64_t j0 = t * TB;
             const int bs = (int)((n - j0) < TB ? (n - j0) : TB);
-            trsv_diag_kernel<<<1, 32, 0, s>>>(L, ld, j0, bs, 0, b, info);
+            trsv_diag_kernel<<<1, 32, 0, s>>>(L, ld, j0, bs, 0, b, info, skip);
             GP_LAUNCH_CHECK();
             const int64_t rest = n - j0 - bs;
             if (rest > 0) {
                 trsv_fwd_update_kernel<<<(unsigned)ceil_div(rest, 256), 256, 0, s>>>(L, ld, j0, bs, n,
-                                                                                      b, info);
+                                                                                      b, info, skip);
                 GP_LAUNCH_CHECK();
             }
         }
@@ -135,16 +138,21 @@ int trsv_blocked(const double *L, int64_t ld, int64_t n, int trans, double *b,
         for (int64_t t = T - 1; t >= 0; --t) {
             const int64_t j0 = t * TB;
             const int bs = (int)((n - j0) < TB ? (n - j0) : TB);
-            trsv_diag_kernel<<<1, 32, 0, s>>>(L, ld, j0, bs, 1, b, info);
+            trsv_diag_kernel<<<1, 32, 0, s>>>(L, ld, j0, bs, 1, b, info, skip);
             GP_LAUNCH_CHECK();
             if (j0 > 0) {
                 trsv_bwd_update_kernel<<<(unsigned)ceil_div(j0, 64), 256, 0, s>>>(L, ld, j0, bs, b,
-                                                                                   info);
+                                                                                   info, skip);
                 GP_LAUNCH_CHECK();
             }
         }
     }
     return GP_OK;
+}
+
+int trsv_blocked(const double *L, int64_t ld, int64_t n, int trans, double *b,
+                 const int64_t *info, cudaStream_t s) {
+    return trsv_blocked_skip(L, ld, n, trans, b, info, nullptr, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -181,7 +189,7 @@ int lower_matvec(const double *L, int64_t ld, int64_t n, const double *z, double
 }
 
 // ---------------------------------------------------------------------------
-// logdet = 2 sum log L_ii and q = v^T v over i < n, Neumaier-compensated per
+// logdet = 2 sum log L_ii and q = u^T v over i < n, Neumaier-compensated per
 // thread and combined in thread order (deterministic).  out = {loglik,
 // logdet, q, resid}; NaN when *info != 0.
 // ---------------------------------------------------------------------------
@@ -197,13 +205,14 @@ struct NSum {
 };
 
 __global__ void __launch_bounds__(1024) loglik_reduce_kernel(const double *L, int64_t ld, int64_t n,
-                                                             const double *v, double resid,
-                                                             double *out, const int64_t *info) {
+                                                             const double *u, const double *v,
+                                                             const double *resid, double *out,
+                                                             const int64_t *info) {
     __shared__ double ps[2][1024];
     NSum a, b;
     for (int64_t i = threadIdx.x; i < n; i += 1024) {
         a.add(log(L[i + i * ld]));
-        b.add(v[i] * v[i]);
+        b.add(u[i] * v[i]);
     }
     ps[0][threadIdx.x] = a.get();
     ps[1][threadIdx.x] = b.get();
@@ -222,14 +231,14 @@ __global__ void __launch_bounds__(1024) loglik_reduce_kernel(const double *L, in
             out[0] = -0.5 * logdet - 0.5 * q - 0.5 * (double)n * LOG_2PI;
             out[1] = logdet;
             out[2] = q;
-            out[3] = resid;
+            out[3] = resid ? *resid : 0.0;
         }
     }
 }
 
-int launch_loglik_reduce(const double *L, int64_t ld, int64_t n, const double *v, double *out,
-                         const int64_t *info, cudaStream_t s) {
-    loglik_reduce_kernel<<<1, 1024, 0, s>>>(L, ld, n, v, 0.0, out, info);
+int launch_loglik_reduce(const double *L, int64_t ld, int64_t n, const double *u, const double *v,
+                         const double *resid, double *out, const int64_t *info, cudaStream_t s) {
+    loglik_reduce_kernel<<<1, 1024, 0, s>>>(L, ld, n, u, v, resid, out, info);
     GP_LAUNCH_CHECK();
     return GP_OK;
 }

@@ -1,198 +1,119 @@
-// tc_gemm.cu -- the dense contraction of the trailing update (Sec. 2.1: "most
-// of the total work is in the matrix multiplications") on the sm_103a
-// tensor cores, with FP64 operands carried as BF16 slices.
+// tc_gemm.cu -- the dense contractions of the blocked Cholesky (Sec. 2.1:
+// "most of the total work is in the matrix multiplications") and of the
+// gradient's inverse, on the sm_103a tensor cores, with FP64 operands
+// carried as BF16 slices.
 //
-// Operand splitting.  Each FP64 operand element x is written as a sum of
-// S BF16 slices, s_0 = bf16(x), s_1 = bf16(x - s_0), s_2 = bf16(x - s_0 - s_1);
-// each slice keeps 8 more significant bits, so three slices carry x to about
-// 2^-24 relative.  A product x*y is then the sum of the slice products
-// s_p t_q with p + q < S (6 products for S = 3; the dropped ones are below
-// 2^-24 relative).  All of them accumulate in one FP32 accumulator in
-// tensor memory, so the contraction is FP32-accurate; the factor's FP64
-// parts (diagonal blocks, pivots, log-determinant, residuals) stay FP64.
+// Operand splitting (row-scaled).  For operand row r let 2^e_r bound its
+// entries over the packed K range.  Each FP64 entry x becomes three BF16
+// slices:
+//   s0 = round(x 2^{7-e_r}) 2^{e_r-7}     an integer in [-128, 128] times a
+//                                         per-row power of two (exact in BF16)
+//   s1 = bf16(x - s0),  s2 = bf16(x - s0 - s1)
+// so x = s0 + s1 + s2 to about 2^-26 of the row's largest entry.  A product
+// sum over k is the sum of slice products s_p t_q with p + q < 3 (the
+// dropped ones are below 2^-25 of the row maxima).  The leading products
+// s0 t0 are integers times one common power of two for a given output
+// (r, c); their sums stay below 2^24 units for K <= 1024, so the FP32
+// tensor-core accumulator holds them exactly however it rounds.  They go to
+// their own accumulator ("hi"); the five smaller products share a second one
+// ("lo"), whose rounding is 2^-7 smaller.  The epilogue adds hi + lo.
 //
-// Slice layout.  An operand of R rows and K columns is packed as
-// bf16[S][R][K] (K contiguous, "K-major"), read by TMA with a 3-D tensor map
-// {K, R, S} in 64 x rows boxes with the 128-byte swizzle, which is the
-// canonical K-major SWIZZLE_128B layout the tcgen05 shared-memory
-// descriptors address.
-//
-// Kernel.  One CTA per 128 x 256 output tile, 6 warps:
-//   warp 0  TMA producer (one elected thread), 4-stage ring of 48 KB stages;
-//   warp 1  TMEM allocation (256 FP32 columns) and the MMA issuer (one
-//           thread issues tcgen05.mma.cta_group::1.kind::f16 with BF16
-//           inputs, 4 x K16 per stage, and tcgen05.commit to free the stage);
-//   warps 2-5  epilogue: tcgen05.ld 32 lanes x 32 columns, then
-//           C = beta C + alpha acc in FP64, one row per thread, so each warp
-//           store covers 32 consecutive rows of a column (coalesced).
-// Every mbarrier wait is bounded; a wait that gives up sets *info = -1 and
-// the CTA winds down (waiting, again bounded, for its copies in flight)
-// and frees its tensor memory.
+// Kernel.  Persistent: one CTA per SM walks a static tile schedule of
+// 128 x 128 output tiles (grouped 16 tile-rows at a time so the operand
+// tiles in flight stay in L2).  6 warps:
+//   warp 0     TMA producer (one thread): a 6-stage ring of 32 KB stages
+//              (A and B 128 x 64 BF16 boxes, 128-byte swizzle).
+//   warp 1     TMEM owner (512 columns = 2 tile buffers x {hi, lo}) and MMA
+//              issuer (one thread): tcgen05.mma.cta_group::1.kind::f16,
+//              128 x 128 x 16 per instruction; tcgen05.commit frees stages
+//              and hands finished accumulators to the epilogue.
+//   warps 2-5  epilogue: tcgen05.ld of hi and lo (32 lanes x 32 columns),
+//              output in FP64 (C = beta C + alpha acc) or FP32 (C += alpha
+//              acc), one row per thread so that every warp access covers 32
+//              consecutive rows of one column; all loads of a 32-column chunk
+//              are issued before any store.  The two TMEM buffers let the
+//              epilogue of one tile overlap the MMAs of the next.
+// Every mbarrier wait is bounded (1 s); a wait that gives up sets
+// *info = -1, the roles wind down (the producer waits, bounded, for its
+// copies in flight) and TMEM is freed.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
 #include "internal.h"
 #include "tc_gemm.h"
+#include "tc_ptx.cuh"
 
 namespace gp {
 
 constexpr int TC_BM = 128;
-constexpr int TC_BN = 256;
+constexpr int TC_BN = 128;
 constexpr int TC_BK = 64;
-constexpr int TC_STAGES = 4;
+constexpr int TC_STAGES = 6;
 constexpr int TC_A_BYTES = TC_BM * TC_BK * 2;
 constexpr int TC_B_BYTES = TC_BN * TC_BK * 2;
 constexpr int TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;
 constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024 /*barriers*/ + 1024 /*align*/;
-constexpr uint32_t TC_TMEM_COLS = 256;
-constexpr uint32_t WAIT_LIMIT = 1u << 24;  // x ~100 ns backoff: well above any real wait
+constexpr uint32_t TC_TMEM_COLS = 512;
+constexpr int TC_GROUP = 16;  // tile rows per scheduling group
+constexpr int TC_MAX_PAIRS = 6;
 
-// ---------------------------------------------------------------------------
-// PTX wrappers
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
+struct TcGemmArgs {
+    void *C;
+    int64_t ldc;
+    int fp32;
+    double alpha, beta;
+    int lower;
+    int64_t diag_off;
+    int64_t M, N;
+    int a_row_off, b_row_off, a_k_off, b_k_off;
+    int kblocks;
+    int tri_k;
+    int64_t tri_off;
+    int tiles_m, tiles_n;
+    int npairs;
+    int pa[TC_MAX_PAIRS], pb[TC_MAX_PAIRS];
+    int64_t *info;
+};
 
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-                 : "memory");
-}
+struct TileInfo {
+    int tm, tn, kb_lo, kb_hi;
+    bool skip;
+};
 
-__device__ __forceinline__ void fence_barrier_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait: false when the budget ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (uint32_t i = 0; i < WAIT_LIMIT; ++i) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (i > 16) __nanosleep(64);
+__device__ __forceinline__ TileInfo tile_at(const TcGemmArgs &a, int t) {
+    TileInfo ti;
+    const int per_group = TC_GROUP * a.tiles_n;
+    const int g = t / per_group;
+    const int rem = t - g * per_group;
+    const int rows_in_group = min(TC_GROUP, a.tiles_m - g * TC_GROUP);
+    ti.tn = rem / rows_in_group;
+    ti.tm = g * TC_GROUP + rem % rows_in_group;
+    const int64_t row0 = (int64_t)ti.tm * TC_BM, col0 = (int64_t)ti.tn * TC_BN;
+    ti.skip = a.lower && (col0 > row0 + (TC_BM - 1) + a.diag_off);
+    ti.kb_lo = 0;
+    if (a.tri_k) {
+        int64_t k0 = col0 - a.tri_off;
+        ti.kb_lo = k0 > 0 ? (int)(k0 / TC_BK) : 0;
     }
-    return false;
+    ti.kb_hi = a.kblocks;
+    return ti;
 }
 
-__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int x,
-                                            int y, int z) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-        "[%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
-        : "memory");
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(dst)),
-                 "r"(ncols)
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_relinquish() {
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
-                 : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tc_fence_after() {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void mma_bf16_ss(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                            uint32_t idesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart (SBO); LBO unused for swizzled K-major; version 1.
-__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
-    d |= static_cast<uint64_t>(1) << 16;
-    d |= static_cast<uint64_t>(1024 >> 4) << 32;
-    d |= static_cast<uint64_t>(1) << 46;
-    d |= static_cast<uint64_t>(2) << 61;
-    return d;
-}
-
-// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
-__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
-           (static_cast<uint32_t>(M >> 4) << 24);
-}
-
-// ---------------------------------------------------------------------------
-// the kernel
-// ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(192, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    TcGemmArgs args) {
     extern __shared__ uint8_t smem_raw[];
-    const int tile_m = blockIdx.x, tile_n = blockIdx.y;
-    const int64_t row0 = (int64_t)tile_m * TC_BM, col0 = (int64_t)tile_n * TC_BN;
-    if (args.lower && col0 >= row0 + TC_BM) return;  // tile strictly above the diagonal
     if (args.info && failed(args.info)) return;
-
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                 ~static_cast<uintptr_t>(1023));
-    uint8_t *stage_base = smem;
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + TC_STAGES * TC_STAGE_BYTES);
     uint64_t *empty = full + TC_STAGES;
-    uint64_t *done = empty + TC_STAGES;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
-    __shared__ int abort_flag;
+    uint64_t *tfull = empty + TC_STAGES;   // [2] accumulator ready
+    uint64_t *tempty = tfull + 2;          // [2] accumulator drained
+    uint64_t *drain = tempty + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    __shared__ volatile int abort_flag;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -200,7 +121,11 @@ __global__ void __launch_bounds__(192, 1)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(done, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 4);
+        }
+        mbar_init(drain, 1);
         abort_flag = 0;
         fence_barrier_init();
     }
@@ -212,79 +137,158 @@ __global__ void __launch_bounds__(192, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const int kt = args.npairs * args.kblocks;
+    const int ntiles = args.tiles_m * args.tiles_n;
 
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer ----------------
-        int issued = 0;
-        for (int it = 0; it < kt; ++it) {
-            const int s = it % TC_STAGES, use = it / TC_STAGES;
-            if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1)) {
-                abort_flag = 1;
-                break;
+        uint32_t it = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const TileInfo ti = tile_at(args, t);
+            if (ti.skip) continue;
+            const int ra = ti.tm * TC_BM + args.a_row_off, rb = ti.tn * TC_BN + args.b_row_off;
+            for (int p = 0; p < args.npairs && ok; ++p) {
+                for (int kb = ti.kb_lo; kb < ti.kb_hi; ++kb, ++it) {
+                    const uint32_t s = it % TC_STAGES, use = it / TC_STAGES;
+                    if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    if (abort_flag) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *a_s = smem + s * TC_STAGE_BYTES;
+                    mbar_arrive_expect_tx(&full[s], TC_STAGE_BYTES);
+                    const int kx = kb * TC_BK;
+                    tma_load_3d(a_s, &tmA, &full[s], args.a_k_off + kx, ra, args.pa[p]);
+                    tma_load_3d(a_s + TC_A_BYTES, &tmB, &full[s], args.b_k_off + kx, rb, args.pb[p]);
+                }
             }
-            const int pair = it / args.kblocks, kb = it % args.kblocks;
-            uint8_t *a_s = stage_base + s * TC_STAGE_BYTES;
-            uint8_t *b_s = a_s + TC_A_BYTES;
-            mbar_arrive_expect_tx(&full[s], TC_STAGE_BYTES);
-            tma_load_3d(a_s, &tmA, &full[s], kb * TC_BK, (int)row0 + args.a_row_off, args.pa[pair]);
-            tma_load_3d(b_s, &tmB, &full[s], kb * TC_BK, (int)col0 + args.b_row_off, args.pb[pair]);
-            issued = it + 1;
         }
-        // drain: every issued stage must land before the CTA may exit
-        for (int it = (issued > TC_STAGES ? issued - TC_STAGES : 0); it < issued; ++it) {
-            const int s = it % TC_STAGES, use = it / TC_STAGES;
-            mbar_wait(&full[s], use & 1);
-        }
+        if (!ok) abort_flag = 1;
+        // drain: copies still in flight must land before the CTA exits
+        for (uint32_t j = (it > TC_STAGES ? it - TC_STAGES : 0); j < it; ++j)
+            mbar_wait(&full[j % TC_STAGES], (j / TC_STAGES) & 1);
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
         constexpr uint32_t idesc = idesc_bf16_f32(TC_BM, TC_BN);
+        uint32_t it = 0, local = 0;
         bool ok = true;
-        for (int it = 0; it < kt; ++it) {
-            const int s = it % TC_STAGES, use = it / TC_STAGES;
-            if (!mbar_wait(&full[s], use & 1)) {
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const TileInfo ti = tile_at(args, t);
+            if (ti.skip) continue;
+            const uint32_t buf = local & 1, u = local >> 1;
+            if (u > 0 && !mbar_wait(&tempty[buf], (u - 1) & 1)) {
                 ok = false;
                 break;
             }
             tc_fence_after();
-            const uint32_t a_addr = smem_u32(stage_base + s * TC_STAGE_BYTES);
-            const uint32_t b_addr = a_addr + TC_A_BYTES;
+            for (int p = 0; p < args.npairs && ok; ++p) {
+                const uint32_t acc = tmem + (buf * 2 + (p > 0 ? 1 : 0)) * TC_BN;
+                const bool first_of_acc = (p <= 1);
+                for (int kb = ti.kb_lo; kb < ti.kb_hi; ++kb, ++it) {
+                    const uint32_t s = it % TC_STAGES, use = it / TC_STAGES;
+                    if (!mbar_wait(&full[s], use & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a_addr = smem_u32(smem + s * TC_STAGE_BYTES);
+                    const uint32_t b_addr = a_addr + TC_A_BYTES;
 #pragma unroll
-            for (int k = 0; k < TC_BK / 16; ++k) {
-                mma_bf16_ss(tmem, sdesc_sw128(a_addr + k * 32), sdesc_sw128(b_addr + k * 32), idesc,
-                            (it > 0 || k > 0) ? 1u : 0u);
+                    for (int k = 0; k < TC_BK / 16; ++k) {
+                        const uint32_t accumulate = (first_of_acc && kb == ti.kb_lo && k == 0) ? 0u : 1u;
+                        mma_bf16_ss(acc, sdesc_sw128(a_addr + k * 32), sdesc_sw128(b_addr + k * 32),
+                                    idesc, accumulate);
+                    }
+                    mma_commit(&empty[s]);
+                }
             }
-            mma_commit(&empty[s]);
+            mma_commit(&tfull[buf]);
+            ++local;
         }
         if (!ok) abort_flag = 1;
-        mma_commit(done);  // arrives once all issued MMAs have completed
+        mma_commit(drain);
+        mbar_wait(drain, 0);
     } else if (warp >= 2) {
         // ---------------- epilogue ----------------
         const int q = warp & 3;  // TMEM lane quarter this warp may access
-        bool ok = mbar_wait(done, 0);
-        tc_fence_after();
-        const bool go = __all_sync(0xffffffffu, ok && !abort_flag);
-        if (go) {
-            const int64_t row = row0 + q * 32 + lane;
-            const double alpha = args.alpha, beta = args.beta;
+        uint32_t local = 0;
+        const float alpha_f = static_cast<float>(args.alpha);
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            const TileInfo ti = tile_at(args, t);
+            if (ti.skip) continue;
+            const uint32_t buf = local & 1, u = local >> 1;
+            bool ok = mbar_wait(&tfull[buf], u & 1);
+            ok = __all_sync(0xffffffffu, ok) && !abort_flag;
+            if (!ok) {
+                if (lane == 0) abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            const bool has_acc = ti.kb_lo < ti.kb_hi;
+            const bool has_lo = args.npairs > 1;
+            const int64_t row = (int64_t)ti.tm * TC_BM + q * 32 + lane;
+            const bool row_ok = row < args.M;
             for (int c0 = 0; c0 < TC_BN; c0 += 32) {
-                uint32_t v[32];
-                tmem_ld_32x32b_x32(tmem + (static_cast<uint32_t>(q * 32) << 16) + c0, v);
-                if (row >= args.M) continue;
+                uint32_t hi[32], lo[32];
+                if (has_acc) {
+                    const uint32_t base = tmem + (static_cast<uint32_t>(q * 32) << 16) + c0;
+                    tmem_ld_32x32b_x32(base + (buf * 2) * TC_BN, hi);
+                    if (has_lo) tmem_ld_32x32b_x32(base + (buf * 2 + 1) * TC_BN, lo);
+                    tmem_ld_wait();
+                }
+                float v[32];
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    const int64_t col = col0 + c0 + j;
-                    if (col >= args.N) break;
-                    if (args.lower && row < col) continue;
-                    double *p = args.C + row + col * args.ldc;
-                    double acc = static_cast<double>(__uint_as_float(v[j]));
-                    double r = alpha * acc;
-                    if (beta != 0.0) r = fma(beta, *p, r);
-                    *p = r;
+                    float h = has_acc ? __uint_as_float(hi[j]) : 0.0f;
+                    float l = (has_acc && has_lo) ? __uint_as_float(lo[j]) : 0.0f;
+                    v[j] = h + l;
+                }
+                const int64_t colb = (int64_t)ti.tn * TC_BN + c0;
+                bool okc[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int64_t col = colb + j;
+                    okc[j] = row_ok && col < args.N && (!args.lower || row + args.diag_off >= col);
+                }
+                if (args.fp32) {
+                    float *base = static_cast<float *>(args.C) + row + colb * args.ldc;
+                    float old[32];
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) old[j] = okc[j] ? base[j * args.ldc] : 0.0f;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (okc[j]) base[j * args.ldc] = fmaf(alpha_f, v[j], old[j]);
+                } else {
+                    double *base = static_cast<double *>(args.C) + row + colb * args.ldc;
+                    if (args.beta != 0.0) {
+                        double old[32];
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) old[j] = okc[j] ? base[j * args.ldc] : 0.0;
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (okc[j])
+                                base[j * args.ldc] =
+                                    fma(args.beta, old[j], args.alpha * static_cast<double>(v[j]));
+                    } else if (args.alpha == 1.0 || args.alpha == -1.0) {
+                        const float sg = args.alpha > 0.0 ? 1.0f : -1.0f;
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (okc[j]) base[j * args.ldc] = static_cast<double>(sg * v[j]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (okc[j]) base[j * args.ldc] = args.alpha * static_cast<double>(v[j]);
+                    }
                 }
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[buf]);
+            ++local;
         }
-        if (!ok && lane == 0) abort_flag = 1;
     }
     tc_fence_before();
     __syncthreads();
@@ -296,63 +300,135 @@ __global__ void __launch_bounds__(192, 1)
 }
 
 // ---------------------------------------------------------------------------
-// Split FP64 -> BF16 slices.
-// src(r, k) = src[r + k ld]          (trans = 0: rows of the operand are rows
-//                                     of the column-major source)
-// src(r, k) = src[k + r ld]          (trans = 1: rows are source columns)
-// lower_mask: zero entries with source row < source column (a triangular
-// source whose upper part holds stale data).
-// dst[p][r][k], p < S, shape S x R x K (K contiguous); columns k >= Kvalid
-// are written as zeros (K padded to the 64-column MMA step).  32 x 32 tiles are
-// transposed through shared memory so both sides stay coalesced.
+// Row-scaled split of FP64 operands into three BF16 slices (see the top of
+// this file).  The operand element (r, k) is
+//   trans = 0: src[r + k ld]   (operand rows are rows of the column-major
+//                               source, K runs along its columns)
+//   trans = 1: src[k + r ld]   (operand rows are source columns)
+// lower_mask: entries above the source diagonal are treated as zero
+// (trans = 0: r + diag_off < k; trans = 1: k + diag_off < r), for triangular
+// sources whose upper part holds stale data.  One CTA packs 32 rows over
+// the whole K range: pass 1 finds each row's bound 2^e_r, pass 2 writes the
+// slices with k contiguous (trans = 0 goes through a shared-memory
+// transpose so that both the FP64 reads and the BF16 writes are coalesced).
+// The split runs in FP32 after one FP64 -> (hi, lo) FP32 conversion.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) split_bf16_kernel(const double *__restrict__ src, int64_t ld,
-                                                          int64_t R, int64_t K, int64_t Kvalid,
-                                                          int trans, int64_t diag_off,
-                                                          int lower_mask, int S,
-                                                          __nv_bfloat16 *__restrict__ dst) {
-    __shared__ double t[32][33];
-    const int64_t r0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 32;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // ty 0..7
-    // load a 32 x 32 block indexed [r][k]
-    for (int i = ty; i < 32; i += 8) {
-        double v = 0.0;
-        if (trans == 0) {
-            const int64_t r = r0 + tx, k = k0 + i;  // source rows contiguous: r fastest
-            if (r < R && k < Kvalid) {
-                v = src[r + k * ld];
-                if (lower_mask && r + diag_off < k) v = 0.0;
+struct SplitArgs {
+    const double *src;
+    int64_t ld, R, K, Kvalid;
+    int trans;
+    int64_t diag_off;
+    int lower_mask;
+    int S;
+    __nv_bfloat16 *dst;
+    int64_t dst_rows, dst_kld, dst_row_off, dst_k_off;
+};
+
+__device__ __forceinline__ double split_get(const SplitArgs &a, int64_t r, int64_t k) {
+    if (r >= a.R || k >= a.Kvalid) return 0.0;
+    if (a.lower_mask) {
+        if (a.trans ? (k + a.diag_off < r) : (r + a.diag_off < k)) return 0.0;
+    }
+    return a.trans ? a.src[k + r * a.ld] : a.src[r + k * a.ld];
+}
+
+// s0, s1, s2 for one entry, given the row's scale 2^{7-e} (sc) and 2^{e-7} (isc).
+__device__ __forceinline__ void split3(double x, float sc, float isc, __nv_bfloat16 (&s)[3]) {
+    const float xh = static_cast<float>(x);
+    const float xl = static_cast<float>(x - static_cast<double>(xh));
+    const float q = rintf(xh * sc);
+    const float s0 = q * isc;
+    const float r1 = (xh - s0) + xl;
+    const __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
+    const float r2 = r1 - __bfloat162float(b1);
+    s[0] = __float2bfloat16_rn(s0);
+    s[1] = b1;
+    s[2] = __float2bfloat16_rn(r2);
+}
+
+__global__ void __launch_bounds__(256) split_rows_kernel(SplitArgs a) {
+    __shared__ float pmax[8][32];
+    __shared__ float sc_s[32], isc_s[32];
+    __shared__ unsigned short tile[3][32][33];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t r0 = (int64_t)blockIdx.x * 32;
+    // pass 1: row bounds
+    if (a.trans == 0) {
+        float m = 0.0f;
+        for (int64_t k = warp; k < a.Kvalid; k += 8)
+            m = fmaxf(m, fabsf(static_cast<float>(split_get(a, r0 + lane, k))));
+        pmax[warp][lane] = m;
+    } else {
+        for (int i = warp; i < 32; i += 8) {
+            float m = 0.0f;
+            for (int64_t k = lane; k < a.Kvalid; k += 32)
+                m = fmaxf(m, fabsf(static_cast<float>(split_get(a, r0 + i, k))));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (lane == 0) {
+                pmax[0][i] = m;
+                for (int w = 1; w < 8; ++w) pmax[w][i] = 0.0f;
             }
-            t[tx][i] = v;
-        } else {
-            const int64_t r = r0 + i, k = k0 + tx;  // source column r, row k: k fastest
-            if (r < R && k < Kvalid) {
-                v = src[k + r * ld];
-                if (lower_mask && k + diag_off < r) v = 0.0;
-            }
-            t[i][tx] = v;
         }
     }
     __syncthreads();
-    const int64_t RK = R * K;
-    for (int i = ty; i < 32; i += 8) {
-        const int64_t r = r0 + i, k = k0 + tx;
-        if (r >= R || k >= K) continue;
-        double x = t[i][tx];
-        __nv_bfloat16 *d = dst + r * K + k;
-        for (int p = 0; p < S; ++p) {
-            __nv_bfloat16 h = __double2bfloat16(x);
-            d[p * RK] = h;
-            x -= static_cast<double>(__bfloat162float(h));
+    if (threadIdx.x < 32) {
+        float m = 0.0f;
+        for (int w = 0; w < 8; ++w) m = fmaxf(m, pmax[w][threadIdx.x]);
+        // the float rounding of the max can round up across a power of two;
+        // one extra unit of headroom keeps |x 2^{7-e}| <= 128
+        int e = 0;
+        if (m > 0.0f) e = ilogbf(m) + 1;
+        e = max(-100, min(e, 120));
+        sc_s[threadIdx.x] = ldexpf(1.0f, 7 - e);
+        isc_s[threadIdx.x] = ldexpf(1.0f, e - 7);
+    }
+    __syncthreads();
+    const int64_t slice = a.dst_rows * a.dst_kld;
+    __nv_bfloat16 *d0 = a.dst + (a.dst_row_off + r0) * a.dst_kld + a.dst_k_off;
+    if (a.trans == 0) {
+        for (int64_t kc = 0; kc < a.K; kc += 32) {
+            // lane = row: coalesced FP64 reads down each column
+            for (int i = warp; i < 32; i += 8) {
+                __nv_bfloat16 s[3];
+                split3(split_get(a, r0 + lane, kc + i), sc_s[lane], isc_s[lane], s);
+#pragma unroll
+                for (int p = 0; p < 3; ++p) tile[p][i][lane] = __bfloat16_as_ushort(s[p]);
+            }
+            __syncthreads();
+            // lane = k: coalesced BF16 writes along each row
+            for (int i = warp; i < 32; i += 8) {
+                const int64_t r = r0 + i, k = kc + lane;
+                if (r < a.R && k < a.K) {
+                    for (int p = 0; p < a.S; ++p)
+                        d0[p * slice + (int64_t)i * a.dst_kld + k] =
+                            __ushort_as_bfloat16(tile[p][lane][i]);
+                }
+            }
+            __syncthreads();
+        }
+    } else {
+        for (int i = warp; i < 32; i += 8) {
+            const int64_t r = r0 + i;
+            if (r >= a.R) continue;
+            for (int64_t k = lane; k < a.K; k += 32) {
+                __nv_bfloat16 s[3];
+                split3(split_get(a, r, k), sc_s[i], isc_s[i], s);
+                for (int p = 0; p < a.S; ++p) d0[p * slice + (int64_t)i * a.dst_kld + k] = s[p];
+            }
         }
     }
 }
 
-int split_bf16(const double *src, int64_t ld, int64_t R, int64_t K, int64_t Kvalid, int trans,
-               int64_t diag_off, int lower_mask, int S, __nv_bfloat16 *dst, cudaStream_t s) {
+int split_rows(const double *src, int64_t ld, int64_t R, int64_t K, int64_t Kvalid, int trans,
+               int64_t diag_off, int lower_mask, int S, __nv_bfloat16 *dst, int64_t dst_rows,
+               int64_t dst_kld, int64_t dst_row_off, int64_t dst_k_off, cudaStream_t s) {
     if (R <= 0 || K <= 0) return GP_OK;
-    dim3 g((unsigned)ceil_div(K, 32), (unsigned)ceil_div(R, 32));
-    split_bf16_kernel<<<g, 256, 0, s>>>(src, ld, R, K, Kvalid, trans, diag_off, lower_mask, S, dst);
+    if (S < 1 || S > 3 || dst_row_off + R > dst_rows || dst_k_off + K > dst_kld)
+        return GP_ERR_INVALID;
+    SplitArgs a{src, ld, R, K, Kvalid < K ? Kvalid : K, trans, diag_off, lower_mask, S, dst,
+                dst_rows, dst_kld, dst_row_off, dst_k_off};
+    split_rows_kernel<<<(unsigned)ceil_div(R, 32), 256, 0, s>>>(a);
     GP_LAUNCH_CHECK();
     return GP_OK;
 }
@@ -373,26 +449,36 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-static int make_slice_map(CUtensorMap *map, const __nv_bfloat16 *base, int64_t R, int64_t K, int S,
-                          int box_rows) {
+static int make_slice_map(CUtensorMap *map, const TcOperand &op, int box_rows) {
     auto fn = encode_fn();
     if (!fn) return GP_ERR_CUDA;
-    if ((reinterpret_cast<uintptr_t>(base) & 15) || (K * 2) % 16) return GP_ERR_INVALID;
-    cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)R, (cuuint64_t)S};
-    cuuint64_t strides[2] = {(cuuint64_t)K * 2, (cuuint64_t)(R * K * 2)};
+    if ((reinterpret_cast<uintptr_t>(op.slices) & 15) || (op.Kld % TC_BK)) return GP_ERR_INVALID;
+    cuuint64_t dims[3] = {(cuuint64_t)op.Kld, (cuuint64_t)op.rows, (cuuint64_t)op.S};
+    cuuint64_t strides[2] = {(cuuint64_t)op.Kld * 2, (cuuint64_t)(op.rows * op.Kld * 2)};
     cuuint32_t box[3] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16 *>(base), dims,
-                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16 *>(op.slices),
+                    dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? GP_OK : GP_ERR_CUDA;
 }
 
-int tc_gemm(const TcOperand &A, const TcOperand &B, int64_t M, int64_t N, int64_t K, double alpha,
-            double beta, double *C, int64_t ldc, int lower, int nslices, int64_t *info,
-            cudaStream_t s) {
+static int num_sms() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) n = 0;
+    }
+    return n;
+}
+
+int tc_gemm(const TcOperand &A, const TcOperand &B, int64_t M, int64_t N, int64_t K,
+            const TcOut &out, int tri_k, int64_t tri_off, int64_t *info, cudaStream_t s) {
     if (M <= 0 || N <= 0) return GP_OK;
-    if (K % TC_BK) return GP_ERR_INVALID;
+    if (K % TC_BK || A.k_off % TC_BK || B.k_off % TC_BK) return GP_ERR_INVALID;
+    if (A.k_off + K > A.Kld || B.k_off + K > B.Kld || A.S != B.S) return GP_ERR_INVALID;
     static bool attr_set = false;
     if (!attr_set) {
         if (cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -401,30 +487,40 @@ int tc_gemm(const TcOperand &A, const TcOperand &B, int64_t M, int64_t N, int64_
         attr_set = true;
     }
     CUtensorMap ma, mb;
-    GP_TRY(make_slice_map(&ma, A.slices, A.rows, A.K, A.S, TC_BM));
-    GP_TRY(make_slice_map(&mb, B.slices, B.rows, B.K, B.S, TC_BN));
+    GP_TRY(make_slice_map(&ma, A, TC_BM));
+    GP_TRY(make_slice_map(&mb, B, TC_BN));
     TcGemmArgs a{};
-    a.C = C;
-    a.ldc = ldc;
+    a.C = out.C;
+    a.ldc = out.ldc;
+    a.fp32 = out.fp32;
+    a.alpha = out.alpha;
+    a.beta = out.beta;
+    a.lower = out.lower;
+    a.diag_off = out.diag_off;
     a.M = M;
     a.N = N;
-    a.alpha = alpha;
-    a.beta = beta;
-    a.kblocks = (int)(K / TC_BK);
-    a.lower = lower;
-    a.info = info;
     a.a_row_off = (int)A.row_off;
     a.b_row_off = (int)B.row_off;
+    a.a_k_off = (int)A.k_off;
+    a.b_k_off = (int)B.k_off;
+    a.kblocks = (int)(K / TC_BK);
+    a.tri_k = tri_k;
+    a.tri_off = tri_off;
+    a.tiles_m = (int)ceil_div(M, TC_BM);
+    a.tiles_n = (int)ceil_div(N, TC_BN);
+    a.info = info;
     int np = 0;
-    for (int p = 0; p < nslices; ++p)
-        for (int q = 0; p + q < nslices; ++q) {
+    for (int d = 0; d < A.S; ++d)      // pairs in order of decreasing size:
+        for (int p = 0; p <= d; ++p) { // (0,0) first, it owns the "hi" accumulator
             a.pa[np] = p;
-            a.pb[np] = q;
+            a.pb[np] = d - p;
             ++np;
         }
     a.npairs = np;
-    dim3 g((unsigned)ceil_div(M, TC_BM), (unsigned)ceil_div(N, TC_BN));
-    tc_gemm_kernel<<<g, 192, TC_SMEM, s>>>(ma, mb, a);
+    const int64_t ntiles = (int64_t)a.tiles_m * a.tiles_n;
+    const int sms = num_sms();
+    const int grid = (int)(ntiles < sms ? ntiles : (sms > 0 ? sms : 148));
+    tc_gemm_kernel<<<grid, 192, TC_SMEM, s>>>(ma, mb, a);
     GP_LAUNCH_CHECK();
     return GP_OK;
 }

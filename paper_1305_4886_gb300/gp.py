@@ -30,6 +30,9 @@ SYMBOLS = [
     "gp_backsolve",
     "gp_mult_chol",
     "gp_loglik",
+    "gp_loglik_grad",
+    "gp_syrk_workspace_bytes",
+    "gp_syrk_lower",
 ]
 
 
@@ -92,7 +95,12 @@ def lib():
             L.gp_backsolve.argtypes = [p, i64, i64, ci, p, p, p]
             L.gp_mult_chol.argtypes = [p, i64, i64, p, p, p]
             L.gp_loglik.argtypes = [p, p, p, i64, PP, ci, p, sz, p, p, p, p]
-            for name in ["gp_cov_fill", "gp_chol", "gp_backsolve", "gp_mult_chol", "gp_loglik"]:
+            L.gp_loglik_grad.argtypes = [p, p, p, i64, PP, ci, p, sz, p, p, p, p, p]
+            L.gp_syrk_workspace_bytes.argtypes = [i64, i64, ci]
+            L.gp_syrk_workspace_bytes.restype = sz
+            L.gp_syrk_lower.argtypes = [p, i64, p, i64, i64, i64, ci, p, sz, p, p]
+            for name in ["gp_cov_fill", "gp_chol", "gp_backsolve", "gp_mult_chol", "gp_loglik",
+                         "gp_loglik_grad", "gp_syrk_lower"]:
                 getattr(L, name).restype = ci
             _lib = L
     return _lib
@@ -185,6 +193,24 @@ def gp_loglik(x, y, mu, n, prm, precision, ws, out, alpha, info, stream=None):
            "gp_loglik")
 
 
+def gp_loglik_grad(x, y, mu, n, prm, precision, ws, out, alpha, grad, info, stream=None):
+    wsb = ws.numel() * ws.element_size()
+    _check(lib().gp_loglik_grad(_f64(x), _f64(y), _f64(mu), int(n), ctypes.byref(prm),
+                                _prec(precision), _ptr(ws), wsb, _f64(out), _f64(alpha),
+                                _f64(grad), _ptr(info), _stream(stream)), "gp_loglik_grad")
+
+
+def gp_syrk_workspace_bytes(m, k, precision="mixed_bf16"):
+    return lib().gp_syrk_workspace_bytes(int(m), int(k), _prec(precision))
+
+
+def gp_syrk_lower(C, ldc, P, ldp, m, k, precision, ws, info=None, stream=None):
+    wsb = 0 if ws is None else ws.numel() * ws.element_size()
+    _check(lib().gp_syrk_lower(_f64(C), int(ldc), _f64(P), int(ldp), int(m), int(k),
+                               _prec(precision), _ptr(ws), wsb, _ptr(info), _stream(stream)),
+           "gp_syrk_lower")
+
+
 # ---------------------------------------------------------------------------
 # convenience wrappers that allocate with torch (device memory only)
 # ---------------------------------------------------------------------------
@@ -224,3 +250,29 @@ def loglik(x, y, kernel, sigma2, rho, tau2, mu=None, precision="fp64", ws=None,
         if iv != 0:
             raise GpDeviceError(iv)
     return dict(out=out, alpha=alpha, info=info, ws=ws)
+
+
+def loglik_grad(x, y, kernel, sigma2, rho, tau2, mu=None, precision="fp64", ws=None,
+                want_alpha=True, check=True):
+    """Log-likelihood and gradient on the device; returns dict of device tensors
+    {out: [loglik, logdet, q, resid], grad: d/d(log s2, log rho, log tau2),
+    alpha, info}."""
+    n = x.shape[0]
+    dev = x.device
+    if ws is None:
+        ws = workspace(n, precision, True, dev)
+    out = torch.empty(4, dtype=torch.float64, device=dev)
+    grad = torch.empty(3, dtype=torch.float64, device=dev)
+    alpha = torch.empty(n, dtype=torch.float64, device=dev) if want_alpha else None
+    info = torch.zeros(1, dtype=torch.int64, device=dev)
+    mu_t = None
+    if mu is not None:
+        mu_t = mu if torch.is_tensor(mu) else torch.full((n,), float(mu), dtype=torch.float64,
+                                                         device=dev)
+    gp_loglik_grad(x, y, mu_t, n, params(kernel, sigma2, rho, tau2), precision, ws, out, alpha,
+                   grad, info)
+    if check:
+        iv = int(info.item())
+        if iv != 0:
+            raise GpDeviceError(iv)
+    return dict(out=out, grad=grad, alpha=alpha, info=info, ws=ws)
