@@ -1,0 +1,377 @@
+#!/usr/bin/env python3
+"""Benchmark of the GP marginal log-likelihood + gradient on GB300.
+
+One step = one evaluation of loglik and d loglik / d(log s2, log rho, log tau2)
+through the C ABI (gp_loglik_grad): covariance fill, blocked Cholesky,
+solves with refinement, reductions, blocked inverse and the gradient
+contraction.  Default workload: the paper-scale problem n = 67,275 (the size
+of the Sec. 4 supernova data set), Matern 3/2 with sigma2 = 1, rho = 0.02,
+tau2 = 0.1 on 50 Gaussian clusters (sd 0.02) plus 20% uniform background,
+y = L z, in the mixed form (BF16-slice tcgen05 contractions, FP64 pivots,
+log-determinant and residuals).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+With N > 1 (torchrun, one rank per GPU) every rank evaluates its own
+replica: the single large problem does not shard (replicas only), so the
+whole-job value is N x K evaluations over the slowest rank's time.
+
+--impl reference times the FP64 CPU oracle (the plain implementation the
+parity tests use) on the host cores, on a bounded sample of the same
+workload, and prints the same JSON line with "impl": "reference".
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_HEADLINE = 67275
+METRIC = "GP loglik+grad evaluations/s at n=67,275"
+UNIT = "evals/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=N_HEADLINE, help="problem size (exploration only)")
+    ap.add_argument("--precision", default="mixed_bf16", choices=["mixed_bf16", "fp64"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0,
+                    help="seconds of oracle work for the CPU baseline sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_config(n, precision):
+    return {
+        "workload": f"GP loglik+grad, Matern 3/2, n={n}, 2-D clustered locations "
+                    "(50 clusters sd 0.02 + 20% uniform), sigma2=1 rho=0.02 tau2=0.1, y=Lz",
+        "n": n,
+        "kernel": "matern32",
+        "precision": precision,
+        "seed": 48863,
+        "l2": "inputs larger than L2 (n_p^2 FP64 matrix, no flush needed)",
+    }
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled with nvidia-smi during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, \
+            "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+def oracle_sample(n_target, budget_s, p_full=None):
+    """Times the oracle's loglik+grad on a size whose cost fits the budget and
+    extrapolates to n_target by the n^3 cost.  Returns (evals/s at n_target,
+    description, threads, seconds)."""
+    import oracle
+    from paper_1305_4886_gb300 import inputs
+    oracle.build()
+    threads = oracle.num_threads()
+
+    def run(n):
+        p = inputs.config3(n)
+        t0 = time.perf_counter()
+        oracle.loglik_grad(p.x, p.z, p.kernel, p.s2, p.rho, p.tau2)
+        return time.perf_counter() - t0
+
+    n0 = 384
+    t0 = run(n0)
+    n_s = int(n0 * (budget_s / max(t0, 1e-3)) ** (1.0 / 3.0))
+    n_s = max(n0, min(n_s, 6144, n_target))
+    t_s = run(n_s)
+    t_full = t_s * (n_target / n_s) ** 3
+    desc = (f"oracle loglik+grad on the same recipe at n={n_s} ({t_s:.1f} s, {threads} threads), "
+            f"extrapolated to n={n_target} by n^3")
+    return 1.0 / t_full, desc, threads, t_s, n_s
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1305_4886_gb300 import inputs
+    oracle.build()
+    threads = oracle.num_threads()
+    # one step = one oracle loglik+grad on a bounded sample of the workload
+    budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    p0 = inputs.config3(384)
+    t0 = time.perf_counter()
+    oracle.loglik_grad(p0.x, p0.z, p0.kernel, p0.s2, p0.rho, p0.tau2)
+    t0 = time.perf_counter() - t0
+    n_s = max(384, min(4096, int(384 * (budget / max(t0, 1e-3)) ** (1.0 / 3.0))))
+    p = inputs.config3(n_s)
+    for _ in range(args.warmup):
+        oracle.loglik_grad(p.x, p.z, p.kernel, p.s2, p.rho, p.tau2)
+    ts = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        oracle.loglik_grad(p.x, p.z, p.kernel, p.s2, p.rho, p.tau2)
+        ts.append(time.perf_counter() - t)
+    t_step = sum(ts) / len(ts)
+    t_full = t_step * (args.n / n_s) ** 3
+    value = 1.0 / t_full
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_full * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(args.n, "fp64 (CPU oracle)"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"each step: oracle loglik+grad at n={n_s} "
+                                   f"({t_step:.2f} s), extrapolated to n={args.n} by n^3"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    from paper_1305_4886_gb300 import gp, inputs
+
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    gp.lib()
+
+    n = args.n
+    prec = args.precision
+    p = inputs.config3(n)
+    prm = gp.params(p.kernel, p.s2, p.rho, p.tau2)
+    np_ = gp.gp_padded_order(n)
+    x = torch.as_tensor(p.x, device="cuda")
+    z = torch.as_tensor(p.z, device="cuda")
+    ws = gp.workspace(n, prec, want_grad=True)
+    out = torch.empty(4, dtype=torch.float64, device="cuda")
+    grad = torch.empty(3, dtype=torch.float64, device="cuda")
+    alpha = torch.empty(n, dtype=torch.float64, device="cuda")
+    info = torch.zeros(1, dtype=torch.int64, device="cuda")
+
+    # y = L z with this library's factor of C(theta) (untimed set-up)
+    gp.gp_loglik(x, z, None, n, prm, prec, ws, out, None, info)
+    y = torch.empty(n, dtype=torch.float64, device="cuda")
+    gp.gp_mult_chol(ws[: np_ * np_ * 8].view(torch.float64), n, np_, z, y)
+    torch.cuda.synchronize()
+    if int(info.item()) != 0:
+        raise RuntimeError(f"set-up factorisation failed, info={int(info.item())}")
+
+    def step():
+        gp.gp_loglik_grad(x, y, None, n, prm, prec, ws, out, alpha, grad, info)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if int(info.item()) != 0:
+        raise RuntimeError(f"warm-up failed, info={int(info.item())}")
+
+    # ---- timed region: inputs resident in HBM ----
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    gp.gp_prof_enable(True)
+    launches0 = gp.gp_launch_count()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = gp.gp_launch_count() - launches0
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    elapsed_ms = e0.elapsed_time(e1)
+    prof = {c: gp.gp_prof_read(c) for c in ["contract", "fill", "residual", "grad"]}
+    gp.gp_prof_enable(False)
+    if int(info.item()) != 0:
+        raise RuntimeError(f"timed steps failed, info={int(info.item())}")
+    t_max = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    elapsed_ms = float(t_max.item())
+    value = world * args.steps / (elapsed_ms / 1e3)
+    res = out.cpu().numpy()
+    g_res = grad.cpu().numpy()
+
+    # ---- end to end through the public API: host buffers in, scalars out ----
+    e2e = None
+    if not args.no_e2e:
+        x_h = torch.as_tensor(p.x).pin_memory()
+        y_h = y.cpu().pin_memory()
+        out_h = torch.empty(4, dtype=torch.float64).pin_memory()
+        grad_h = torch.empty(3, dtype=torch.float64).pin_memory()
+        x_d = torch.empty_like(x)
+        y_d = torch.empty_like(y)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            x_d.copy_(x_h, non_blocking=True)
+            y_d.copy_(y_h, non_blocking=True)
+            gp.gp_loglik_grad(x_d, y_d, None, n, prm, prec, ws, out, alpha, grad, info)
+            out_h.copy_(out, non_blocking=True)
+            grad_h.copy_(grad, non_blocking=True)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = f0.elapsed_time(f1)
+        tm = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+        if dist:
+            dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * args.steps / (float(tm.item()) / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(x_h.numel() * 8 + y_h.numel() * 8),
+               "d2h_bytes_per_step": int((out_h.numel() + grad_h.numel()) * 8)}
+
+    peaks, peak_src = measured_peaks()
+    ms_c, cnt_c, fl_c, _ = prof["contract"]
+    achieved = fl_c / (ms_c / 1e3) / 1e12 if ms_c > 0 else None
+    peak_tf = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+    roofline = {
+        "kernel": "tc_gemm_kernel (tcgen05 BF16-slice contraction: Cholesky update, "
+                  "panel solve, TRTRI/LAUUM)",
+        "bound": "tensor", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
+        "frac": (achieved / peak_tf) if achieved else None, "traffic": None,
+        "peak_source": f"bf16 sustained, {peak_src}", "launches": cnt_c,
+        "share_of_step": ms_c / elapsed_ms if elapsed_ms > 0 else None,
+        "flops_counted": "slice-product flops (6 BF16 products per FP64 product) over the "
+                         "useful output entries and K ranges",
+    }
+    ms_f, cnt_f, _, by_f = prof["fill"]
+    fill = {"achieved_gbs": (by_f / (ms_f / 1e3) / 1e9) if ms_f > 0 else None,
+            "peak_gbs": peaks.get("hbm_gbs"), "ms_per_launch": ms_f / max(cnt_f, 1),
+            "bound": "fp64 alu (exp)"}
+    fill["frac_of_hbm"] = (fill["achieved_gbs"] / fill["peak_gbs"]) if fill["achieved_gbs"] else None
+    chol_alg = n ** 3 / 3.0
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 + bf16 slices (fp32 accumulate)" if prec == "mixed_bf16" else "f64",
+        "data": "synthetic", "config": workload_config(n, prec), "clocks": clk,
+        "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "fill": fill,
+        "result": {"loglik": float(res[0]), "logdet": float(res[1]), "quad": float(res[2]),
+                   "refine_resid": float(res[3]), "grad": [float(v) for v in g_res]},
+        "loglik_grad_alg_tflops": n ** 3 / (elapsed_ms / args.steps / 1e3) / 1e12,
+        "per_step_ms": {c: prof[c][0] / args.steps for c in prof},
+        "cholesky_alg_flop": chol_alg,
+        "parallelism": "replicas" if world > 1 else "single GPU",
+    }
+
+    if rank == 0 and not args.no_cpu_baseline:
+        v, desc, thr, _, _ = oracle_sample(n, args.cpu_budget)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
+                                "sample": desc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

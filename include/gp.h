@@ -162,6 +162,31 @@ size_t gp_syrk_workspace_bytes(int64_t m, int64_t k, int precision);
 int gp_syrk_lower(double *d_C, int64_t ldc, const double *d_P, int64_t ldp, int64_t m, int64_t k,
                   int precision, void *d_ws, size_t ws_bytes, int64_t *d_info, void *stream);
 
+/* ---- measurement aid ------------------------------------------------ */
+
+/* Number of kernels this library has launched in this process so far. */
+int64_t gp_launch_count(void);
+
+/* Kernel classes timed by the optional profiler. */
+#define GP_PROF_CONTRACT 0 /* tcgen05 BF16-slice contraction (Cholesky update,
+                              panel solve, inverse); flops = slice products */
+#define GP_PROF_FILL 1     /* covariance fill; bytes = lower-triangle FP64 */
+#define GP_PROF_RESIDUAL 2 /* matrix-free refinement residual */
+#define GP_PROF_GRAD 3     /* gradient contraction; bytes = lower-triangle FP64 */
+
+/* gp_prof_enable(1) clears the counters and brackets each later launch of
+ * the classes above with a pair of CUDA events recorded on the launch's own
+ * stream (host-side only: no device allocation, no synchronisation);
+ * gp_prof_enable(0) stops recording.  Not for concurrent use from several
+ * host threads.  Returns GP_ERR_CUDA if events cannot be created.        */
+int gp_prof_enable(int on);
+
+/* Sums for one class over the launches recorded since gp_prof_enable(1):
+ * total event time (ms), launch count, algorithmic flops and bytes.  Waits
+ * for the recorded events.  Returns GP_ERR_WORKSPACE if launches were
+ * dropped because the event pool (16384 launches) was full.               */
+int gp_prof_read(int cls, double *ms_total, int64_t *launches, double *flops, double *bytes);
+
 #ifdef __cplusplus
 }
 #endif

@@ -301,9 +301,11 @@ int grad_contract(const double *d_x, int64_t n, int64_t np, const KernParams &kp
                   const int64_t *info, cudaStream_t s) {
     GradWs w = grad_layout(ws, np, precision, S);
     const int64_t nt = ntiles64(np);
+    const int ev = prof_start(s);
     grad_contract_kernel<<<(unsigned)nt, 256, 0, s>>>(reinterpret_cast<const double2 *>(d_x), n, kp,
                                                        W, ld, alpha, w.part, info);
     GP_LAUNCH_CHECK();
+    prof_stop(ev, s, GP_PROF_GRAD, 0.0, 8.0 * (double)np * (double)(np + 1) / 2.0);
     grad_reduce_kernel<<<1, 1024, 0, s>>>(w.part, nt, grad, info);
     GP_LAUNCH_CHECK();
     return GP_OK;

@@ -6,7 +6,12 @@
 #include "internal.h"
 #include "kern.cuh"
 
+#include <atomic>
+
 namespace gp {
+
+static std::atomic<int64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 struct Carve {
     char *base;
@@ -117,6 +122,8 @@ using namespace gp;
 extern "C" {
 
 int gp_abi_version(void) { return GP_ABI_VERSION; }
+
+int64_t gp_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 const char *gp_status_string(int status) {
     switch (status) {

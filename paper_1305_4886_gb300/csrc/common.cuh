@@ -35,8 +35,14 @@ __device__ __forceinline__ void lower_tile_coords(int64_t t, int64_t &ti, int64_
 
 }  // namespace gp
 
+namespace gp {
+void count_launch();  // api.cu: tally of this library's kernel launches
+}
+
+// Every kernel launch in libgp is followed by this check, which also counts it.
 #define GP_LAUNCH_CHECK()                                   \
     do {                                                    \
+        gp::count_launch();                                 \
         cudaError_t e_ = cudaGetLastError();                \
         if (e_ != cudaSuccess) return GP_ERR_CUDA;          \
     } while (0)

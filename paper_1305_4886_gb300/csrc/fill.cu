@@ -57,9 +57,11 @@ int launch_cov_fill(const double *d_x, int64_t n, int64_t np, const KernParams &
     const int64_t T = np / TB;
     const int64_t ntiles = T * (T + 1) / 2;
     if (ntiles > 0x7fffffffLL) return GP_ERR_INVALID;
+    const int ev = prof_start(s);
     cov_fill_kernel<<<(unsigned)ntiles, 256, 0, s>>>(reinterpret_cast<const double2 *>(d_x), n, T,
                                                      kp, d_C, ldc, d_info);
     GP_LAUNCH_CHECK();
+    prof_stop(ev, s, GP_PROF_FILL, 0.0, 8.0 * (double)np * (double)(np + 1) / 2.0);
     return GP_OK;
 }
 

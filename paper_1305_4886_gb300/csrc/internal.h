@@ -7,6 +7,10 @@ namespace gp {
 
 struct KernParams;
 
+// prof.cu (event timing of selected launches; no-ops unless enabled)
+int prof_start(cudaStream_t s);
+void prof_stop(int idx, cudaStream_t s, int cls, double flops, double bytes);
+
 // fill.cu
 int launch_cov_fill(const double *d_x, int64_t n, int64_t np, const KernParams &kp, double *d_C,
                     int64_t ldc, int64_t *d_info, cudaStream_t s);

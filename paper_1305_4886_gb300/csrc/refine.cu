@@ -115,9 +115,11 @@ int cov_matvec(const double *d_x, int64_t n, int64_t np, const KernParams &kp, c
                double *acc, const int *skip, const int64_t *info, cudaStream_t s) {
     if (cudaMemsetAsync(acc, 0, sizeof(double) * n, s) != cudaSuccess) return GP_ERR_CUDA;
     const int64_t T = np / TB;
+    const int ev = prof_start(s);
     cov_matvec_kernel<<<(unsigned)(T * (T + 1) / 2), 256, 0, s>>>(
         reinterpret_cast<const double2 *>(d_x), n, kp, a, acc, skip, info);
     GP_LAUNCH_CHECK();
+    prof_stop(ev, s, GP_PROF_RESIDUAL, 0.0, 0.0);
     return GP_OK;
 }
 

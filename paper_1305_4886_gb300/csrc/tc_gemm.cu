@@ -520,8 +520,24 @@ int tc_gemm(const TcOperand &A, const TcOperand &B, int64_t M, int64_t N, int64_
     const int64_t ntiles = (int64_t)a.tiles_m * a.tiles_n;
     const int sms = num_sms();
     const int grid = (int)(ntiles < sms ? ntiles : (sms > 0 ? sms : 148));
+    const int ev = prof_start(s);
     tc_gemm_kernel<<<grid, 192, TC_SMEM, s>>>(ma, mb, a);
     GP_LAUNCH_CHECK();
+    if (ev >= 0) {
+        // slice-product flops over the useful output entries and K ranges
+        double useful = 0.0;
+        for (int64_t c = 0; c < N; ++c) {
+            int64_t rows = M;
+            if (out.lower) {
+                const int64_t r_lo = c - out.diag_off;  // first row written in column c
+                rows = r_lo <= 0 ? M : (r_lo >= M ? 0 : M - r_lo);
+            }
+            int64_t keff = K;
+            if (tri_k && c - tri_off > 0) keff = K - (c - tri_off) > 0 ? K - (c - tri_off) : 0;
+            useful += (double)rows * (double)keff;
+        }
+        prof_stop(ev, s, GP_PROF_CONTRACT, 2.0 * np * useful, 0.0);
+    }
     return GP_OK;
 }
 

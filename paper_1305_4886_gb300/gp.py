@@ -33,6 +33,9 @@ SYMBOLS = [
     "gp_loglik_grad",
     "gp_syrk_workspace_bytes",
     "gp_syrk_lower",
+    "gp_launch_count",
+    "gp_prof_enable",
+    "gp_prof_read",
 ]
 
 
@@ -99,8 +102,14 @@ def lib():
             L.gp_syrk_workspace_bytes.argtypes = [i64, i64, ci]
             L.gp_syrk_workspace_bytes.restype = sz
             L.gp_syrk_lower.argtypes = [p, i64, p, i64, i64, i64, ci, p, sz, p, p]
+            L.gp_launch_count.restype = i64
+            L.gp_prof_enable.argtypes = [ci]
+            L.gp_prof_read.argtypes = [ci, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double)]
             for name in ["gp_cov_fill", "gp_chol", "gp_backsolve", "gp_mult_chol", "gp_loglik",
-                         "gp_loglik_grad", "gp_syrk_lower"]:
+                         "gp_loglik_grad", "gp_syrk_lower", "gp_prof_enable", "gp_prof_read"]:
                 getattr(L, name).restype = ci
             _lib = L
     return _lib
@@ -209,6 +218,29 @@ def gp_syrk_lower(C, ldc, P, ldp, m, k, precision, ws, info=None, stream=None):
     _check(lib().gp_syrk_lower(_f64(C), int(ldc), _f64(P), int(ldp), int(m), int(k),
                                _prec(precision), _ptr(ws), wsb, _ptr(info), _stream(stream)),
            "gp_syrk_lower")
+
+
+PROF_CLASSES = {"contract": 0, "fill": 1, "residual": 2, "grad": 3}
+
+
+def gp_launch_count():
+    return lib().gp_launch_count()
+
+
+def gp_prof_enable(on):
+    _check(lib().gp_prof_enable(int(bool(on))), "gp_prof_enable")
+
+
+def gp_prof_read(cls):
+    """(total ms, launches, flops, bytes) of one profiled kernel class."""
+    c = PROF_CLASSES[cls] if isinstance(cls, str) else int(cls)
+    ms, fl, by = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    cnt = ctypes.c_int64()
+    st = lib().gp_prof_read(c, ctypes.byref(ms), ctypes.byref(cnt), ctypes.byref(fl),
+                            ctypes.byref(by))
+    if st not in (GP_OK, GP_ERR_WORKSPACE):
+        raise GpError(st, "gp_prof_read")
+    return ms.value, cnt.value, fl.value, by.value
 
 
 # ---------------------------------------------------------------------------
