@@ -275,7 +275,7 @@ def run_ours(args, rank, world, local):
     if dist:
         dist.barrier()
     elapsed_ms = e0.elapsed_time(e1)
-    prof = {c: gp.gp_prof_read(c) for c in ["contract", "fill", "residual", "grad"]}
+    prof = {c: gp.gp_prof_read(c) for c in gp.PROF_CLASSES}
     gp.gp_prof_enable(False)
     if int(info.item()) != 0:
         raise RuntimeError(f"timed steps failed, info={int(info.item())}")
@@ -345,7 +345,8 @@ def run_ours(args, rank, world, local):
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64 + bf16 slices (fp32 accumulate)" if prec == "mixed_bf16" else "f64",
         "data": "synthetic", "config": workload_config(n, prec), "clocks": clk,
-        "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "fill": fill,
+        "e2e": e2e, "gpu_launches": int(launches), "launches_before_timed": int(launches0),
+        "roofline": roofline, "fill": fill,
         "result": {"loglik": float(res[0]), "logdet": float(res[1]), "quad": float(res[2]),
                    "refine_resid": float(res[3]), "grad": [float(v) for v in g_res]},
         "loglik_grad_alg_tflops": n ** 3 / (elapsed_ms / args.steps / 1e3) / 1e12,

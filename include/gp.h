@@ -173,6 +173,12 @@ int64_t gp_launch_count(void);
 #define GP_PROF_FILL 1     /* covariance fill; bytes = lower-triangle FP64 */
 #define GP_PROF_RESIDUAL 2 /* matrix-free refinement residual */
 #define GP_PROF_GRAD 3     /* gradient contraction; bytes = lower-triangle FP64 */
+#define GP_PROF_DIAG 4     /* FP64 tiled Cholesky of a diagonal block (or of the
+                              whole matrix in GP_FP64); flops = nb^3/3 */
+#define GP_PROF_DIAGINV 5  /* FP64 inverse of a diagonal block; flops = nb^3/3 */
+#define GP_PROF_SOLVE 6    /* triangular solves; bytes = 8 per lower entry read */
+#define GP_PROF_PACK 7     /* FP64 -> BF16 slice packing */
+#define GP_PROF_FOLD 8     /* FP32 pending-update fold into the FP64 block column */
 
 /* gp_prof_enable(1) clears the counters and brackets each later launch of
  * the classes above with a pair of CUDA events recorded on the launch's own

@@ -72,9 +72,11 @@ static int pack(const Store &st, const double *src, int64_t ld, int64_t R, int64
     if (st.f64) {
         double *dst = static_cast<double *>(st.p) + row_off * st.kld + k_off;
         dim3 g((unsigned)ceil_div(K, 32), (unsigned)ceil_div(R, 32));
+        const int ev = prof_start(s);
         pack_f64_kernel<<<g, 256, 0, s>>>(src, ld, R, K, Kvalid, trans, diag_off, lower_mask, dst,
                                           st.kld);
         GP_LAUNCH_CHECK();
+        prof_stop(ev, s, GP_PROF_PACK, 0.0, 16.0 * (double)R * K);
         return GP_OK;
     }
     return split_rows(src, ld, R, K, Kvalid, trans, diag_off, lower_mask, st.S,
@@ -90,7 +92,7 @@ static int contract(const Store &A, int64_t a_row, int64_t a_k, const Store &B, 
     if (A.f64) {
         const double *a = static_cast<const double *>(A.p) + a_row * A.kld + a_k;
         const double *b = static_cast<const double *>(B.p) + b_row * B.kld + b_k;
-        F64Mask m{lower, diag_off, tri_k, tri_off};
+        F64Mask m{lower, diag_off, tri_k, tri_off, 0};
         return gemm_f64_ex(M, N, K, alpha, a, A.kld, 1, b, B.kld, 0, beta, C, ldc, 0, m, info, s);
     }
     TcOperand ta{static_cast<const __nv_bfloat16 *>(A.p), A.rows, A.kld, A.S, a_row, a_k};
@@ -163,7 +165,9 @@ static int trtri_inplace(double *A, int64_t ld, int64_t np, GradWs &w, int64_t *
     for (int64_t k0 = 0; k0 < np; k0 += GNB) {
         const int64_t nb = (np - k0) < GNB ? (np - k0) : GNB;
         double *Akk = A + k0 + k0 * ld;
+        const int ev = prof_start(s);
         GP_TRY(trtri_fp64_blocked(Akk, ld, nb, w.Wd, nb, w.tmp, info, s));
+        prof_stop(ev, s, GP_PROF_DIAGINV, (double)nb * nb * nb / 3.0, 0.0);
         if (k0 > 0) {
             // T (nb x k0) = L[k, 0:k0] X[0:k0, 0:k0]
             GP_TRY(pack(w.SArow, A + k0, ld, nb, k0, k0, 0, 0, 0, 0, 0, s));

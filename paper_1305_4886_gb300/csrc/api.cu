@@ -56,6 +56,7 @@ struct LoglikWs {
     double *s = nullptr;      // refinement residual / correction (n_p)
     double *stats = nullptr;  // [0] refinement residual ratio
     int *conv = nullptr;      // refinement converged flag
+    int *tsync = nullptr;     // ticket + flags of the single-launch solves
     void *chol = nullptr;
     size_t bytes = 0;
 };
@@ -71,6 +72,7 @@ static LoglikWs loglik_ws_layout(void *base, int64_t n, int precision, int want_
     w.s = c.take<double>((size_t)np);
     w.stats = c.take<double>(4);
     w.conv = c.take<int>(4);
+    w.tsync = c.take<int>(trsv_sync_ints(np));
     size_t cb = chol_ws_bytes(np, precision);
     if (want_grad) {  // the inverse and contraction reuse the factorisation's scratch
         size_t gb = grad_ws_bytes(np, precision, MIXED_SLICES);
@@ -83,7 +85,12 @@ static LoglikWs loglik_ws_layout(void *base, int64_t n, int precision, int want_
 
 static int run_chol(double *A, int64_t np, int64_t ld, int precision, void *ws, int64_t *info,
                     cudaStream_t s) {
-    if (precision == GP_FP64) return chol_fp64_tiled(A, ld, np, 0, info, s);
+    if (precision == GP_FP64) {
+        const int ev = prof_start(s);
+        GP_TRY(chol_fp64_tiled(A, ld, np, 0, info, s));
+        prof_stop(ev, s, GP_PROF_DIAG, (double)np * np * np / 3.0, 0.0);
+        return GP_OK;
+    }
     if (precision == GP_MIXED_BF16) return chol_mixed(A, ld, np, MIXED_SLICES, ws, info, s);
     return GP_ERR_INVALID;
 }
@@ -99,17 +106,17 @@ static int loglik_core(const double *d_x, const double *d_y, const double *d_mu,
     GP_TRY(launch_residual(d_y, d_mu, n, np, w.r, d_info, s));
     if (cudaMemcpyAsync(w.v, w.r, sizeof(double) * np, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return GP_ERR_CUDA;
-    GP_TRY(trsv_blocked(w.A, np, n, 0, w.v, d_info, s));
+    GP_TRY(trsv_persist(w.A, np, n, 0, w.v, w.tsync, d_info, nullptr, s));
     if (precision == GP_FP64) {
         // q = v^T v with v = L^{-1} r (Sec. 2.2.2); then alpha = L^{-T} v
         GP_TRY(launch_loglik_reduce(w.A, np, n, w.v, w.v, nullptr, d_out, d_info, s));
-        GP_TRY(trsv_blocked(w.A, np, n, 1, w.v, d_info, s));
+        GP_TRY(trsv_persist(w.A, np, n, 1, w.v, w.tsync, d_info, nullptr, s));
         return GP_OK;
     }
     // mixed: alpha from the low-precision factor, refined against the FP64
     // matrix-free residual; q = r^T alpha with the refined alpha
-    GP_TRY(trsv_blocked(w.A, np, n, 1, w.v, d_info, s));
-    GP_TRY(refine_alpha(d_x, n, np, kp, w.A, np, w.r, w.v, w.acc, w.s, w.stats, w.conv,
+    GP_TRY(trsv_persist(w.A, np, n, 1, w.v, w.tsync, d_info, nullptr, s));
+    GP_TRY(refine_alpha(d_x, n, np, kp, w.A, np, w.r, w.v, w.acc, w.s, w.stats, w.conv, w.tsync,
                         REFINE_EVALS, REFINE_TOL, d_info, s));
     GP_TRY(launch_loglik_reduce(w.A, np, n, w.r, w.v, w.stats, d_out, d_info, s));
     return GP_OK;

@@ -76,14 +76,20 @@ int chol_mixed(double *A, int64_t ld, int64_t np, int S, void *ws, int64_t *info
         const int64_t rows = np - k0;
         if (k0 > 0) {
             dim3 g((unsigned)ceil_div(rows, 256 * 4) + 1, (unsigned)nb);
+            const int ev = prof_start(s);
             fold_delta_kernel<<<g, 256, 0, s>>>(Akk, ld, w.D + k0 + k0 * np, np, rows, nb, info);
             GP_LAUNCH_CHECK();
+            prof_stop(ev, s, GP_PROF_FOLD, 0.0, 12.0 * (double)rows * nb);
         }
+        int ev = prof_start(s);
         GP_TRY(chol_fp64_tiled(Akk, ld, nb, k0, info, s));
+        prof_stop(ev, s, GP_PROF_DIAG, (double)nb * nb * nb / 3.0, 0.0);
         const int64_t m = np - k0 - nb;
         if (m <= 0) break;
         double *P = Akk + nb;  // m x nb panel below the diagonal block
+        ev = prof_start(s);
         GP_TRY(trtri_fp64_blocked(Akk, ld, nb, w.W, nb, w.tmp, info, s));
+        prof_stop(ev, s, GP_PROF_DIAGINV, (double)nb * nb * nb / 3.0, 0.0);
         GP_TRY(split_rows(w.W, nb, nb, nb, nb, 0, 0, 1, S, w.SB, NB, NB, 0, 0, s));
         GP_TRY(split_rows(P, ld, m, nb, nb, 0, 0, 0, S, w.SA, np, NB, 0, 0, s));
         TcOperand opA{w.SA, np, NB, S, 0, 0};

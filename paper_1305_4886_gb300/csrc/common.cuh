@@ -11,8 +11,8 @@ namespace gp {
 constexpr int TB = 64;        // FP64 CUDA-core tile (diagonal POTRF / TRSM / TRSV)
 constexpr int PAD = GP_PAD;   // padding granularity of n
 
-inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
-inline int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__host__ __device__ inline int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
 
 // The first device-side failure wins: d_info is only written while it is 0.
 __device__ __forceinline__ void set_info(int64_t *info, int64_t v) {

@@ -63,37 +63,49 @@ __global__ void __launch_bounds__(256) potrf_tile_kernel(double *A, int64_t ld, 
 }
 
 // ---------------------------------------------------------------------------
-// B <- B L^{-T} for the 64-row tiles below the diagonal tile L (the panel
-// forward-solve of Sec. 2.1).  B tile t starts at B0 + 64 t.
+// B <- B L^{-T} for the rows below the diagonal tile L (the panel
+// forward-solve of Sec. 2.1).  Each CTA solves 32 rows (rows r0 = 32 blockIdx
+// of B0) against the whole 64 x 64 triangle; the pivots' reciprocals are
+// formed once.
 // ---------------------------------------------------------------------------
+constexpr int TR_ROWS = 32;
+
 __global__ void __launch_bounds__(256) trsm_tiles_kernel(const double *L, double *B0, int64_t ld,
-                                                         const int64_t *info) {
+                                                         int64_t rows, const int64_t *info) {
     __shared__ double Ls[TB * (TB + 1)];
-    __shared__ double Bs[TB * (TB + 1)];
+    __shared__ double Bs[TB * (TR_ROWS + 1)];
+    __shared__ double rinv[TB];
     if (failed(info)) return;
     const int tid = threadIdx.x;
-    double *B = B0 + (int64_t)blockIdx.x * TB;
+    const int64_t r0 = (int64_t)blockIdx.x * TR_ROWS;
+    double *B = B0 + r0;
+    const int nr = (int)((rows - r0) < TR_ROWS ? (rows - r0) : TR_ROWS);
     for (int e = tid; e < TB * TB; e += blockDim.x) {
         int r = e & (TB - 1), c = e >> 6;
         Ls[c * (TB + 1) + r] = (r >= c) ? L[r + (int64_t)c * ld] : 0.0;
-        Bs[c * (TB + 1) + r] = B[r + (int64_t)c * ld];
     }
+    for (int e = tid; e < TB * TR_ROWS; e += blockDim.x) {
+        int r = e & (TR_ROWS - 1), c = e >> 5;
+        Bs[c * (TR_ROWS + 1) + r] = (r < nr) ? B[r + (int64_t)c * ld] : 0.0;
+    }
+    __syncthreads();
+    if (tid < TB) rinv[tid] = 1.0 / Ls[tid * (TB + 1) + tid];
     __syncthreads();
     // X L^T = B: column c of X = (B_c - sum_{l<c} X_l L_cl) / L_cc
     for (int c = 0; c < TB; ++c) {
-        if (tid < TB) Bs[c * (TB + 1) + tid] /= Ls[c * (TB + 1) + c];
+        if (tid < TR_ROWS) Bs[c * (TR_ROWS + 1) + tid] *= rinv[c];
         __syncthreads();
         const int w = TB - 1 - c;
-        for (int e = tid; e < w * TB; e += blockDim.x) {
-            int c2 = c + 1 + e / TB;
-            int r = e & (TB - 1);
-            Bs[c2 * (TB + 1) + r] -= Bs[c * (TB + 1) + r] * Ls[c * (TB + 1) + c2];
+        for (int e = tid; e < w * TR_ROWS; e += blockDim.x) {
+            int c2 = c + 1 + e / TR_ROWS;
+            int r = e & (TR_ROWS - 1);
+            Bs[c2 * (TR_ROWS + 1) + r] -= Bs[c * (TR_ROWS + 1) + r] * Ls[c * (TB + 1) + c2];
         }
         __syncthreads();
     }
-    for (int e = tid; e < TB * TB; e += blockDim.x) {
-        int r = e & (TB - 1), c = e >> 6;
-        B[r + (int64_t)c * ld] = Bs[c * (TB + 1) + r];
+    for (int e = tid; e < TB * TR_ROWS; e += blockDim.x) {
+        int r = e & (TR_ROWS - 1), c = e >> 5;
+        if (r < nr) B[r + (int64_t)c * ld] = Bs[c * (TR_ROWS + 1) + r];
     }
 }
 
@@ -238,10 +250,119 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(int64_t M, int64_t N, int
     }
 }
 
+// 32 x 32 output tiles, 64 threads (4 x 4 per thread): four times the CTAs of
+// the 64 x 64 kernel for the small, latency-bound updates of the diagonal
+// blocks.  mask.kchunk > 0 splits K into chunks over grid.z and adds each
+// partial product with FP64 atomics (C must already hold beta C).
+constexpr int SB = 32;
+
+__global__ void __launch_bounds__(64) gemm_f64_s32_kernel(int64_t M, int64_t N, int64_t K,
+                                                          double alpha,
+                                                          const double *__restrict__ A,
+                                                          int64_t lda, int opA,
+                                                          const double *__restrict__ B,
+                                                          int64_t ldb, int opB, double beta,
+                                                          double *C, int64_t ldc, F64Mask mask,
+                                                          const int64_t *info) {
+    __shared__ double As[GBK][SB + 1];
+    __shared__ double Bs[GBK][SB + 1];
+    if (info && failed(info)) return;
+    const int64_t r0 = (int64_t)blockIdx.x * SB, c0 = (int64_t)blockIdx.y * SB;
+    if (mask.out_lower && c0 > r0 + (SB - 1) + mask.diag_off) return;
+    int64_t kbeg = 0, kend = K;
+    if (mask.kchunk > 0) {
+        kbeg = (int64_t)blockIdx.z * mask.kchunk;
+        kend = min(K, kbeg + mask.kchunk);
+    }
+    if (mask.tri_k && c0 - mask.tri_off > kbeg) kbeg = ((c0 - mask.tri_off) / GBK) * GBK;
+    if (kbeg >= kend) return;
+    const int tid = threadIdx.x;
+    const int tx = tid & 7, ty = tid >> 3;
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    for (int64_t k0 = kbeg; k0 < kend; k0 += GBK) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int idx = tid + 64 * q;  // 0..511
+            int r, k, c, kb;
+            double v = 0.0, w = 0.0;
+            if (opA == 0) { r = idx & 31; k = idx >> 5; }
+            else { k = idx & 15; r = idx >> 4; }
+            {
+                const int64_t gr = r0 + r, gk = k0 + k;
+                if (gr < M && gk < kend) v = opA == 0 ? A[gr + gk * lda] : A[gk + gr * lda];
+            }
+            As[k][r] = v;
+            if (opB == 0) { kb = idx & 15; c = idx >> 4; }
+            else { c = idx & 31; kb = idx >> 5; }
+            {
+                const int64_t gc = c0 + c, gk = k0 + kb;
+                if (gc < N && gk < kend) w = opB == 0 ? B[gk + gc * ldb] : B[gc + gk * ldb];
+            }
+            Bs[kb][c] = w;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < GBK; ++k) {
+            double av[4], bv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) av[a] = As[k][tx + 8 * a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) bv[b] = Bs[k][ty + 8 * b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const int64_t gc = c0 + ty + 8 * b;
+        if (gc >= N) continue;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int64_t gr = r0 + tx + 8 * a;
+            if (gr >= M) continue;
+            if (mask.out_lower && gr + mask.diag_off < gc) continue;
+            double *p = C + gr + gc * ldc;
+            if (mask.kchunk > 0) {
+                atomicAdd(p, alpha * acc[a][b]);
+            } else {
+                double v = alpha * acc[a][b];
+                if (beta != 0.0) v = fma(beta, *p, v);
+                *p = v;
+            }
+        }
+    }
+}
+
 int gemm_f64_ex(int64_t M, int64_t N, int64_t K, double alpha, const double *A, int64_t lda,
                 int opA, const double *B, int64_t ldb, int opB, double beta, double *C, int64_t ldc,
                 int lower, const F64Mask &mask, const int64_t *info, cudaStream_t s) {
     if (M <= 0 || N <= 0) return GP_OK;
+    const int64_t tiles64 = lower ? ceil_div(M, TB) * (ceil_div(M, TB) + 1) / 2
+                                  : ceil_div(M, TB) * ceil_div(N, TB);
+    if (mask.kchunk > 0 || tiles64 < 256) {
+        // small launch: 32 x 32 tiles (a lower request masks the upper tiles)
+        F64Mask m = mask;
+        if (lower) {
+            m.out_lower = 1;
+            m.diag_off = 0;
+        }
+        if (m.kchunk > 0 && beta != 1.0) {
+            if (beta != 0.0) return GP_ERR_INVALID;  // split K accumulates into C
+        }
+        const int64_t kz = m.kchunk > 0 ? ceil_div(K, m.kchunk) : 1;
+        dim3 g((unsigned)ceil_div(M, SB), (unsigned)ceil_div(N, SB), (unsigned)kz);
+        gemm_f64_s32_kernel<<<g, 64, 0, s>>>(M, N, K, alpha, A, lda, opA, B, ldb, opB, beta, C, ldc,
+                                             m, info);
+        GP_LAUNCH_CHECK();
+        return GP_OK;
+    }
     if (lower) {
         if (M != N) return GP_ERR_INVALID;
         int64_t T = ceil_div(M, TB);
@@ -259,7 +380,7 @@ int gemm_f64_ex(int64_t M, int64_t N, int64_t K, double alpha, const double *A, 
 int gemm_f64(int64_t M, int64_t N, int64_t K, double alpha, const double *A, int64_t lda, int opA,
              const double *B, int64_t ldb, int opB, double beta, double *C, int64_t ldc, int lower,
              const int64_t *info, cudaStream_t s) {
-    F64Mask none{0, 0, 0, 0};
+    F64Mask none{0, 0, 0, 0, 0};
     return gemm_f64_ex(M, N, K, alpha, A, lda, opA, B, ldb, opB, beta, C, ldc, lower, none, info, s);
 }
 
@@ -279,7 +400,7 @@ int chol_fp64_tiled(double *A, int64_t ld, int64_t m, int64_t col_base, int64_t 
         const int64_t rest = m - k0 - TB;
         if (rest <= 0) continue;
         double *P = Akk + TB;  // rows below the diagonal tile
-        trsm_tiles_kernel<<<(unsigned)(rest / TB), 256, 0, s>>>(Akk, P, ld, info);
+        trsm_tiles_kernel<<<(unsigned)ceil_div(rest, TR_ROWS), 256, 0, s>>>(Akk, P, ld, rest, info);
         GP_LAUNCH_CHECK();
         double *C = P + TB * ld;  // trailing block
         GP_TRY(gemm_f64(rest, rest, TB, -1.0, P, ld, 0, P, ld, 1, 1.0, C, ld, 1, info, s));
@@ -302,8 +423,12 @@ int trtri_fp64_blocked(const double *L, int64_t ld_l, int64_t m, double *X, int6
     GP_LAUNCH_CHECK();
     for (int64_t i = 1; i < T; ++i) {
         const int64_t i0 = i * TB;
-        // tmp (64 x i0) = L[i0:i0+64, 0:i0] * X[0:i0, 0:i0]
-        GP_TRY(gemm_f64(TB, i0, i0, 1.0, L + i0, ld_l, 0, X, ld_x, 0, 0.0, tmp, TB, 0, info, s));
+        // tmp (64 x i0) = L[i0:i0+64, 0:i0] * X[0:i0, 0:i0]; X lower, so column
+        // block j needs K >= j only; K split in 64-chunks accumulated atomically
+        if (cudaMemsetAsync(tmp, 0, sizeof(double) * TB * i0, s) != cudaSuccess) return GP_ERR_CUDA;
+        F64Mask split{0, 0, 1, 0, TB};
+        GP_TRY(gemm_f64_ex(TB, i0, i0, 1.0, L + i0, ld_l, 0, X, ld_x, 0, 1.0, tmp, TB, 0, split,
+                           info, s));
         // X[i0:i0+64, 0:i0] = -X_ii * tmp
         GP_TRY(gemm_f64(TB, i0, TB, -1.0, X + i0 + i0 * ld_x, ld_x, 0, tmp, TB, 0, 0.0, X + i0,
                         ld_x, 0, info, s));

@@ -17,10 +17,11 @@ int launch_cov_fill(const double *d_x, int64_t n, int64_t np, const KernParams &
 
 // dense_f64.cu
 struct F64Mask {
-    int out_lower;
+    int out_lower;    // write only entries with row + diag_off >= col
     int64_t diag_off;
-    int tri_k;
+    int tri_k;        // op(B)(k, c) vanishes for k < c - tri_off
     int64_t tri_off;
+    int64_t kchunk;   // > 0: split K into chunks, accumulate into C with atomics
 };
 int gemm_f64_ex(int64_t M, int64_t N, int64_t K, double alpha, const double *A, int64_t lda,
                 int opA, const double *B, int64_t ldb, int opB, double beta, double *C, int64_t ldc,
@@ -45,6 +46,11 @@ int trsv_blocked_skip(const double *L, int64_t ld, int64_t n, int trans, double 
 int launch_loglik_reduce(const double *L, int64_t ld, int64_t n, const double *u, const double *v,
                          const double *resid, double *out, const int64_t *info, cudaStream_t s);
 
+// trsv_persist.cu (single-launch solves; sync holds trsv_sync_ints(n) ints)
+size_t trsv_sync_ints(int64_t n);
+int trsv_persist(const double *L, int64_t ld, int64_t n, int trans, double *b, int *sync,
+                 int64_t *info, const int *skip, cudaStream_t s);
+
 // chol_mixed.cu
 size_t chol_mixed_ws_bytes(int64_t np, int S);
 int chol_mixed(double *A, int64_t ld, int64_t np, int S, void *ws, int64_t *info, cudaStream_t s);
@@ -65,7 +71,7 @@ int cov_matvec(const double *d_x, int64_t n, int64_t np, const KernParams &kp, c
                double *acc, const int *skip, const int64_t *info, cudaStream_t s);
 int refine_alpha(const double *d_x, int64_t n, int64_t np, const KernParams &kp, const double *L,
                  int64_t ld, const double *r, double *alpha, double *acc, double *s,
-                 double *stats, int *conv, int max_evals, double tol, const int64_t *info,
+                 double *stats, int *conv, int *tsync, int max_evals, double tol, int64_t *info,
                  cudaStream_t st);
 
 }  // namespace gp

@@ -125,7 +125,7 @@ int cov_matvec(const double *d_x, int64_t n, int64_t np, const KernParams &kp, c
 
 int refine_alpha(const double *d_x, int64_t n, int64_t np, const KernParams &kp, const double *L,
                  int64_t ld, const double *r, double *alpha, double *acc, double *s,
-                 double *stats, int *conv, int max_evals, double tol, const int64_t *info,
+                 double *stats, int *conv, int *tsync, int max_evals, double tol, int64_t *info,
                  cudaStream_t st) {
     if (cudaMemsetAsync(conv, 0, sizeof(int), st) != cudaSuccess) return GP_ERR_CUDA;
     for (int it = 0; it < max_evals; ++it) {
@@ -133,8 +133,8 @@ int refine_alpha(const double *d_x, int64_t n, int64_t np, const KernParams &kp,
         refine_resid_kernel<<<1, 1024, 0, st>>>(r, acc, n, s, tol, stats, conv, info);
         GP_LAUNCH_CHECK();
         if (it + 1 == max_evals) break;  // the last evaluation only reports
-        GP_TRY(trsv_blocked_skip(L, ld, n, 0, s, info, conv, st));
-        GP_TRY(trsv_blocked_skip(L, ld, n, 1, s, info, conv, st));
+        GP_TRY(trsv_persist(L, ld, n, 0, s, tsync, info, conv, st));
+        GP_TRY(trsv_persist(L, ld, n, 1, s, tsync, info, conv, st));
         axpy_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(n, s, alpha, conv, info);
         GP_LAUNCH_CHECK();
     }

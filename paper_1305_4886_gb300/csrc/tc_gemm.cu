@@ -428,8 +428,10 @@ int split_rows(const double *src, int64_t ld, int64_t R, int64_t K, int64_t Kval
         return GP_ERR_INVALID;
     SplitArgs a{src, ld, R, K, Kvalid < K ? Kvalid : K, trans, diag_off, lower_mask, S, dst,
                 dst_rows, dst_kld, dst_row_off, dst_k_off};
+    const int ev = prof_start(s);
     split_rows_kernel<<<(unsigned)ceil_div(R, 32), 256, 0, s>>>(a);
     GP_LAUNCH_CHECK();
+    prof_stop(ev, s, GP_PROF_PACK, 0.0, (double)R * K * (8.0 + 2.0 * S));
     return GP_OK;
 }
 

@@ -220,7 +220,8 @@ def gp_syrk_lower(C, ldc, P, ldp, m, k, precision, ws, info=None, stream=None):
            "gp_syrk_lower")
 
 
-PROF_CLASSES = {"contract": 0, "fill": 1, "residual": 2, "grad": 3}
+PROF_CLASSES = {"contract": 0, "fill": 1, "residual": 2, "grad": 3, "diag_chol": 4,
+                "diag_inv": 5, "solve": 6, "pack": 7, "fold": 8}
 
 
 def gp_launch_count():
