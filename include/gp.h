@@ -55,7 +55,8 @@ typedef enum {
     GP_ERR_INVALID = 2,   /* bad argument (sizes, parameters, NULL pointers) */
     GP_ERR_CUDA = 3,      /* a CUDA launch or runtime call failed */
     GP_ERR_TIMEOUT = 4,   /* reserved: device-side detection goes to d_info */
-    GP_ERR_WORKSPACE = 5  /* workspace missing or smaller than required */
+    GP_ERR_WORKSPACE = 5, /* workspace missing or smaller than required */
+    GP_ERR_TOO_LARGE = 6  /* n above GP_NOALLOC_MAX_N for gp_loglik_noalloc */
 } gp_status;
 
 /* Covariance functions k(u), u = d / rho, d Euclidean distance (Sec. 1;
@@ -150,6 +151,31 @@ int gp_loglik(const double *d_x, const double *d_y, const double *d_mu, int64_t 
 int gp_loglik_grad(const double *d_x, const double *d_y, const double *d_mu, int64_t n,
                    const gp_params *prm, int precision, void *d_ws, size_t ws_bytes,
                    double *d_out, double *d_alpha, double *d_grad, int64_t *d_info, void *stream);
+
+/* Log-likelihood without any workspace or allocation (GP_FP64 only).  The
+ * paper has no counterpart: this entry point serves callers that cannot
+ * allocate device memory when they need a log-likelihood -- code running
+ * while a stream is being captured into a CUDA graph, real-time or embedded
+ * callers whose device memory is fixed at start-up, plug-ins inside an
+ * application that owns every device allocation.  Same arguments and
+ * results as gp_loglik with precision GP_FP64, minus the workspace; the
+ * caller still passes the inputs and outputs.
+ *
+ * Scratch: one static device array of GP_NOALLOC_SCRATCH_BYTES (about
+ * 2.1 MB) inside libgp, which every GPU that loads the library holds until
+ * the process exits.  n above GP_NOALLOC_MAX_N returns GP_ERR_TOO_LARGE
+ * before any device work.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress, with that device current);
+ * make that first call before any stream capture starts.  All calls on a
+ * device share the array, which keeps the last call's contents: calls whose
+ * work overlaps on the GPU (other streams, other host threads) race and
+ * must be serialised by the caller.  Each call rewrites every scratch entry
+ * it reads, so earlier calls do not affect its result.                     */
+#define GP_NOALLOC_MAX_N 512
+#define GP_NOALLOC_SCRATCH_BYTES 2105856
+int gp_loglik_noalloc(const double *d_x, const double *d_y, const double *d_mu, int64_t n,
+                      const gp_params *prm, double *d_out, double *d_alpha, int64_t *d_info,
+                      void *stream);
 
 /* One trailing update of the block Cholesky (Sec. 2.1, the matrix
  * multiplication and subtraction that carries most of the work), on its

@@ -140,6 +140,7 @@ const char *gp_status_string(int status) {
         case GP_ERR_CUDA: return "CUDA error";
         case GP_ERR_TIMEOUT: return "device wait timed out";
         case GP_ERR_WORKSPACE: return "workspace missing or too small";
+        case GP_ERR_TOO_LARGE: return "n exceeds the static scratch of gp_loglik_noalloc";
         default: return "unknown status";
     }
 }

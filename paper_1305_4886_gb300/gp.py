@@ -31,6 +31,7 @@ SYMBOLS = [
     "gp_mult_chol",
     "gp_loglik",
     "gp_loglik_grad",
+    "gp_loglik_noalloc",
     "gp_syrk_workspace_bytes",
     "gp_syrk_lower",
     "gp_launch_count",
@@ -99,6 +100,8 @@ def lib():
             L.gp_mult_chol.argtypes = [p, i64, i64, p, p, p]
             L.gp_loglik.argtypes = [p, p, p, i64, PP, ci, p, sz, p, p, p, p]
             L.gp_loglik_grad.argtypes = [p, p, p, i64, PP, ci, p, sz, p, p, p, p, p]
+            L.gp_loglik_noalloc.argtypes = [p, p, p, i64, PP, p, p, p, p]
+            L.gp_loglik_noalloc.restype = ci
             L.gp_syrk_workspace_bytes.argtypes = [i64, i64, ci]
             L.gp_syrk_workspace_bytes.restype = sz
             L.gp_syrk_lower.argtypes = [p, i64, p, i64, i64, i64, ci, p, sz, p, p]
@@ -200,6 +203,14 @@ def gp_loglik(x, y, mu, n, prm, precision, ws, out, alpha, info, stream=None):
     _check(lib().gp_loglik(_f64(x), _f64(y), _f64(mu), int(n), ctypes.byref(prm), _prec(precision),
                            _ptr(ws), wsb, _f64(out), _f64(alpha), _ptr(info), _stream(stream)),
            "gp_loglik")
+
+
+def gp_loglik_noalloc(x, y, mu, n, prm, out, alpha, info, stream=None):
+    """FP64 log-likelihood for n <= 512 with the library's static scratch: for
+    callers that cannot allocate device memory (see include/gp.h)."""
+    _check(lib().gp_loglik_noalloc(_f64(x), _f64(y), _f64(mu), int(n), ctypes.byref(prm),
+                                   _f64(out), _f64(alpha), _ptr(info), _stream(stream)),
+           "gp_loglik_noalloc")
 
 
 def gp_loglik_grad(x, y, mu, n, prm, precision, ws, out, alpha, grad, info, stream=None):
