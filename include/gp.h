@@ -152,6 +152,26 @@ int gp_loglik_grad(const double *d_x, const double *d_y, const double *d_mu, int
                    const gp_params *prm, int precision, void *d_ws, size_t ws_bytes,
                    double *d_out, double *d_alpha, double *d_grad, int64_t *d_info, void *stream);
 
+/* Batched log-likelihood + gradient of nprob independent problems of uneven
+ * n (independent data sets or a theta grid; the paper evaluates one
+ * problem per session, Sec. 2.3.4).  Host arrays, one entry per problem:
+ * h_n (sizes), h_dx / h_dy (device pointers to locations and data), h_dmu
+ * (NULL, or device pointers to means, each NULL = 0), h_prm (parameters).
+ * Device outputs: d_out (nprob x 4, as gp_loglik), d_grad (nprob x 3),
+ * d_info (nprob, per-problem status as d_info of gp_loglik).  d_ws:
+ * gp_batched_workspace_bytes; problem i owns a slice of it.
+ * The problems run on a pool of library streams (created on the first
+ * batched call on a device and kept for the process), largest first with a
+ * longest-processing-time assignment; the pool forks from `stream` and
+ * joins back to it with events, so every result is ordered after the call
+ * on `stream`, and a capture of `stream` records the whole batch as one
+ * CUDA graph (make the first call outside a capture).                      */
+size_t gp_batched_workspace_bytes(int nprob, const int64_t *h_n, int precision);
+int gp_loglik_grad_batched(int nprob, const int64_t *h_n, const double *const *h_dx,
+                           const double *const *h_dy, const double *const *h_dmu,
+                           const gp_params *h_prm, int precision, void *d_ws, size_t ws_bytes,
+                           double *d_out, double *d_grad, int64_t *d_info, void *stream);
+
 /* Log-likelihood without any workspace or allocation (GP_FP64 only).  The
  * paper has no counterpart: this entry point serves callers that cannot
  * allocate device memory when they need a log-likelihood -- code running

@@ -220,6 +220,8 @@ __global__ void __launch_bounds__(256) grad_contract_kernel(const double2 *__res
                                                             int64_t ld, const double *a,
                                                             double *part, const int64_t *info) {
     __shared__ double2 xc[TB];
+    __shared__ double tab[EXP_TAB];
+    stage_exp_table(kp, tab);
     __shared__ double ac[TB];
     __shared__ double red[3][8];
     if (failed(info)) return;
@@ -250,7 +252,7 @@ __global__ void __launch_bounds__(256) grad_contract_kernel(const double2 *__res
             } else {
                 const double cb2 = fma(ai, ac[c], -w);
                 double cv, dr;
-                cov_and_dlogrho(kp, pair_dist(xi, xc[c]), cv, dr);
+                cov_and_dlogrho(kp, pair_dist(xi, xc[c]), cv, dr, tab);
                 g0 = fma(cb2, cv, g0);
                 g1 = fma(cb2, dr, g1);
             }

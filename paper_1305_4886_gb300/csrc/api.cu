@@ -6,7 +6,10 @@
 #include "internal.h"
 #include "kern.cuh"
 
+#include <algorithm>
 #include <atomic>
+#include <mutex>
+#include <vector>
 
 namespace gp {
 
@@ -227,6 +230,126 @@ int gp_loglik_grad(const double *d_x, const double *d_y, const double *d_mu, int
         cudaMemcpyAsync(d_alpha, w.v, sizeof(double) * n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return GP_ERR_CUDA;
     return GP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched evaluation: independent problems on a pool of library streams,
+// forked from and joined back to the caller's stream with events, so that a
+// capture of the caller's stream records the whole batch as one graph.
+// ---------------------------------------------------------------------------
+size_t gp_batched_workspace_bytes(int nprob, const int64_t *h_n, int precision) {
+    if (nprob < 1 || !h_n || !precision_ok(precision)) return 0;
+    size_t tot = 0;
+    for (int i = 0; i < nprob; ++i) {
+        if (h_n[i] < 1) return 0;
+        tot += (loglik_ws_layout(nullptr, h_n[i], precision, 1).bytes + 255) & ~size_t(255);
+    }
+    return tot;
+}
+
+}  // extern "C"
+
+namespace gp {
+
+constexpr int BATCH_STREAMS = 24;
+
+struct StreamPool {
+    cudaStream_t s[BATCH_STREAMS];
+    cudaEvent_t done[BATCH_STREAMS];
+    cudaEvent_t fork;
+};
+
+// One pool per device, created on first use and kept for the process.
+static int batch_pool(StreamPool **out) {
+    static std::mutex mu;
+    static StreamPool *pools[64] = {};
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return GP_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!pools[dev]) {
+        StreamPool *p = new StreamPool();
+        if (cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming) != cudaSuccess) {
+            delete p;
+            return GP_ERR_CUDA;
+        }
+        for (int k = 0; k < BATCH_STREAMS; ++k) {
+            if (cudaStreamCreateWithFlags(&p->s[k], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&p->done[k], cudaEventDisableTiming) != cudaSuccess) {
+                delete p;
+                return GP_ERR_CUDA;
+            }
+        }
+        pools[dev] = p;
+    }
+    *out = pools[dev];
+    return GP_OK;
+}
+
+}  // namespace gp
+
+extern "C" {
+
+int gp_loglik_grad_batched(int nprob, const int64_t *h_n, const double *const *h_dx,
+                           const double *const *h_dy, const double *const *h_dmu,
+                           const gp_params *h_prm, int precision, void *d_ws, size_t ws_bytes,
+                           double *d_out, double *d_grad, int64_t *d_info, void *stream) {
+    if (nprob < 1 || !h_n || !h_dx || !h_dy || !h_prm || !d_out || !d_grad || !d_info ||
+        !precision_ok(precision))
+        return GP_ERR_INVALID;
+    for (int i = 0; i < nprob; ++i)
+        if (h_n[i] < 1 || !h_dx[i] || !h_dy[i] || !params_ok(&h_prm[i])) return GP_ERR_INVALID;
+    const size_t need = gp_batched_workspace_bytes(nprob, h_n, precision);
+    if (!d_ws || ws_bytes < need) return GP_ERR_WORKSPACE;
+    StreamPool *pool = nullptr;
+    GP_TRY(batch_pool(&pool));
+    cudaStream_t s = (cudaStream_t)stream;
+    // workspace offsets in problem order
+    std::vector<size_t> off(nprob);
+    size_t acc = 0;
+    for (int i = 0; i < nprob; ++i) {
+        off[i] = acc;
+        acc += (loglik_ws_layout(nullptr, h_n[i], precision, 1).bytes + 255) & ~size_t(255);
+    }
+    // longest-processing-time assignment of problems (cost ~ n^3) to streams
+    std::vector<int> order(nprob);
+    for (int i = 0; i < nprob; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return h_n[a] > h_n[b]; });
+    const int ns = nprob < BATCH_STREAMS ? nprob : BATCH_STREAMS;
+    std::vector<double> load(ns, 0.0);
+    std::vector<std::vector<int>> lists(ns);
+    for (int i : order) {
+        int best = 0;
+        for (int k = 1; k < ns; ++k)
+            if (load[k] < load[best]) best = k;
+        load[best] += (double)h_n[i] * h_n[i] * h_n[i];
+        lists[best].push_back(i);
+    }
+    if (cudaEventRecord(pool->fork, s) != cudaSuccess) return GP_ERR_CUDA;
+    int status = GP_OK;
+    for (int k = 0; k < ns; ++k) {
+        cudaStream_t sk = pool->s[k];
+        if (cudaStreamWaitEvent(sk, pool->fork, 0) != cudaSuccess) return GP_ERR_CUDA;
+        for (int i : lists[k]) {
+            const int64_t n = h_n[i];
+            const int64_t np = padded(n);
+            LoglikWs w = loglik_ws_layout(static_cast<char *>(d_ws) + off[i], n, precision, 1);
+            KernParams kp = make_kern(h_prm[i]);
+            const double *mu = h_dmu ? h_dmu[i] : nullptr;
+            int st = loglik_core(h_dx[i], h_dy[i], mu, n, kp, precision, w, d_out + 4 * i,
+                                 d_info + i, sk);
+            if (st == GP_OK)
+                st = chol_inverse(w.A, np, np, precision, MIXED_SLICES, w.chol, d_info + i, sk);
+            if (st == GP_OK)
+                st = grad_contract(h_dx[i], n, np, kp, w.A, np, w.v, w.chol, precision,
+                                   MIXED_SLICES, d_grad + 3 * i, d_info + i, sk);
+            if (st != GP_OK && status == GP_OK) status = st;
+        }
+        // join even after a launch error, so that the caller's stream stays ordered
+        if (cudaEventRecord(pool->done[k], sk) != cudaSuccess ||
+            cudaStreamWaitEvent(s, pool->done[k], 0) != cudaSuccess)
+            return GP_ERR_CUDA;
+    }
+    return status;
 }
 
 size_t gp_syrk_workspace_bytes(int64_t m, int64_t k, int precision) {

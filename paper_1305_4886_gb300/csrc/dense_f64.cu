@@ -17,12 +17,18 @@ namespace gp {
 
 // ---------------------------------------------------------------------------
 // Cholesky of the 64 x 64 tile at A (column-major, ld), right-looking in
-// shared memory.  col_base is the global column of the tile's first column
-// (for the d_info convention).  Pivots <= 0 or NaN stop the factorisation.
+// shared memory on the unscaled columns: step j subtracts a_rj a_cj / d_j
+// from the trailing lower triangle (d_j the current pivot), and the columns
+// are scaled by 1/sqrt(d_j) once at the end (L_rj = a_rj / sqrt(d_j)).  One
+// thread forms 1/d_j per step, so each step costs two barriers and no FP64
+// division or square root on the serial chain.  col_base is the global
+// column of the tile's first column (for the d_info convention).  A pivot
+// <= 0 or NaN stops the factorisation.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) potrf_tile_kernel(double *A, int64_t ld, int64_t col_base,
                                                          int64_t *info) {
     __shared__ double S[TB * (TB + 1)];
+    __shared__ double dinv[TB];
     __shared__ int bad;
     if (failed(info)) return;
     const int tid = threadIdx.x;
@@ -33,32 +39,33 @@ __global__ void __launch_bounds__(256) potrf_tile_kernel(double *A, int64_t ld, 
     if (tid == 0) bad = 0;
     __syncthreads();
     for (int j = 0; j < TB; ++j) {
-        double d = S[j * (TB + 1) + j];
-        if (!(d > 0.0)) {  // uniform: every thread read the same value
-            if (tid == 0) {
+        if (tid == 0) {
+            const double d = S[j * (TB + 1) + j];
+            if (!(d > 0.0)) {
                 bad = 1;
                 set_info(info, col_base + j + 1);
+            } else {
+                dinv[j] = 1.0 / d;
             }
-            break;
         }
-        double ljj = sqrt(d);
         __syncthreads();
-        if (tid >= j && tid < TB) S[j * (TB + 1) + tid] = (tid == j) ? ljj : S[j * (TB + 1) + tid] / ljj;
-        __syncthreads();
-        // rank-1 update of the trailing lower triangle, columns j+1..63
+        if (bad) break;  // uniform
+        const double inv = dinv[j];
+        const double *cj = S + j * (TB + 1);
+        // a_rc -= a_rj a_cj / d_j for j < c <= r < 64
         const int w = TB - 1 - j;
         for (int e = tid; e < w * TB; e += blockDim.x) {
-            int c = j + 1 + e / TB;
-            int r = e & (TB - 1);
-            if (r >= c) S[c * (TB + 1) + r] -= S[j * (TB + 1) + r] * S[j * (TB + 1) + c];
+            const int c = j + 1 + e / TB;
+            const int r = e & (TB - 1);
+            if (r >= c) S[c * (TB + 1) + r] -= cj[r] * (cj[c] * inv);
         }
         __syncthreads();
     }
-    __syncthreads();
     if (bad) return;
+    // L_rj = a_rj / sqrt(d_j):  a_rj * sqrt(1/d_j)
     for (int e = tid; e < TB * TB; e += blockDim.x) {
         int r = e & (TB - 1), c = e >> 6;
-        if (r >= c) A[r + (int64_t)c * ld] = S[c * (TB + 1) + r];
+        if (r >= c) A[r + (int64_t)c * ld] = S[c * (TB + 1) + r] * sqrt(dinv[c]);
     }
 }
 
@@ -91,10 +98,15 @@ __global__ void __launch_bounds__(256) trsm_tiles_kernel(const double *L, double
     __syncthreads();
     if (tid < TB) rinv[tid] = 1.0 / Ls[tid * (TB + 1) + tid];
     __syncthreads();
+    // M_{c2,c} = L_{c2,c} / L_cc, so that on the unscaled columns
+    // b_c2 -= b_c M_{c2,c} (X_c = b_c / L_cc is applied once at the end)
+    for (int e = tid; e < TB * TB; e += blockDim.x) {
+        int r = e & (TB - 1), c = e >> 6;
+        if (r > c) Ls[c * (TB + 1) + r] *= rinv[c];
+    }
+    __syncthreads();
     // X L^T = B: column c of X = (B_c - sum_{l<c} X_l L_cl) / L_cc
-    for (int c = 0; c < TB; ++c) {
-        if (tid < TR_ROWS) Bs[c * (TR_ROWS + 1) + tid] *= rinv[c];
-        __syncthreads();
+    for (int c = 0; c < TB - 1; ++c) {
         const int w = TB - 1 - c;
         for (int e = tid; e < w * TR_ROWS; e += blockDim.x) {
             int c2 = c + 1 + e / TR_ROWS;
@@ -105,7 +117,7 @@ __global__ void __launch_bounds__(256) trsm_tiles_kernel(const double *L, double
     }
     for (int e = tid; e < TB * TR_ROWS; e += blockDim.x) {
         int r = e & (TR_ROWS - 1), c = e >> 5;
-        if (r < nr) B[r + (int64_t)c * ld] = Bs[c * (TR_ROWS + 1) + r];
+        if (r < nr) B[r + (int64_t)c * ld] = Bs[c * (TR_ROWS + 1) + r] * rinv[c];
     }
 }
 
@@ -128,10 +140,18 @@ __global__ void __launch_bounds__(256) trtri_tiles_kernel(const double *L, int64
         Bs[c * (TB + 1) + r] = (r == c) ? 1.0 : 0.0;
     }
     __syncthreads();
+    __shared__ double rinv[TB];
+    if (tid < TB) rinv[tid] = 1.0 / Ls[tid * (TB + 1) + tid];
+    __syncthreads();
+    // row c of L scaled by 1/L_cc: on the unscaled columns b_c2 -= b_c L_c,c2 / L_cc,
+    // and X_c = b_c / L_cc is applied once at the end
+    for (int e = tid; e < TB * TB; e += blockDim.x) {
+        int r = e & (TB - 1), c = e >> 6;
+        if (r > c) Ls[c * (TB + 1) + r] *= rinv[r];
+    }
+    __syncthreads();
     // X L = I: column c of X (descending) = (B_c - sum_{l>c} X_l L_lc) / L_cc
-    for (int c = TB - 1; c >= 0; --c) {
-        if (tid < TB) Bs[c * (TB + 1) + tid] /= Ls[c * (TB + 1) + c];
-        __syncthreads();
+    for (int c = TB - 1; c > 0; --c) {
         for (int e = tid; e < c * TB; e += blockDim.x) {
             int c2 = e / TB;
             int r = e & (TB - 1);
@@ -141,7 +161,7 @@ __global__ void __launch_bounds__(256) trtri_tiles_kernel(const double *L, int64
     }
     for (int e = tid; e < TB * TB; e += blockDim.x) {
         int r = e & (TB - 1), c = e >> 6;
-        Xt[r + (int64_t)c * ld_x] = (r >= c) ? Bs[c * (TB + 1) + r] : 0.0;
+        Xt[r + (int64_t)c * ld_x] = (r >= c) ? Bs[c * (TB + 1) + r] * rinv[c] : 0.0;
     }
 }
 

@@ -18,6 +18,8 @@ __global__ void __launch_bounds__(256) cov_fill_kernel(const double2 *__restrict
                                                        double *__restrict__ C, int64_t ldc,
                                                        int64_t *info) {
     __shared__ double2 xc[TB];
+    __shared__ double tab[EXP_TAB];
+    stage_exp_table(kp, tab);
     int64_t ti, tj;
     lower_tile_coords(blockIdx.x, ti, tj);
     (void)tiles_per_side;
@@ -44,7 +46,7 @@ __global__ void __launch_bounds__(256) cov_fill_kernel(const double2 *__restrict
         const int64_t j = col0 + c;
         double v;
         if (i < n && j < n) {
-            v = (i == j) ? kp.diag : cov_offdiag(kp, pair_dist(xi, xc[c]));
+            v = (i == j) ? kp.diag : cov_offdiag(kp, pair_dist(xi, xc[c]), tab);
         } else {
             v = (i == j) ? 1.0 : 0.0;
         }

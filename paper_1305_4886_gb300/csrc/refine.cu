@@ -22,6 +22,8 @@ __global__ void __launch_bounds__(256) cov_matvec_kernel(const double2 *__restri
                                                          const double *__restrict__ a, double *acc,
                                                          const int *skip, const int64_t *info) {
     __shared__ double2 xc[TB];
+    __shared__ double tab[EXP_TAB];
+    stage_exp_table(kp, tab);
     __shared__ double ac[TB];
     __shared__ double colsum[2][TB];
     __shared__ double rowsum[4][TB];
@@ -51,7 +53,7 @@ __global__ void __launch_bounds__(256) cov_matvec_kernel(const double2 *__restri
     for (int c = cg; c < TB; c += 4) {
         const int64_t j = col0 + c;
         double v = 0.0;
-        if (row_ok && j < n) v = (i == j) ? kp.diag : cov_offdiag(kp, pair_dist(xi, xc[c]));
+        if (row_ok && j < n) v = (i == j) ? kp.diag : cov_offdiag(kp, pair_dist(xi, xc[c]), tab);
         rs = fma(v, ac[c], rs);
         if (!diag) {
             double cs = v * ai;

@@ -307,8 +307,10 @@ __global__ void __launch_bounds__(192, 1)
 //   trans = 1: src[k + r ld]   (operand rows are source columns)
 // lower_mask: entries above the source diagonal are treated as zero
 // (trans = 0: r + diag_off < k; trans = 1: k + diag_off < r), for triangular
-// sources whose upper part holds stale data.  One CTA packs 32 rows over
-// the whole K range: pass 1 finds each row's bound 2^e_r, pass 2 writes the
+// sources whose upper part holds stale data.  One CTA packs 32 rows over a
+// 512-column chunk of K: pass 1 finds each row's bound 2^e_r over the chunk
+// (so the leading products are exact within every 512-deep chunk of a
+// contraction whose operands share the chunking), pass 2 writes the
 // slices with k contiguous (trans = 0 goes through a shared-memory
 // transpose so that both the FP64 reads and the BF16 writes are coalesced).
 // The split runs in FP32 after one FP64 -> (hi, lo) FP32 conversion.
@@ -324,18 +326,46 @@ struct SplitArgs {
     int64_t dst_rows, dst_kld, dst_row_off, dst_k_off;
 };
 
-__device__ __forceinline__ double split_get(const SplitArgs &a, int64_t r, int64_t k) {
-    if (r >= a.R || k >= a.Kvalid) return 0.0;
+// raw bits of operand element (r, k); masked and out-of-range entries are +0
+__device__ __forceinline__ unsigned long long split_get(const SplitArgs &a, int64_t r, int64_t k) {
+    if (r >= a.R || k >= a.Kvalid) return 0ull;
     if (a.lower_mask) {
-        if (a.trans ? (k + a.diag_off < r) : (r + a.diag_off < k)) return 0.0;
+        if (a.trans ? (k + a.diag_off < r) : (r + a.diag_off < k)) return 0ull;
     }
-    return a.trans ? a.src[k + r * a.ld] : a.src[r + k * a.ld];
+    const double v = a.trans ? a.src[k + r * a.ld] : a.src[r + k * a.ld];
+    return static_cast<unsigned long long>(__double_as_longlong(v));
+}
+
+// x = hi + lo with integer operations only (the FP64 pipe is the scarce one
+// on this part): hi keeps the top 24 significant bits (truncated), lo the
+// remaining 29 rounded to FP32.  Magnitudes below 2^-126 map to 0 and lo
+// parts below 2^-126 are dropped (negligible next to the row bounds used).
+__device__ __forceinline__ void f64_hi_lo(unsigned long long u, float &hi, float &lo) {
+    const unsigned int sign = static_cast<unsigned int>(u >> 32) & 0x80000000u;
+    const int E = static_cast<int>((u >> 52) & 0x7FF);
+    const int ef = E - 1023 + 127;
+    hi = 0.0f;
+    lo = 0.0f;
+    if (E == 0 || ef <= 0) return;
+    if (ef >= 255) {
+        hi = __int_as_float(sign | 0x7F800000u);
+        return;
+    }
+    const unsigned long long mant = u & 0x000FFFFFFFFFFFFFull;
+    hi = __int_as_float(sign | (static_cast<unsigned int>(ef) << 23) |
+                        static_cast<unsigned int>(mant >> 29));
+    const int es = E - 1075;  // weight of the mantissa's last bit
+    if (es >= -126) {
+        const float lf = __uint2float_rn(static_cast<unsigned int>(mant & 0x1FFFFFFFull));
+        lo = __int_as_float(__float_as_int(lf * __int_as_float((es + 127) << 23)) | sign);
+    }
 }
 
 // s0, s1, s2 for one entry, given the row's scale 2^{7-e} (sc) and 2^{e-7} (isc).
-__device__ __forceinline__ void split3(double x, float sc, float isc, __nv_bfloat16 (&s)[3]) {
-    const float xh = static_cast<float>(x);
-    const float xl = static_cast<float>(x - static_cast<double>(xh));
+__device__ __forceinline__ void split3(unsigned long long u, float sc, float isc,
+                                       __nv_bfloat16 (&s)[3]) {
+    float xh, xl;
+    f64_hi_lo(u, xh, xl);
     const float q = rintf(xh * sc);
     const float s0 = q * isc;
     const float r1 = (xh - s0) + xl;
@@ -346,39 +376,53 @@ __device__ __forceinline__ void split3(double x, float sc, float isc, __nv_bfloa
     s[2] = __float2bfloat16_rn(r2);
 }
 
+constexpr int64_t SPLIT_KCH = 512;  // K chunk of one CTA (and of one row bound)
+
 __global__ void __launch_bounds__(256) split_rows_kernel(SplitArgs a) {
-    __shared__ float pmax[8][32];
+    __shared__ unsigned long long pmax[8][32];
     __shared__ float sc_s[32], isc_s[32];
     __shared__ unsigned short tile[3][32][33];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t r0 = (int64_t)blockIdx.x * 32;
-    // pass 1: row bounds
+    // this CTA's K chunk; each (row, chunk) gets its own bound 2^e
+    const int64_t kb = (int64_t)blockIdx.y * SPLIT_KCH;
+    const int64_t ke = min(a.K, kb + SPLIT_KCH);
+    const int64_t kev = min(ke, a.Kvalid);
+    constexpr unsigned long long ABS = 0x7FFFFFFFFFFFFFFFull;
+    // pass 1: row bounds, as the largest magnitude's bit pattern
     if (a.trans == 0) {
-        float m = 0.0f;
-        for (int64_t k = warp; k < a.Kvalid; k += 8)
-            m = fmaxf(m, fabsf(static_cast<float>(split_get(a, r0 + lane, k))));
+        unsigned long long m = 0ull;
+        for (int64_t k = kb + warp; k < kev; k += 8) {
+            const unsigned long long v = split_get(a, r0 + lane, k) & ABS;
+            m = v > m ? v : m;
+        }
         pmax[warp][lane] = m;
     } else {
         for (int i = warp; i < 32; i += 8) {
-            float m = 0.0f;
-            for (int64_t k = lane; k < a.Kvalid; k += 32)
-                m = fmaxf(m, fabsf(static_cast<float>(split_get(a, r0 + i, k))));
+            unsigned long long m = 0ull;
+            for (int64_t k = kb + lane; k < kev; k += 32) {
+                const unsigned long long v = split_get(a, r0 + i, k) & ABS;
+                m = v > m ? v : m;
+            }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
+                m = t > m ? t : m;
+            }
             if (lane == 0) {
                 pmax[0][i] = m;
-                for (int w = 1; w < 8; ++w) pmax[w][i] = 0.0f;
+                for (int w = 1; w < 8; ++w) pmax[w][i] = 0ull;
             }
         }
     }
     __syncthreads();
     if (threadIdx.x < 32) {
-        float m = 0.0f;
-        for (int w = 0; w < 8; ++w) m = fmaxf(m, pmax[w][threadIdx.x]);
-        // the float rounding of the max can round up across a power of two;
-        // one extra unit of headroom keeps |x 2^{7-e}| <= 128
+        unsigned long long m = 0ull;
+        for (int w = 0; w < 8; ++w) m = pmax[w][threadIdx.x] > m ? pmax[w][threadIdx.x] : m;
+        // every entry of the row is below 2^e, e = unbiased exponent of the max + 1
         int e = 0;
-        if (m > 0.0f) e = ilogbf(m) + 1;
+        const int E = static_cast<int>(m >> 52);
+        if (E > 0) e = E - 1022;
         e = max(-100, min(e, 120));
         sc_s[threadIdx.x] = ldexpf(1.0f, 7 - e);
         isc_s[threadIdx.x] = ldexpf(1.0f, e - 7);
@@ -387,7 +431,7 @@ __global__ void __launch_bounds__(256) split_rows_kernel(SplitArgs a) {
     const int64_t slice = a.dst_rows * a.dst_kld;
     __nv_bfloat16 *d0 = a.dst + (a.dst_row_off + r0) * a.dst_kld + a.dst_k_off;
     if (a.trans == 0) {
-        for (int64_t kc = 0; kc < a.K; kc += 32) {
+        for (int64_t kc = kb; kc < ke; kc += 32) {
             // lane = row: coalesced FP64 reads down each column
             for (int i = warp; i < 32; i += 8) {
                 __nv_bfloat16 s[3];
@@ -399,7 +443,7 @@ __global__ void __launch_bounds__(256) split_rows_kernel(SplitArgs a) {
             // lane = k: coalesced BF16 writes along each row
             for (int i = warp; i < 32; i += 8) {
                 const int64_t r = r0 + i, k = kc + lane;
-                if (r < a.R && k < a.K) {
+                if (r < a.R && k < ke) {
                     for (int p = 0; p < a.S; ++p)
                         d0[p * slice + (int64_t)i * a.dst_kld + k] =
                             __ushort_as_bfloat16(tile[p][lane][i]);
@@ -411,7 +455,7 @@ __global__ void __launch_bounds__(256) split_rows_kernel(SplitArgs a) {
         for (int i = warp; i < 32; i += 8) {
             const int64_t r = r0 + i;
             if (r >= a.R) continue;
-            for (int64_t k = lane; k < a.K; k += 32) {
+            for (int64_t k = kb + lane; k < ke; k += 32) {
                 __nv_bfloat16 s[3];
                 split3(split_get(a, r, k), sc_s[i], isc_s[i], s);
                 for (int p = 0; p < a.S; ++p) d0[p * slice + (int64_t)i * a.dst_kld + k] = s[p];
@@ -429,7 +473,8 @@ int split_rows(const double *src, int64_t ld, int64_t R, int64_t K, int64_t Kval
     SplitArgs a{src, ld, R, K, Kvalid < K ? Kvalid : K, trans, diag_off, lower_mask, S, dst,
                 dst_rows, dst_kld, dst_row_off, dst_k_off};
     const int ev = prof_start(s);
-    split_rows_kernel<<<(unsigned)ceil_div(R, 32), 256, 0, s>>>(a);
+    dim3 g((unsigned)ceil_div(R, 32), (unsigned)ceil_div(K, SPLIT_KCH));
+    split_rows_kernel<<<g, 256, 0, s>>>(a);
     GP_LAUNCH_CHECK();
     prof_stop(ev, s, GP_PROF_PACK, 0.0, (double)R * K * (8.0 + 2.0 * S));
     return GP_OK;

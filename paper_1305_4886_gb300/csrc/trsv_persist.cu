@@ -57,6 +57,8 @@ __global__ void __launch_bounds__(256) trsv_fwd_persist_kernel(const double *__r
     __shared__ int s_blk, s_ok;
     __shared__ double xs[PB];
     __shared__ double part[4][PB];
+    __shared__ double Ld[PB * (PB + 1)];  // diagonal tile, Ld[c (PB+1) + r] = L[r0+r, r0+c]
+    __shared__ double rinv[PB];
     if ((skip && *skip) || failed(info)) return;
     const int tid = threadIdx.x;
     const int T = (int)ceil_div(n, PB);
@@ -67,6 +69,14 @@ __global__ void __launch_bounds__(256) trsv_fwd_persist_kernel(const double *__r
     const int64_t r0 = (int64_t)i * PB;
     const int bs = (int)min((int64_t)PB, n - r0);
     const int r = tid & (PB - 1), cg = tid >> 6;
+    // the diagonal tile and its pivots' reciprocals do not depend on other
+    // blocks: stage them while the earlier blocks are still being solved
+    for (int e = tid; e < PB * PB; e += blockDim.x) {
+        const int rr = e & (PB - 1), cc = e >> 6;
+        Ld[cc * (PB + 1) + rr] = (rr < bs && cc < bs && rr >= cc) ? L[(r0 + rr) + (r0 + cc) * ld] : 0.0;
+    }
+    __syncthreads();
+    if (tid < bs) rinv[tid] = 1.0 / Ld[tid * (PB + 1) + tid];
     double acc = 0.0;
     for (int j = 0; j < i; ++j) {
         if (tid == 0) s_ok = wait_flag(&sync[1 + j], info);
@@ -85,20 +95,19 @@ __global__ void __launch_bounds__(256) trsv_fwd_persist_kernel(const double *__r
     __syncthreads();
     if (tid >= 32) return;
     const int l = tid;
-    const double *Td = L + r0 + r0 * ld;
     double v0 = 0.0, v1 = 0.0;
     if (l < bs) v0 = b[r0 + l] - (part[0][l] + part[1][l] + part[2][l] + part[3][l]);
     if (l + 32 < bs)
         v1 = b[r0 + l + 32] - (part[0][l + 32] + part[1][l + 32] + part[2][l + 32] + part[3][l + 32]);
     for (int c = 0; c < bs; ++c) {
         const double mine = (c < 32) ? v0 : v1;
-        const double xc = __shfl_sync(0xffffffffu, mine, c & 31) / Td[c + (int64_t)c * ld];
+        const double xc = __shfl_sync(0xffffffffu, mine, c & 31) * rinv[c];
         if (l == (c & 31)) {
             if (c < 32) v0 = xc; else v1 = xc;
         }
-        const double *col = Td + (int64_t)c * ld;
-        if (l > c && l < bs) v0 -= col[l] * xc;
-        if (l + 32 > c && l + 32 < bs) v1 -= col[l + 32] * xc;
+        const double *col = Ld + c * (PB + 1);
+        if (l > c) v0 -= col[l] * xc;
+        if (l + 32 > c) v1 -= col[l + 32] * xc;
     }
     publish(b, r0, bs, v0, v1, &sync[1 + i]);
 }
@@ -112,6 +121,8 @@ __global__ void __launch_bounds__(256) trsv_bwd_persist_kernel(const double *__r
     __shared__ int s_blk, s_ok;
     __shared__ double xs[PB];
     __shared__ double part[PB];
+    __shared__ double Ld[PB * (PB + 1)];  // diagonal tile, Ld[c (PB+1) + r] = L[r0+r, r0+c]
+    __shared__ double rinv[PB];
     if ((skip && *skip) || failed(info)) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int T = (int)ceil_div(n, PB);
@@ -122,6 +133,12 @@ __global__ void __launch_bounds__(256) trsv_bwd_persist_kernel(const double *__r
     const int i = T - 1 - t;
     const int64_t r0 = (int64_t)i * PB;
     const int bs = (int)min((int64_t)PB, n - r0);
+    for (int e = tid; e < PB * PB; e += blockDim.x) {
+        const int rr = e & (PB - 1), cc = e >> 6;
+        Ld[cc * (PB + 1) + rr] = (rr < bs && cc < bs && rr >= cc) ? L[(r0 + rr) + (r0 + cc) * ld] : 0.0;
+    }
+    __syncthreads();
+    if (tid < bs) rinv[tid] = 1.0 / Ld[tid * (PB + 1) + tid];
     // lane partials for the 8 columns (of this block) owned by this warp
     double acc[8];
 #pragma unroll
@@ -158,18 +175,18 @@ __global__ void __launch_bounds__(256) trsv_bwd_persist_kernel(const double *__r
     __syncthreads();
     if (tid >= 32) return;
     const int l = tid;
-    const double *Td = L + r0 + r0 * ld;
     double v0 = 0.0, v1 = 0.0;
     if (l < bs) v0 = b[r0 + l] - part[l];
     if (l + 32 < bs) v1 = b[r0 + l + 32] - part[l + 32];
     for (int c = bs - 1; c >= 0; --c) {
         const double mine = (c < 32) ? v0 : v1;
-        const double xc = __shfl_sync(0xffffffffu, mine, c & 31) / Td[c + (int64_t)c * ld];
+        const double xc = __shfl_sync(0xffffffffu, mine, c & 31) * rinv[c];
         if (l == (c & 31)) {
             if (c < 32) v0 = xc; else v1 = xc;
         }
-        if (l < c) v0 -= Td[c + (int64_t)l * ld] * xc;
-        if (l + 32 < c) v1 -= Td[c + (int64_t)(l + 32) * ld] * xc;
+        // row c of the tile: L[r0+c, r0+l] = Ld[l (PB+1) + c]
+        if (l < c) v0 -= Ld[l * (PB + 1) + c] * xc;
+        if (l + 32 < c) v1 -= Ld[(l + 32) * (PB + 1) + c] * xc;
     }
     publish(b, r0, bs, v0, v1, &sync[1 + i]);
 }

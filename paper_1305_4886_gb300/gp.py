@@ -31,6 +31,8 @@ SYMBOLS = [
     "gp_mult_chol",
     "gp_loglik",
     "gp_loglik_grad",
+    "gp_batched_workspace_bytes",
+    "gp_loglik_grad_batched",
     "gp_loglik_noalloc",
     "gp_syrk_workspace_bytes",
     "gp_syrk_lower",
@@ -100,6 +102,10 @@ def lib():
             L.gp_mult_chol.argtypes = [p, i64, i64, p, p, p]
             L.gp_loglik.argtypes = [p, p, p, i64, PP, ci, p, sz, p, p, p, p]
             L.gp_loglik_grad.argtypes = [p, p, p, i64, PP, ci, p, sz, p, p, p, p, p]
+            L.gp_batched_workspace_bytes.argtypes = [ci, p, ci]
+            L.gp_batched_workspace_bytes.restype = sz
+            L.gp_loglik_grad_batched.argtypes = [ci, p, p, p, p, p, ci, p, sz, p, p, p, p]
+            L.gp_loglik_grad_batched.restype = ci
             L.gp_loglik_noalloc.argtypes = [p, p, p, i64, PP, p, p, p, p]
             L.gp_loglik_noalloc.restype = ci
             L.gp_syrk_workspace_bytes.argtypes = [i64, i64, ci]
@@ -203,6 +209,52 @@ def gp_loglik(x, y, mu, n, prm, precision, ws, out, alpha, info, stream=None):
     _check(lib().gp_loglik(_f64(x), _f64(y), _f64(mu), int(n), ctypes.byref(prm), _prec(precision),
                            _ptr(ws), wsb, _f64(out), _f64(alpha), _ptr(info), _stream(stream)),
            "gp_loglik")
+
+
+class Batch:
+    """Host-side argument arrays of gp_loglik_grad_batched, kept alive with
+    the device tensors they point to."""
+
+    def __init__(self, xs, ys, prms, mus=None):
+        self.nprob = len(xs)
+        self.xs, self.ys, self.mus = list(xs), list(ys), mus
+        self.n = (ctypes.c_int64 * self.nprob)(*[int(x.shape[0]) for x in xs])
+        P = ctypes.c_void_p * self.nprob
+        self.px = P(*[_f64(x).value for x in xs])
+        self.py = P(*[_f64(y).value for y in ys])
+        self.pmu = P(*[(_f64(m).value if m is not None else None) for m in mus]) if mus else None
+        self.prm = (GpParams * self.nprob)(*prms)
+
+
+def gp_batched_workspace_bytes(ns, precision="mixed_bf16"):
+    arr = (ctypes.c_int64 * len(ns))(*[int(v) for v in ns])
+    return lib().gp_batched_workspace_bytes(len(ns), ctypes.cast(arr, ctypes.c_void_p),
+                                            _prec(precision))
+
+
+def gp_loglik_grad_batched(batch, precision, ws, out, grad, info, stream=None):
+    wsb = ws.numel() * ws.element_size()
+    v = ctypes.c_void_p
+    _check(lib().gp_loglik_grad_batched(
+        batch.nprob, ctypes.cast(batch.n, v), ctypes.cast(batch.px, v), ctypes.cast(batch.py, v),
+        ctypes.cast(batch.pmu, v) if batch.pmu is not None else None,
+        ctypes.cast(batch.prm, v), _prec(precision), _ptr(ws), wsb, _f64(out), _f64(grad),
+        _ptr(info), _stream(stream)), "gp_loglik_grad_batched")
+
+
+def loglik_grad_batched(xs, ys, prms, precision="mixed_bf16", mus=None, ws=None):
+    """Evaluate a batch on the device; returns dict(out (nprob x 4), grad
+    (nprob x 3), info (nprob,), ws, batch).  prms: list of GpParams."""
+    batch = Batch(xs, ys, prms, mus)
+    dev = xs[0].device
+    if ws is None:
+        nb = gp_batched_workspace_bytes([x.shape[0] for x in xs], precision)
+        ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+    out = torch.empty(batch.nprob, 4, dtype=torch.float64, device=dev)
+    grad = torch.empty(batch.nprob, 3, dtype=torch.float64, device=dev)
+    info = torch.zeros(batch.nprob, dtype=torch.int64, device=dev)
+    gp_loglik_grad_batched(batch, precision, ws, out, grad, info)
+    return dict(out=out, grad=grad, info=info, ws=ws, batch=batch)
 
 
 def gp_loglik_noalloc(x, y, mu, n, prm, out, alpha, info, stream=None):

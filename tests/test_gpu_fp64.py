@@ -152,3 +152,37 @@ def test_nonfinite_inputs_flagged(g):
     assert int(r["info"].item()) == -2
     with pytest.raises(g.GpDeviceError):
         g.loglik(dev(x), dev(yb), "exp", 1.0, 0.1, 0.1)
+
+
+def test_fill_exponent_range(g, orc):
+    """Kernel arguments a spread over [0, 1600] (the device exp's whole range,
+    including the flush to zero near the FP64 underflow).
+
+    exp(-a) has condition number a, so one ulp of a (the oracle divides by
+    rho, the device multiplies by 1/rho) moves it by a*eps relative: against
+    the oracle the bound is 1e-13 + 8 a eps.  Against numpy's exp at the very
+    same a (formed like the device: sqrt of the squared differences times
+    c/rho), the device exp itself must hold 1e-13 relative.  Entries below
+    1e-290 must be below 1e-290 on the device too."""
+    n = 700
+    t = np.linspace(0.0, 1.0, n)
+    x = np.stack([t * t, np.zeros(n)], axis=1)  # uneven spacing: many distinct a
+    rho = 1.0 / 720.0
+    np_ = g.gp_padded_order(n)
+    buf = torch.empty(np_ * np_, dtype=torch.float64, device="cuda")
+    low = np.tril_indices(n, -1)
+    d = np.sqrt((x[:, None, 0] - x[None, :, 0]) ** 2 + (x[:, None, 1] - x[None, :, 1]) ** 2)[low]
+    eps = np.finfo(np.float64).eps
+    for kern, c in [("exp", 1.0), ("matern32", math.sqrt(3.0)), ("matern52", math.sqrt(5.0))]:
+        g.gp_cov_fill(dev(x), g.params(kern, 1.0, rho, 0.0), buf, np_)
+        torch.cuda.synchronize()
+        C = colmajor_to_numpy(buf, np_)[:n, :n][low]
+        a = d * (c / rho)
+        e = np.exp(-a)
+        same_a = {"exp": e, "matern32": (a * e + e),
+                  "matern52": (1.0 + a + a * a * (1.0 / 3.0)) * e}[kern]
+        ref = orc.cov_fill(x, kern, 1.0, rho, 0.0)[low]
+        big = np.abs(ref) > 1e-290
+        assert np.all(np.abs(C[big] - same_a[big]) <= 1e-13 * np.abs(same_a[big]))
+        assert np.all(np.abs(C[big] - ref[big]) <= (1e-13 + 8 * eps * a[big]) * np.abs(ref[big]))
+        assert np.all(np.abs(C[~big]) <= 1e-290)
