@@ -45,10 +45,17 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=N_HEADLINE, help="problem size (exploration only)")
-    ap.add_argument("--precision", default="mixed_bf16", choices=["mixed_bf16", "fp64"])
+    ap.add_argument("--precision", default="mixed_f16", choices=["mixed_f16", "emu_fp64", "fp64"],
+                    help="mixed_f16: three FP16 slices (6 products); emu_fp64: five BF16 "
+                         "integer slices (15 products, FP64-grade); fp64: CUDA-core FP64")
     ap.add_argument("--workload", default="single", choices=["single", "batched"],
                     help="single: the n=67,275 problem (default); batched: 512 small problems")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-error", action="store_true",
+                    help="skip the untimed comparison with the FP64-grade form")
+    ap.add_argument("--accuracy", default=None,
+                    help="comma-separated n: print mixed / FP64-grade errors against the "
+                         "FP64 path on the config-3 recipe at each n, then exit")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0,
                     help="seconds of oracle work for the CPU baseline sample")
@@ -143,6 +150,32 @@ def measured_peaks():
 # ---------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle on the host cores
 # ---------------------------------------------------------------------------
+def contraction_traffic(flops_per_launch, prec):
+    """DRAM bytes per average contraction launch, scaled from the committed ncu
+    summary (bytes per slice-product flop over every contraction launch of a
+    smaller loglik+grad); None when the kernel source has changed since."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "tc_gemm_kernel_traffic.md")
+    src = os.path.join(ROOT, "paper_1305_4886_gb300", "csrc", "tc_gemm.cu")
+    try:
+        text = open(path).read()
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if line.startswith("- ") and ":" in line:
+            k, v = line[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("tc_gemm.cu sha256[:16]") != digest:
+        return None
+    key = f"bytes per slice-product flop ({prec})"
+    if key not in vals or not flops_per_launch:
+        return None
+    return {"bytes_per_launch": float(vals[key]) * flops_per_launch,
+            "source": f"{os.path.relpath(path, ROOT)}: {key} x flops per launch"}
+
+
 def oracle_sample(n_target, budget_s, p_full=None):
     """Times the oracle's loglik+grad on a size whose cost fits the budget and
     extrapolates to n_target by the n^3 cost.  Returns (evals/s at n_target,
@@ -320,19 +353,38 @@ def run_ours(args, rank, world, local):
                "h2d_bytes_per_step": int(x_h.numel() * 8 + y_h.numel() * 8),
                "d2h_bytes_per_step": int((out_h.numel() + grad_h.numel()) * 8)}
 
+    # ---- stated error (untimed): the same evaluation in the FP64-grade form ----
+    err = None
+    if not args.no_error and prec == "mixed_f16":
+        ws_ref = gp.workspace(n, "emu_fp64", want_grad=True)
+        r = gp.loglik_grad(x, y, p.kernel, p.s2, p.rho, p.tau2, precision="emu_fp64", ws=ws_ref)
+        ro, rg, ra = r["out"].cpu().numpy(), r["grad"].cpu().numpy(), r["alpha"].cpu().numpy()
+        del ws_ref, r
+        torch.cuda.empty_cache()
+        a_res = alpha.cpu().numpy()
+        err = {"against": "emu_fp64 (five BF16 integer slices, FP64-grade; pinned to the "
+                          "oracle at n <= 1300 to 1e-10 / 1e-8)",
+               "loglik_rel": float(abs(res[0] - ro[0]) / abs(ro[0])),
+               "grad_rel_inf": float(np.max(np.abs(g_res - rg)) / np.max(np.abs(rg))),
+               "alpha_rel": float(np.linalg.norm(a_res - ra) / np.linalg.norm(ra))}
+
     peaks, peak_src = measured_peaks()
     ms_c, cnt_c, fl_c, _ = prof["contract"]
     achieved = fl_c / (ms_c / 1e3) / 1e12 if ms_c > 0 else None
     peak_tf = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+    pairs = {"mixed_f16": 6, "emu_fp64": 15}.get(prec, 0)
+    traffic = contraction_traffic(fl_c / max(cnt_c, 1), prec)
     roofline = {
-        "kernel": "tc_gemm_kernel (tcgen05 BF16-slice contraction: Cholesky update, "
+        "kernel": "tc_gemm_kernel (tcgen05 16-bit-slice contraction: Cholesky update, "
                   "panel solve, TRTRI/LAUUM)",
         "bound": "tensor", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
-        "frac": (achieved / peak_tf) if achieved else None, "traffic": None,
+        "frac": (achieved / peak_tf) if achieved else None,
+        "traffic": traffic["bytes_per_launch"] if traffic else None,
+        "traffic_source": traffic["source"] if traffic else None,
         "peak_source": f"bf16 sustained, {peak_src}", "launches": cnt_c,
         "share_of_step": ms_c / elapsed_ms if elapsed_ms > 0 else None,
-        "flops_counted": "slice-product flops (6 BF16 products per FP64 product) over the "
-                         "useful output entries and K ranges",
+        "flops_counted": f"slice-product flops ({pairs} 16-bit products per FP64 product) "
+                         "over the useful output entries and K ranges, per launch (average)",
     }
     ms_f, cnt_f, _, by_f = prof["fill"]
     fill = {"achieved_gbs": (by_f / (ms_f / 1e3) / 1e9) if ms_f > 0 else None,
@@ -345,12 +397,14 @@ def run_ours(args, rank, world, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64 + bf16 slices (fp32 accumulate)" if prec == "mixed_bf16" else "f64",
+        "dtype": {"mixed_f16": "f64 + fp16 slices (fp32 accumulate)",
+                  "emu_fp64": "f64 + bf16 integer slices (fp32 accumulate)"}.get(prec, "f64"),
         "data": "synthetic", "config": workload_config(n, prec), "clocks": clk,
         "e2e": e2e, "gpu_launches": int(launches), "launches_before_timed": int(launches0),
         "roofline": roofline, "fill": fill,
         "result": {"loglik": float(res[0]), "logdet": float(res[1]), "quad": float(res[2]),
                    "refine_resid": float(res[3]), "grad": [float(v) for v in g_res]},
+        "error": err,
         "loglik_grad_alg_tflops": n ** 3 / (elapsed_ms / args.steps / 1e3) / 1e12,
         "per_step_ms": {c: prof[c][0] / args.steps for c in prof},
         "cholesky_alg_flop": chol_alg,
@@ -365,6 +419,42 @@ def run_ours(args, rank, world, local):
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+    return 0
+
+
+def run_accuracy(args):
+    """Errors of the mixed and FP64-grade forms against the FP64 path (config-3
+    recipe, y = L z with the FP64 factor), one JSON line per n and form."""
+    import numpy as np
+    import torch
+
+    from paper_1305_4886_gb300 import gp, inputs
+
+    for n in [int(v) for v in args.accuracy.split(",")]:
+        p = inputs.config3(n)
+        x = torch.as_tensor(p.x, device="cuda")
+        z = torch.as_tensor(p.z, device="cuda")
+        np_ = gp.gp_padded_order(n)
+        ws = gp.workspace(n, "fp64", want_grad=True)
+        gp.loglik(x, z, p.kernel, p.s2, p.rho, p.tau2, precision="fp64", ws=ws)
+        y = torch.empty_like(z)
+        gp.gp_mult_chol(gp.factor_view(ws, n).reshape(-1), n, np_, z, y)
+        ref = gp.loglik_grad(x, y, p.kernel, p.s2, p.rho, p.tau2, precision="fp64", ws=ws)
+        ro, rg, ra = (ref["out"].cpu().numpy(), ref["grad"].cpu().numpy(),
+                      ref["alpha"].cpu().numpy())
+        del ws, ref
+        torch.cuda.empty_cache()
+        for prec in ["mixed_f16", "emu_fp64"]:
+            r = gp.loglik_grad(x, y, p.kernel, p.s2, p.rho, p.tau2, precision=prec)
+            o, g, a = r["out"].cpu().numpy(), r["grad"].cpu().numpy(), r["alpha"].cpu().numpy()
+            del r
+            torch.cuda.empty_cache()
+            print(json.dumps({"n": n, "precision": prec, "against": "fp64",
+                              "loglik_rel": float(abs(o[0] - ro[0]) / abs(ro[0])),
+                              "logdet_rel": float(abs(o[1] - ro[1]) / abs(ro[1])),
+                              "grad_rel_inf": float(np.max(np.abs(g - rg)) / np.max(np.abs(rg))),
+                              "alpha_rel": float(np.linalg.norm(a - ra) / np.linalg.norm(ra))}),
+                  flush=True)
     return 0
 
 
@@ -440,7 +530,7 @@ def run_batched(args, rank, world, local):
             "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64 + bf16 slices"
-            if prec == "mixed_bf16" else "f64", "data": "synthetic",
+            if prec == "mixed_f16" else "f64", "data": "synthetic",
             "config": {"workload": "512 independent GPs, n log-uniform [256, 4096], 2-D uniform "
                                    "locations, exp / Matern 3/2 alternating, y = L z",
                        "precision": prec, "seed": 48865, "graph": "one CUDA graph per step"},
@@ -458,6 +548,8 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.accuracy:
+        return run_accuracy(args) if rank == 0 else 0
     if args.workload == "batched":
         return run_batched(args, rank, world, local)
     return run_ours(args, rank, world, local)

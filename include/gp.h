@@ -68,13 +68,23 @@ typedef enum { GP_KERNEL_EXP = 0, GP_KERNEL_MATERN32 = 1, GP_KERNEL_MATERN52 = 2
 
 /* Arithmetic of the factorisation.
  *   GP_FP64        every step in FP64 on the CUDA cores.
- *   GP_MIXED_BF16  FP64 diagonal blocks, pivots, log-determinant and
- *                  residuals; the off-diagonal panel solve and the trailing
- *                  SYRK/GEMM updates run on the tcgen05 tensor cores on
- *                  BF16 slices of the FP64 operands (a 3-slice split,
- *                  FP32 accumulation), followed by iterative refinement of
- *                  alpha against a matrix-free FP64 residual.            */
-typedef enum { GP_FP64 = 0, GP_MIXED_BF16 = 1 } gp_precision;
+ *   GP_MIXED_F16  the mixed form: FP64 diagonal blocks, pivots,
+ *                  log-determinant and residuals; the off-diagonal panel
+ *                  solve, the trailing SYRK updates and the gradient's
+ *                  inverse run on the tcgen05 tensor cores over three
+ *                  16-bit slices of each FP64 operand row (an integer
+ *                  leading slice on the row's grid plus two FP16
+ *                  remainders, about 32 bits; 6 slice products, FP32
+ *                  accumulation with the leading products exact), pending
+ *                  trailing updates kept as FP32 pairs (double-float),
+ *                  followed by iterative refinement of alpha against a
+ *                  matrix-free FP64 residual.
+ *   GP_EMU_FP64    the same structure with FP64-grade contractions: five
+ *                  integer-valued BF16 slices per operand row (40 bits),
+ *                  15 slice products, the three leading product groups
+ *                  accumulated exactly in their own FP32 accumulators.
+ *                  About 2.5x the tensor work of GP_MIXED_F16.            */
+typedef enum { GP_FP64 = 0, GP_MIXED_F16 = 1, GP_EMU_FP64 = 2 } gp_precision;
 
 typedef struct {
     int32_t kernel; /* gp_kernel */
@@ -131,8 +141,8 @@ int gp_mult_chol(const double *d_L, int64_t n, int64_t ldc, const double *d_z, d
 
 /* Log-likelihood (Sec. 1, Sec. 2.2.2).  d_mu: n values or NULL (zero mean).
  * d_out[0..3] = {loglik, logdet, q, refinement residual}; the last is
- * ||r - C alpha||_2 / ||r||_2 after refinement in GP_MIXED_BF16, and 0 in
- * GP_FP64.  d_alpha: n values or NULL; receives C^{-1}(y - mu).  d_ws:
+ * ||r - C alpha||_2 / ||r||_2 after refinement in the tensor-core forms,
+ * and 0 in GP_FP64.  d_alpha: n values or NULL; receives C^{-1}(y - mu).  d_ws:
  * gp_workspace_bytes(n, precision, 0); on return its first n_p^2 doubles
  * hold L.                                                                  */
 int gp_loglik(const double *d_x, const double *d_y, const double *d_mu, int64_t n,
@@ -144,8 +154,9 @@ int gp_loglik(const double *d_x, const double *d_y, const double *d_mu, int64_t 
  * d loglik / d(log sigma2, log rho, log tau2), computed as
  *   sum_{i,k} Cbar_ik (dC/dtheta_j)_ik,  Cbar = (alpha alpha^T - C^{-1}) / 2,
  * with C^{-1} formed in place from the factor (blocked TRTRI + LAUUM) and
- * dC/dtheta recomputed tile by tile from the locations.  In GP_MIXED_BF16
- * the inverse's contractions use the tensor cores like the factorisation.
+ * dC/dtheta recomputed tile by tile from the locations.  In the tensor-core
+ * forms the inverse's contractions use the tensor cores like the
+ * factorisation.
  * d_ws: gp_workspace_bytes(n, precision, 1); on return its first n_p^2
  * doubles hold the lower triangle of C^{-1}.                               */
 int gp_loglik_grad(const double *d_x, const double *d_y, const double *d_mu, int64_t n,
@@ -200,9 +211,9 @@ int gp_loglik_noalloc(const double *d_x, const double *d_y, const double *d_mu, 
 /* One trailing update of the block Cholesky (Sec. 2.1, the matrix
  * multiplication and subtraction that carries most of the work), on its
  * own:  C -= P P^T on the lower triangle of the m x m block d_C (ldc),
- * with P the m x k block d_P (column-major, ldp).  GP_MIXED_BF16 runs it on
- * the tcgen05 tensor cores over BF16 slices (FP32 accumulation); GP_FP64 on
- * the CUDA cores.  d_ws: gp_syrk_workspace_bytes (0 for GP_FP64).  d_info
+ * with P the m x k block d_P (column-major, ldp).  The tensor-core forms
+ * run it on tcgen05 over 16-bit slices (FP32 accumulation, one contraction
+ * per 512-deep chunk of k added in FP64); GP_FP64 on the CUDA cores.  d_ws: gp_syrk_workspace_bytes (0 for GP_FP64).  d_info
  * (nullable) receives -1 if a bounded device wait gave up.                */
 size_t gp_syrk_workspace_bytes(int64_t m, int64_t k, int precision);
 int gp_syrk_lower(double *d_C, int64_t ldc, const double *d_P, int64_t ldp, int64_t m, int64_t k,
@@ -214,7 +225,7 @@ int gp_syrk_lower(double *d_C, int64_t ldc, const double *d_P, int64_t ldp, int6
 int64_t gp_launch_count(void);
 
 /* Kernel classes timed by the optional profiler. */
-#define GP_PROF_CONTRACT 0 /* tcgen05 BF16-slice contraction (Cholesky update,
+#define GP_PROF_CONTRACT 0 /* tcgen05 slice contraction (Cholesky update,
                               panel solve, inverse); flops = slice products */
 #define GP_PROF_FILL 1     /* covariance fill; bytes = lower-triangle FP64 */
 #define GP_PROF_RESIDUAL 2 /* matrix-free refinement residual */
@@ -223,8 +234,9 @@ int64_t gp_launch_count(void);
                               whole matrix in GP_FP64); flops = nb^3/3 */
 #define GP_PROF_DIAGINV 5  /* FP64 inverse of a diagonal block; flops = nb^3/3 */
 #define GP_PROF_SOLVE 6    /* triangular solves; bytes = 8 per lower entry read */
-#define GP_PROF_PACK 7     /* FP64 -> BF16 slice packing */
-#define GP_PROF_FOLD 8     /* FP32 pending-update fold into the FP64 block column */
+#define GP_PROF_PACK 7     /* FP64 -> 16-bit slice packing */
+#define GP_PROF_FOLD 8     /* double-float pending-update fold into the FP64
+                              block column */
 
 /* gp_prof_enable(1) clears the counters and brackets each later launch of
  * the classes above with a pair of CUDA events recorded on the launch's own

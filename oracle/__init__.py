@@ -6,6 +6,7 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline legs of
 from .gp_oracle import (  # noqa: F401
     build,
     cov_fill,
+    cov_rows,
     dcov_dlogrho,
     cholesky,
     forward,

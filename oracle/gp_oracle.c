@@ -129,6 +129,20 @@ void orc_cov_fill(const double *x, int64_t n, int kind, double s2, double rho,
     }
 }
 
+/* Selected rows of C(theta): out[r * n + j] = C[rows[r], j] (same definition
+ * as orc_cov_fill), for checks at sizes where the full matrix is too big. */
+void orc_cov_rows(const double *x, int64_t n, const int64_t *rows, int64_t nrows, int kind,
+                  double s2, double rho, double tau2, double *out) {
+#pragma omp parallel for schedule(static)
+    for (int64_t r = 0; r < nrows; ++r) {
+        const int64_t i = rows[r];
+        for (int64_t j = 0; j < n; ++j) {
+            if (i == j) out[r * n + j] = s2 + tau2;
+            else out[r * n + j] = s2 * orc_kernel(kind, dist2d(x, i, j) / rho);
+        }
+    }
+}
+
 /* dC/dlog(rho): full symmetric, zero diagonal */
 void orc_dcov_dlogrho(const double *x, int64_t n, int kind, double s2, double rho,
                       double *D) {

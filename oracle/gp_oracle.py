@@ -65,6 +65,7 @@ def _load():
             lib.orc_kernel_dlogrho.restype = d
             lib.orc_cov_fill.argtypes = [p, i64, ci, d, d, d, p]
             lib.orc_dcov_dlogrho.argtypes = [p, i64, ci, d, d, p]
+            lib.orc_cov_rows.argtypes = [p, i64, p, i64, ci, d, d, d, p]
             lib.orc_cholesky.argtypes = [p, i64]
             lib.orc_cholesky.restype = i64
             lib.orc_forward.argtypes = [p, i64, p, p]
@@ -120,6 +121,17 @@ def cov_fill(x, kernel, s2, rho, tau2):
     C = np.empty((n, n))
     _load().orc_cov_fill(_ptr(x), n, _kind(kernel), s2, rho, tau2, _ptr(C))
     return C
+
+
+def cov_rows(x, rows, kernel, s2, rho, tau2):
+    """Rows `rows` of C(theta), shape (len(rows), n)."""
+    x = _f64(x)
+    n = x.shape[0]
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    out = np.empty((rows.size, n))
+    _load().orc_cov_rows(_ptr(x), n, _ptr(rows), rows.size, _kind(kernel), s2, rho, tau2,
+                         _ptr(out))
+    return out
 
 
 def dcov_dlogrho(x, kernel, s2, rho):

@@ -27,7 +27,7 @@ class GPLogLik(torch.autograd.Function):
         return grad_out * g, None, None, None, None, None, None
 
 
-def gp_marginal_loglik(theta, x, y, kernel="matern32", precision="mixed_bf16", mu=None, ws=None):
+def gp_marginal_loglik(theta, x, y, kernel="matern32", precision="mixed_f16", mu=None, ws=None):
     """Differentiable log-likelihood: theta = (log sigma2, log rho, log tau2).
     Pass a workspace from gp.workspace(n, precision, want_grad=True) to reuse
     device memory across calls."""

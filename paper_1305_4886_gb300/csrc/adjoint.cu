@@ -30,13 +30,18 @@ namespace gp {
 
 constexpr int64_t GNB = 512;  // block rows of TRTRI / LAUUM
 
-// A packed operand store: [S][rows][kld] BF16 slices, or [rows][kld] FP64.
+// A packed operand store: [S][rows][kld] 16-bit slices (plus, for three
+// slices, the row exponents [rows][kld / 512]), or [rows][kld] FP64.
 struct Store {
     void *p = nullptr;
+    int *ex = nullptr;
     int64_t rows = 0, kld = 0;
     int f64 = 0;
     int S = 3;
-    size_t bytes() const { return (size_t)rows * kld * (f64 ? 8 : 2 * S); }
+    size_t slice_bytes() const { return (size_t)rows * kld * (f64 ? 8 : 2 * S); }
+    size_t ex_bytes() const {
+        return (f64 || S != 3) ? 0 : sizeof(int) * (size_t)rows * tc_ex_ld(kld);
+    }
 };
 
 // FP64 pack: dst[(row_off + r) kld + k_off + k] = op(r, k) (see split_rows).
@@ -80,14 +85,14 @@ static int pack(const Store &st, const double *src, int64_t ld, int64_t R, int64
         return GP_OK;
     }
     return split_rows(src, ld, R, K, Kvalid, trans, diag_off, lower_mask, st.S,
-                      static_cast<__nv_bfloat16 *>(st.p), st.rows, st.kld, row_off, k_off, s);
+                      static_cast<uint16_t *>(st.p), st.ex, st.rows, st.kld, row_off, k_off, s);
 }
 
 // C (M x N, FP64) = beta C + alpha A[a_row.., a_k..] B[b_row.., b_k..]^T over K.
 static int contract(const Store &A, int64_t a_row, int64_t a_k, const Store &B, int64_t b_row,
                     int64_t b_k, int64_t M, int64_t N, int64_t K, double alpha, double beta,
                     double *C, int64_t ldc, int lower, int64_t diag_off, int tri_k,
-                    int64_t tri_off, int64_t *info, cudaStream_t s) {
+                    int64_t tri_off, void *acc2, int64_t *info, cudaStream_t s) {
     if (M <= 0 || N <= 0 || K <= 0) return GP_OK;
     if (A.f64) {
         const double *a = static_cast<const double *>(A.p) + a_row * A.kld + a_k;
@@ -95,9 +100,11 @@ static int contract(const Store &A, int64_t a_row, int64_t a_k, const Store &B, 
         F64Mask m{lower, diag_off, tri_k, tri_off, 0};
         return gemm_f64_ex(M, N, K, alpha, a, A.kld, 1, b, B.kld, 0, beta, C, ldc, 0, m, info, s);
     }
-    TcOperand ta{static_cast<const __nv_bfloat16 *>(A.p), A.rows, A.kld, A.S, a_row, a_k};
-    TcOperand tb{static_cast<const __nv_bfloat16 *>(B.p), B.rows, B.kld, B.S, b_row, b_k};
-    TcOut o{C, ldc, 0, alpha, beta, lower, diag_off};
+    TcOperand ta{static_cast<const uint16_t *>(A.p), A.rows, A.kld, A.S, a_row, a_k,
+                 A.ex, tc_ex_ld(A.kld)};
+    TcOperand tb{static_cast<const uint16_t *>(B.p), B.rows, B.kld, B.S, b_row, b_k,
+                 B.ex, tc_ex_ld(B.kld)};
+    TcOut o{C, ldc, 0, alpha, beta, lower, diag_off, acc2};
     return tc_gemm(ta, tb, M, N, K, o, tri_k, tri_off, info, s);
 }
 
@@ -112,6 +119,7 @@ __global__ void copy_lower_kernel(const double *src, int64_t lds, double *dst, i
 struct GradWs {
     Store XT, SArow, SW, ST;
     double *T = nullptr, *Wd = nullptr, *tmp = nullptr, *part = nullptr;
+    void *acc2 = nullptr;  // GNB x np double-float chunk accumulator (tensor path)
     size_t bytes = 0;
 };
 
@@ -139,7 +147,8 @@ static GradWs grad_layout(void *base, int64_t np, int precision, int S) {
         st.kld = kld;
         st.f64 = f64;
         st.S = S;
-        st.p = take(st.bytes());
+        st.p = take(st.slice_bytes());
+        if (st.ex_bytes()) st.ex = reinterpret_cast<int *>(take(st.ex_bytes()));
         return st;
     };
     const int64_t kldp = round_up(np, 64);
@@ -151,6 +160,7 @@ static GradWs grad_layout(void *base, int64_t np, int precision, int S) {
     w.Wd = reinterpret_cast<double *>(take(sizeof(double) * GNB * GNB));
     w.tmp = reinterpret_cast<double *>(take(sizeof(double) * TB * GNB));
     w.part = reinterpret_cast<double *>(take(sizeof(double) * 3 * (size_t)ntiles64(np)));
+    if (!f64) w.acc2 = take(sizeof(float) * 2 * GNB * (size_t)np);
     w.bytes = a256(off);
     return w;
 }
@@ -172,12 +182,12 @@ static int trtri_inplace(double *A, int64_t ld, int64_t np, GradWs &w, int64_t *
             // T (nb x k0) = L[k, 0:k0] X[0:k0, 0:k0]
             GP_TRY(pack(w.SArow, A + k0, ld, nb, k0, k0, 0, 0, 0, 0, 0, s));
             GP_TRY(contract(w.SArow, 0, 0, w.XT, 0, 0, nb, k0, k0, 1.0, 0.0, w.T, nb, 0, 0, 1, 0,
-                            info, s));
+                            w.acc2, info, s));
             // X[k, 0:k0] = -X_kk T
             GP_TRY(pack(w.SW, w.Wd, nb, nb, nb, nb, 0, 0, 1, 0, 0, s));
             GP_TRY(pack(w.ST, w.T, nb, k0, nb, nb, 1, 0, 0, 0, 0, s));
             GP_TRY(contract(w.SW, 0, 0, w.ST, 0, 0, nb, k0, nb, -1.0, 0.0, A + k0, ld, 0, 0, 0, 0,
-                            info, s));
+                            w.acc2, info, s));
         }
         copy_lower_kernel<<<dim3(1, (unsigned)nb), 256, 0, s>>>(w.Wd, nb, Akk, ld, nb, info);
         GP_LAUNCH_CHECK();
@@ -194,7 +204,7 @@ static int lauum_inplace(double *A, int64_t ld, int64_t np, GradWs &w, int64_t *
         const int64_t nb = (np - i0) < GNB ? (np - i0) : GNB;
         const int64_t K = np - i0;
         GP_TRY(contract(w.XT, i0, i0, w.XT, 0, i0, nb, i0 + nb, K, 1.0, 0.0, A + i0, ld, 1, i0, 0, 0,
-                        info, s));
+                        w.acc2, info, s));
     }
     return GP_OK;
 }

@@ -37,18 +37,20 @@ static bool params_ok(const gp_params *p) {
     return true;
 }
 
-static bool precision_ok(int p) { return p == GP_FP64 || p == GP_MIXED_BF16; }
+static bool precision_ok(int p) { return p == GP_FP64 || p == GP_MIXED_F16 || p == GP_EMU_FP64; }
 
 int64_t padded(int64_t n) { return n < 1 ? 0 : round_up(n, PAD); }
 
-constexpr int MIXED_SLICES = 3;      // BF16 slices per FP64 operand (6 slice products)
+// BF16 slices per FP64 operand: 3 in the mixed form (6 slice products), 5
+// integer slices in the FP64-grade emulation (15 products).
+static int slices_of(int precision) { return precision == GP_EMU_FP64 ? 5 : 3; }
 constexpr int REFINE_EVALS = 4;      // residual evaluations of the mixed refinement
 constexpr double REFINE_TOL = 1e-11; // ||r - C alpha|| / ||r|| target
 
 // Workspace of the factorisation (beyond the matrix itself).
 static size_t chol_ws_bytes(int64_t np, int precision) {
     if (precision == GP_FP64) return 0;
-    return chol_mixed_ws_bytes(np, MIXED_SLICES);
+    return chol_mixed_ws_bytes(np, slices_of(precision));
 }
 
 struct LoglikWs {
@@ -78,7 +80,7 @@ static LoglikWs loglik_ws_layout(void *base, int64_t n, int precision, int want_
     w.tsync = c.take<int>(trsv_sync_ints(np));
     size_t cb = chol_ws_bytes(np, precision);
     if (want_grad) {  // the inverse and contraction reuse the factorisation's scratch
-        size_t gb = grad_ws_bytes(np, precision, MIXED_SLICES);
+        size_t gb = grad_ws_bytes(np, precision, slices_of(precision));
         cb = cb > gb ? cb : gb;
     }
     w.chol = c.take<char>(cb);
@@ -94,7 +96,8 @@ static int run_chol(double *A, int64_t np, int64_t ld, int precision, void *ws, 
         prof_stop(ev, s, GP_PROF_DIAG, (double)np * np * np / 3.0, 0.0);
         return GP_OK;
     }
-    if (precision == GP_MIXED_BF16) return chol_mixed(A, ld, np, MIXED_SLICES, ws, info, s);
+    if (precision == GP_MIXED_F16 || precision == GP_EMU_FP64)
+        return chol_mixed(A, ld, np, slices_of(precision), ws, info, s);
     return GP_ERR_INVALID;
 }
 
@@ -223,8 +226,8 @@ int gp_loglik_grad(const double *d_x, const double *d_y, const double *d_mu, int
     const int64_t np = padded(n);
     KernParams kp = make_kern(*prm);
     GP_TRY(loglik_core(d_x, d_y, d_mu, n, kp, precision, w, d_out, d_info, s));
-    GP_TRY(chol_inverse(w.A, np, np, precision, MIXED_SLICES, w.chol, d_info, s));
-    GP_TRY(grad_contract(d_x, n, np, kp, w.A, np, w.v, w.chol, precision, MIXED_SLICES, d_grad,
+    GP_TRY(chol_inverse(w.A, np, np, precision, slices_of(precision), w.chol, d_info, s));
+    GP_TRY(grad_contract(d_x, n, np, kp, w.A, np, w.v, w.chol, precision, slices_of(precision), d_grad,
                          d_info, s));
     if (d_alpha &&
         cudaMemcpyAsync(d_alpha, w.v, sizeof(double) * n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
@@ -338,10 +341,10 @@ int gp_loglik_grad_batched(int nprob, const int64_t *h_n, const double *const *h
             int st = loglik_core(h_dx[i], h_dy[i], mu, n, kp, precision, w, d_out + 4 * i,
                                  d_info + i, sk);
             if (st == GP_OK)
-                st = chol_inverse(w.A, np, np, precision, MIXED_SLICES, w.chol, d_info + i, sk);
+                st = chol_inverse(w.A, np, np, precision, slices_of(precision), w.chol, d_info + i, sk);
             if (st == GP_OK)
                 st = grad_contract(h_dx[i], n, np, kp, w.A, np, w.v, w.chol, precision,
-                                   MIXED_SLICES, d_grad + 3 * i, d_info + i, sk);
+                                   slices_of(precision), d_grad + 3 * i, d_info + i, sk);
             if (st != GP_OK && status == GP_OK) status = st;
         }
         // join even after a launch error, so that the caller's stream stays ordered
@@ -354,18 +357,18 @@ int gp_loglik_grad_batched(int nprob, const int64_t *h_n, const double *const *h
 
 size_t gp_syrk_workspace_bytes(int64_t m, int64_t k, int precision) {
     if (m < 1 || k < 1 || !precision_ok(precision)) return 0;
-    return syrk_ws_bytes(m, k, precision, MIXED_SLICES);
+    return syrk_ws_bytes(m, k, precision, slices_of(precision));
 }
 
 int gp_syrk_lower(double *d_C, int64_t ldc, const double *d_P, int64_t ldp, int64_t m, int64_t k,
                   int precision, void *d_ws, size_t ws_bytes, int64_t *d_info, void *stream) {
     if (m < 1 || k < 1 || !d_C || !d_P || ldc < m || ldp < m || !precision_ok(precision))
         return GP_ERR_INVALID;
-    size_t need = syrk_ws_bytes(m, k, precision, MIXED_SLICES);
+    size_t need = syrk_ws_bytes(m, k, precision, slices_of(precision));
     if (need > 0 && (!d_ws || ws_bytes < need)) return GP_ERR_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
     if (d_info && cudaMemsetAsync(d_info, 0, sizeof(int64_t), s) != cudaSuccess) return GP_ERR_CUDA;
-    return syrk_lower(d_C, ldc, d_P, ldp, m, k, precision, MIXED_SLICES, d_ws, d_info, s);
+    return syrk_lower(d_C, ldc, d_P, ldp, m, k, precision, slices_of(precision), d_ws, d_info, s);
 }
 
 }  // extern "C"

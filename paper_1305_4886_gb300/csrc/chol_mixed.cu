@@ -2,21 +2,24 @@
 // Sec. 2.1 with the two levels of blocking of Sec. 2.2).
 //
 // Outer blocks of NB = 512 columns.  The matrix stays FP64 (the fill's C);
-// trailing updates accumulate in a separate FP32 array D that is folded into
-// the FP64 matrix one block column at a time, just before that column is
-// factored, so the FP64 pipe touches each entry once instead of once per
-// outer step.  Per outer block column k:
-//   1. A[k:, k] += D[k:, k]   (FP64 += FP32, the block column only)
+// trailing updates accumulate in a separate double-float array D (FP32
+// pairs hi + lo, about 48 significant bits, updated with FP32 error-free
+// sums) that is folded into the FP64 matrix one block column at a time, just
+// before that column is factored, so the FP64 pipe (1/64 of the FP32 rate on
+// this part) touches each entry once instead of once per outer step.  An
+// FP32 D would round every pending entry once per outer step, a relative
+// error growing like 2^-24 sqrt(n / NB).  Per outer block column k:
+//   1. A[k:, k] += D[k:, k]   (FP64 += hi + lo, the block column only)
 //   2. FP64 tiled Cholesky of the NB x NB diagonal block      -- FP64
 //   3. W = L_kk^{-1}, blocked FP64 triangular inversion        -- FP64
 //   4. panel solve L_ik = A_ik W^T: one tensor-core contraction over row-
 //      scaled BF16 slices of A_ik and W (the forward-solves of Sec. 2.1),
 //      written to the FP64 matrix
 //   5. trailing update D_ij -= L_ik L_jk^T on the lower triangle, tensor
-//      cores, FP32 accumulation into D ("most of the total work is in the
-//      matrix multiplications", Sec. 2.1).
+//      cores, double-float accumulation into D ("most of the total work is
+//      in the matrix multiplications", Sec. 2.1).
 // The pivots and hence the log-determinant come from FP64 factorisations of
-// blocks that carry FP32-accurate updates.
+// blocks whose updates carry the slice products' accuracy.
 #include "internal.h"
 #include "tc_gemm.h"
 
@@ -27,9 +30,10 @@ constexpr int64_t NB = 512;
 struct MixedWs {
     double *W = nullptr;            // NB x NB, inverse of the diagonal block
     double *tmp = nullptr;          // 64 x NB
-    __nv_bfloat16 *SA = nullptr;    // S x np x NB  panel slices
-    __nv_bfloat16 *SB = nullptr;    // S x NB x NB  inverse slices
-    float *D = nullptr;             // np x np pending trailing updates
+    uint16_t *SA = nullptr;         // S x np x NB  panel slices
+    uint16_t *SB = nullptr;         // S x NB x NB  inverse slices
+    int *exA = nullptr, *exB = nullptr;  // their row exponents (three-slice form)
+    float2 *D = nullptr;            // np x np pending trailing updates (double-float)
     size_t bytes = 0;
 };
 
@@ -47,28 +51,33 @@ static MixedWs mixed_layout(void *base, int64_t np, int S) {
     };
     w.W = reinterpret_cast<double *>(take(sizeof(double) * NB * NB));
     w.tmp = reinterpret_cast<double *>(take(sizeof(double) * TB * NB));
-    w.SA = reinterpret_cast<__nv_bfloat16 *>(take(2ull * S * (size_t)np * NB));
-    w.SB = reinterpret_cast<__nv_bfloat16 *>(take(2ull * S * NB * NB));
-    w.D = reinterpret_cast<float *>(take(sizeof(float) * (size_t)np * (size_t)np));
+    w.SA = reinterpret_cast<uint16_t *>(take(2ull * S * (size_t)np * NB));
+    w.SB = reinterpret_cast<uint16_t *>(take(2ull * S * NB * NB));
+    w.exA = reinterpret_cast<int *>(take(sizeof(int) * (size_t)np * tc_ex_ld(NB)));
+    w.exB = reinterpret_cast<int *>(take(sizeof(int) * NB * tc_ex_ld(NB)));
+    w.D = reinterpret_cast<float2 *>(take(sizeof(float2) * (size_t)np * (size_t)np));
     w.bytes = align256(off);
     return w;
 }
 
 size_t chol_mixed_ws_bytes(int64_t np, int S) { return mixed_layout(nullptr, np, S).bytes; }
 
-// A[r, c] += D[r, c] for the lower part of a block column (rows >= c).
-__global__ void fold_delta_kernel(double *A, int64_t ld, const float *D, int64_t ldd, int64_t rows,
-                                  int64_t cols, const int64_t *info) {
+// A[r, c] += D.hi[r, c] + D.lo[r, c] (double-float pending updates).
+__global__ void fold_delta2_kernel(double *A, int64_t ld, const float2 *D, int64_t ldd,
+                                   int64_t rows, int64_t cols, const int64_t *info) {
     if (failed(info)) return;
     const int64_t c = blockIdx.y;
     for (int64_t r = c + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows;
-         r += (int64_t)gridDim.x * blockDim.x)
-        A[r + c * ld] += static_cast<double>(D[r + c * ldd]);
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const float2 d = D[r + c * ldd];
+        A[r + c * ld] += static_cast<double>(d.x) + static_cast<double>(d.y);
+    }
 }
 
 int chol_mixed(double *A, int64_t ld, int64_t np, int S, void *ws, int64_t *info, cudaStream_t s) {
     MixedWs w = mixed_layout(ws, np, S);
-    if (cudaMemsetAsync(w.D, 0, sizeof(float) * (size_t)np * (size_t)np, s) != cudaSuccess)
+    if (cudaMemsetAsync(w.D, 0, sizeof(float2) * (size_t)np * (size_t)np, s) !=
+        cudaSuccess)
         return GP_ERR_CUDA;
     for (int64_t k0 = 0; k0 < np; k0 += NB) {
         const int64_t nb = (np - k0) < NB ? (np - k0) : NB;
@@ -77,9 +86,9 @@ int chol_mixed(double *A, int64_t ld, int64_t np, int S, void *ws, int64_t *info
         if (k0 > 0) {
             dim3 g((unsigned)ceil_div(rows, 256 * 4) + 1, (unsigned)nb);
             const int ev = prof_start(s);
-            fold_delta_kernel<<<g, 256, 0, s>>>(Akk, ld, w.D + k0 + k0 * np, np, rows, nb, info);
+            fold_delta2_kernel<<<g, 256, 0, s>>>(Akk, ld, w.D + k0 + k0 * np, np, rows, nb, info);
             GP_LAUNCH_CHECK();
-            prof_stop(ev, s, GP_PROF_FOLD, 0.0, 12.0 * (double)rows * nb);
+            prof_stop(ev, s, GP_PROF_FOLD, 0.0, 16.0 * (double)rows * nb);
         }
         int ev = prof_start(s);
         GP_TRY(chol_fp64_tiled(Akk, ld, nb, k0, info, s));
@@ -90,17 +99,17 @@ int chol_mixed(double *A, int64_t ld, int64_t np, int S, void *ws, int64_t *info
         ev = prof_start(s);
         GP_TRY(trtri_fp64_blocked(Akk, ld, nb, w.W, nb, w.tmp, info, s));
         prof_stop(ev, s, GP_PROF_DIAGINV, (double)nb * nb * nb / 3.0, 0.0);
-        GP_TRY(split_rows(w.W, nb, nb, nb, nb, 0, 0, 1, S, w.SB, NB, NB, 0, 0, s));
-        GP_TRY(split_rows(P, ld, m, nb, nb, 0, 0, 0, S, w.SA, np, NB, 0, 0, s));
-        TcOperand opA{w.SA, np, NB, S, 0, 0};
-        TcOperand opW{w.SB, NB, NB, S, 0, 0};
+        int *exA = S == 3 ? w.exA : nullptr, *exB = S == 3 ? w.exB : nullptr;
+        GP_TRY(split_rows(w.W, nb, nb, nb, nb, 0, 0, 1, S, w.SB, exB, NB, NB, 0, 0, s));
+        GP_TRY(split_rows(P, ld, m, nb, nb, 0, 0, 0, S, w.SA, exA, np, NB, 0, 0, s));
+        TcOperand opA{w.SA, np, NB, S, 0, 0, exA, tc_ex_ld(NB)};
+        TcOperand opW{w.SB, NB, NB, S, 0, 0, exB, tc_ex_ld(NB)};
         // L_ik = A_ik W^T  (FP64 out)
         TcOut o1{P, ld, 0, 1.0, 0.0, 0, 0};
         GP_TRY(tc_gemm(opA, opW, m, nb, nb, o1, 0, 0, info, s));
-        GP_TRY(split_rows(P, ld, m, nb, nb, 0, 0, 0, S, w.SA, np, NB, 0, 0, s));
-        // D_22 -= L_ik L_ik^T (lower, FP32)
-        float *D22 = w.D + (k0 + nb) + (k0 + nb) * np;
-        TcOut o2{D22, np, 1, -1.0, 0.0, 1, 0};
+        GP_TRY(split_rows(P, ld, m, nb, nb, 0, 0, 0, S, w.SA, exA, np, NB, 0, 0, s));
+        // D_22 -= L_ik L_ik^T (lower, double-float)
+        TcOut o2{w.D + (k0 + nb) + (k0 + nb) * np, np, 2, -1.0, 0.0, 1, 0};
         GP_TRY(tc_gemm(opA, opA, m, m, nb, o2, 0, 0, info, s));
     }
     return GP_OK;
@@ -111,19 +120,29 @@ int chol_mixed(double *A, int64_t ld, int64_t np, int S, void *ws, int64_t *info
 // ---------------------------------------------------------------------------
 size_t syrk_ws_bytes(int64_t m, int64_t k, int precision, int S) {
     if (precision == GP_FP64) return 0;
-    return align256(2ull * S * (size_t)m * (size_t)round_up(k, 64));
+    const int64_t kp = round_up(k, 64);
+    return align256(2ull * S * (size_t)m * (size_t)kp) +
+           align256(sizeof(int) * (size_t)m * tc_ex_ld(kp));
 }
 
 int syrk_lower(double *C, int64_t ldc, const double *P, int64_t ldp, int64_t m, int64_t k,
                int precision, int S, void *ws, int64_t *info, cudaStream_t s) {
     if (precision == GP_FP64)
         return gemm_f64(m, m, k, -1.0, P, ldp, 0, P, ldp, 1, 1.0, C, ldc, 1, info, s);
-    __nv_bfloat16 *SA = static_cast<__nv_bfloat16 *>(ws);
     const int64_t kp = round_up(k, 64);
-    GP_TRY(split_rows(P, ldp, m, kp, k, 0, 0, 0, S, SA, m, kp, 0, 0, s));
-    TcOperand op{SA, m, kp, S, 0, 0};
-    TcOut o{C, ldc, 0, -1.0, 1.0, 1, 0};
-    return tc_gemm(op, op, m, m, kp, o, 0, 0, info, s);
+    uint16_t *SA = static_cast<uint16_t *>(ws);
+    int *ex = S == 3 ? reinterpret_cast<int *>(static_cast<char *>(ws) +
+                                               align256(2ull * S * (size_t)m * (size_t)kp))
+                     : nullptr;
+    GP_TRY(split_rows(P, ldp, m, kp, k, 0, 0, 0, S, SA, ex, m, kp, 0, 0, s));
+    // one contraction per 512-deep chunk, accumulated in FP64
+    for (int64_t k0 = 0; k0 < kp; k0 += TC_CHUNK_K) {
+        const int64_t kc = (kp - k0) < TC_CHUNK_K ? (kp - k0) : TC_CHUNK_K;
+        TcOperand op{SA, m, kp, S, 0, k0, ex, tc_ex_ld(kp)};
+        TcOut o{C, ldc, 0, -1.0, 1.0, 1, 0};
+        GP_TRY(tc_gemm(op, op, m, m, kc, o, 0, 0, info, s));
+    }
+    return GP_OK;
 }
 
 }  // namespace gp

@@ -4,40 +4,51 @@
 // carried as BF16 slices.
 //
 // Operand splitting (row-scaled).  For operand row r let 2^e_r bound its
-// entries over the packed K range.  Each FP64 entry x becomes three BF16
-// slices:
-//   s0 = round(x 2^{7-e_r}) 2^{e_r-7}     an integer in [-128, 128] times a
-//                                         per-row power of two (exact in BF16)
-//   s1 = bf16(x - s0),  s2 = bf16(x - s0 - s1)
-// so x = s0 + s1 + s2 to about 2^-26 of the row's largest entry.  A product
-// sum over k is the sum of slice products s_p t_q with p + q < 3 (the
-// dropped ones are below 2^-25 of the row maxima).  The leading products
-// s0 t0 are integers times one common power of two for a given output
-// (r, c); their sums stay below 2^24 units for K <= 1024, so the FP32
-// tensor-core accumulator holds them exactly however it rounds.  They go to
-// their own accumulator ("hi"); the five smaller products share a second one
-// ("lo"), whose rounding is 2^-7 smaller.  The epilogue adds hi + lo.
+// entries over a 512-deep chunk of K.  Each FP64 entry x becomes BF16 slices
+// whose leading one is s0 = round(x 2^{7-e_r}) 2^{e_r-7}, an integer in
+// [-128, 128] times a per-row power of two (exact in BF16).
+//   Mixed form (three slices): s1 = bf16(x - s0), s2 = bf16(x - s0 - s1), so
+//   x = s0 + s1 + s2 to about 2^-26 of the row's largest entry; the slice
+//   products s_p t_q with p + q < 3 are kept (the dropped ones are below
+//   2^-25 of the row maxima).
+//   FP64-grade form (five slices): every slice is an integer q_p in
+//   [-128, 128] times 2^{e_r-7-8p}, carrying x to 2^-40 of the row bound;
+//   the 15 products with p + q < 5 are kept.
+// All products of one group d = p + q are integers times one common power of
+// two for a given output (r, c).  A group's sum is exact in an FP32
+// accumulator, however the tensor core rounds, while it stays below 2^24
+// units: for K <= 1024 in group 0, K <= 512 in group 1, and K <= 341 (in
+// practice 512) in group 2.  Exact groups get their own TMEM accumulators:
+// the mixed form has "hi" (group 0) and "lo" (groups 1, 2, rounding 2^-8
+// smaller); the FP64-grade form has groups 0, 1, 2 and a fourth accumulator
+// for groups 3 and 4 (rounding 2^-24 smaller).  The epilogue adds them in
+// FP64 or in double-float.
 //
 // Kernel.  Persistent: one CTA per SM walks a static tile schedule of
 // 128 x 128 output tiles (grouped 16 tile-rows at a time so the operand
-// tiles in flight stay in L2).  6 warps:
+// tiles in flight stay in L2).  10 warps:
 //   warp 0     TMA producer (one thread): a 6-stage ring of 32 KB stages
 //              (A and B 128 x 64 BF16 boxes, 128-byte swizzle).
-//   warp 1     TMEM owner (512 columns = 2 tile buffers x {hi, lo}) and MMA
-//              issuer (one thread): tcgen05.mma.cta_group::1.kind::f16,
-//              128 x 128 x 16 per instruction; tcgen05.commit frees stages
-//              and hands finished accumulators to the epilogue.
-//   warps 2-5  epilogue: tcgen05.ld of hi and lo (32 lanes x 32 columns),
-//              output in FP64 (C = beta C + alpha acc) or FP32 (C += alpha
-//              acc), one row per thread so that every warp access covers 32
-//              consecutive rows of one column; all loads of a 32-column chunk
-//              are issued before any store.  The two TMEM buffers let the
+//   warp 1     TMEM owner (512 columns: 2 tile buffers x {hi, lo}, or one
+//              buffer x 4 groups) and MMA issuer (one thread):
+//              tcgen05.mma.cta_group::1.kind::f16, 128 x 128 x 16 per
+//              instruction; tcgen05.commit frees stages and hands finished
+//              accumulators to the epilogue.
+//   warps 2-9  epilogue, two warps per TMEM lane quarter (32 rows x 64
+//              columns each): tcgen05.ld of the accumulators, output in FP64
+//              (C = beta C + alpha acc) or as a double-float FP32 pair (C +=
+//              alpha acc, error-free sums), one row per thread so that every
+//              warp access covers 32 consecutive rows of one column.  The
+//              previous output values are read one 8-column step ahead (the
+//              first step before the accumulators are ready), so two steps of
+//              loads are in flight per thread.  Two TMEM buffers let the
 //              epilogue of one tile overlap the MMAs of the next.
 // Every mbarrier wait is bounded (1 s); a wait that gives up sets
 // *info = -1, the roles wind down (the producer waits, bounded, for its
 // copies in flight) and TMEM is freed.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
 #include "internal.h"
@@ -56,12 +67,15 @@ constexpr int TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;
 constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024 /*barriers*/ + 1024 /*align*/;
 constexpr uint32_t TC_TMEM_COLS = 512;
 constexpr int TC_GROUP = 16;  // tile rows per scheduling group
-constexpr int TC_MAX_PAIRS = 6;
+constexpr int TC_MAX_PAIRS = 15;
+constexpr int TC_EPI_WARPS = 8;                     // two per TMEM lane quarter
+constexpr int TC_THREADS = 32 * (2 + TC_EPI_WARPS);  // producer, MMA, epilogue
 
 struct TcGemmArgs {
     void *C;
     int64_t ldc;
-    int fp32;
+    int out_mode;  // 0: FP64 C = beta C + alpha v;
+                   // 2: FP32 pair (hi, lo) C += alpha v in double-float
     double alpha, beta;
     int lower;
     int64_t diag_off;
@@ -70,9 +84,17 @@ struct TcGemmArgs {
     int kblocks;
     int tri_k;
     int64_t tri_off;
+    int kchunk;  // > 0: flush the accumulators every kchunk K-blocks (one epilogue
+                 // pass per chunk, out_mode 2 accumulates the chunks in double-float)
     int tiles_m, tiles_n;
     int npairs;
     int pa[TC_MAX_PAIRS], pb[TC_MAX_PAIRS];
+    int acc_of[TC_MAX_PAIRS];    // TMEM accumulator of each slice pair
+    int first_of[TC_MAX_PAIRS];  // pair opens its accumulator
+    int nacc, nbuf;              // accumulators per tile, tile buffers (nacc*nbuf <= 4)
+    uint32_t idesc;              // MMA instruction descriptor (FP16 or BF16 operands)
+    const int *ex_a, *ex_b;      // normalized slices: row exponents per 512-chunk, else null
+    int64_t ex_ld_a, ex_ld_b;
     int64_t *info;
 };
 
@@ -80,6 +102,26 @@ struct TileInfo {
     int tm, tn, kb_lo, kb_hi;
     bool skip;
 };
+
+// Accumulation units of a tile: one (the whole K range, even if empty) when
+// kchunk == 0, else the non-empty kchunk-aligned pieces of [kb_lo, kb_hi).
+__device__ __forceinline__ int tile_chunks(const TcGemmArgs &a, int kb_lo, int kb_hi) {
+    if (a.kchunk <= 0) return 1;
+    if (kb_lo >= kb_hi) return 0;
+    return (kb_hi - 1) / a.kchunk - kb_lo / a.kchunk + 1;
+}
+
+__device__ __forceinline__ void chunk_range(const TcGemmArgs &a, int kb_lo, int kb_hi, int c,
+                                            int &lo, int &hi) {
+    if (a.kchunk <= 0) {
+        lo = kb_lo;
+        hi = kb_hi;
+        return;
+    }
+    const int c0 = kb_lo / a.kchunk + c;
+    lo = max(kb_lo, c0 * a.kchunk);
+    hi = min(kb_hi, (c0 + 1) * a.kchunk);
+}
 
 __device__ __forceinline__ TileInfo tile_at(const TcGemmArgs &a, int t) {
     TileInfo ti;
@@ -100,7 +142,114 @@ __device__ __forceinline__ TileInfo tile_at(const TcGemmArgs &a, int t) {
     return ti;
 }
 
-__global__ void __launch_bounds__(192, 1)
+// Error-free transformations in FP32 (never contracted into FMAs).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+constexpr int TC_EG = 8;  // columns per epilogue step (two steps' loads in flight)
+
+// Previous output values (FP64 or an FP32 pair: 8 bytes either way) of one
+// row and TC_EG columns; masked entries read as 0.
+__device__ __forceinline__ void fetch_old(const TcGemmArgs &a, bool need_old, int64_t row,
+                                          bool row_ok, int64_t colb,
+                                          unsigned long long (&o)[TC_EG]) {
+    const unsigned long long *src =
+        static_cast<const unsigned long long *>(a.C) + row + colb * a.ldc;
+#pragma unroll
+    for (int j = 0; j < TC_EG; ++j) {
+        const int64_t col = colb + j;
+        const bool ok = need_old && row_ok && col < a.N && (!a.lower || row + a.diag_off >= col);
+        o[j] = ok ? src[j * a.ldc] : 0ull;
+    }
+}
+
+// One TC_EG-column step of an epilogue warp: accumulators from TMEM (column
+// tcol of the first one), previous values in old[], result written to C.
+template <int NACC>
+__device__ __forceinline__ void epilogue_group(const TcGemmArgs &args, uint32_t tcol, bool has_acc,
+                                               int64_t row, bool row_ok, int64_t colb,
+                                               float alpha_f, int ea, int ebr, int lane0,
+                                               const unsigned long long (&old)[TC_EG]) {
+    constexpr int nacc = NACC;
+    // normalized slices: this chunk's sums carry the factor 2^{e_a + e_b - 14};
+    // lane lane0 + j holds e_b of column j in ebr (a tile with no K range has
+    // zero sums and reads no exponents)
+    int ksc[TC_EG];
+#pragma unroll
+    for (int j = 0; j < TC_EG; ++j) {
+        const int eb = __shfl_sync(0xffffffffu, ebr, lane0 + j);
+        ksc[j] = (args.ex_b && has_acc) ? max(-252, min(ea + eb - 14, 252)) : 0;
+    }
+    uint32_t a0[TC_EG], a1[TC_EG], a2[TC_EG], a3[TC_EG];
+#pragma unroll
+    for (int j = 0; j < TC_EG; ++j) a0[j] = a1[j] = a2[j] = a3[j] = 0u;
+    if (has_acc) {
+        tmem_ld_32x32b_x8(tcol, a0);
+        tmem_ld_32x32b_x8(tcol + TC_BN, a1);
+        if (nacc > 2) tmem_ld_32x32b_x8(tcol + 2 * TC_BN, a2);
+        if (nacc > 3) tmem_ld_32x32b_x8(tcol + 3 * TC_BN, a3);
+        tmem_ld_wait();
+    }
+    bool okc[TC_EG];
+#pragma unroll
+    for (int j = 0; j < TC_EG; ++j) {
+        const int64_t col = colb + j;
+        okc[j] = row_ok && col < args.N && (!args.lower || row + args.diag_off >= col);
+    }
+    if (args.out_mode == 2) {
+        // double-float: v = a0 + a1 + a2 + a3 as an unevaluated pair (h, l),
+        // then C (hi, lo) += alpha v, all in FP32
+        float2 *dst = static_cast<float2 *>(args.C) + row + colb * args.ldc;
+#pragma unroll
+        for (int j = 0; j < TC_EG; ++j) {
+            const float ox = __uint_as_float(static_cast<uint32_t>(old[j]));
+            const float oy = __uint_as_float(static_cast<uint32_t>(old[j] >> 32));
+            float h, l;
+            two_sum(__uint_as_float(a0[j]), __uint_as_float(a1[j]), h, l);
+            if (nacc > 2) {
+                float m, e, l2, e2;
+                two_sum(__uint_as_float(a2[j]), __uint_as_float(a3[j]), m, e);
+                two_sum(l, m, l2, e2);
+                two_sum(h, l2, h, l);
+                l = __fadd_rn(l, __fadd_rn(e2, e));
+            }
+            // alpha 2^k in two exact power-of-two factors (|k| <= 252 fits)
+            const int k1 = ksc[j] / 2, k2 = ksc[j] - k1;
+            const float f1 = __fmul_rn(alpha_f, __int_as_float((k1 + 127) << 23));
+            const float f2 = __int_as_float((k2 + 127) << 23);
+            h = __fmul_rn(__fmul_rn(h, f1), f2);
+            l = __fmul_rn(__fmul_rn(l, f1), f2);
+            float s1, e1, hi, lo;
+            two_sum(ox, h, s1, e1);
+            e1 = __fadd_rn(e1, __fadd_rn(oy, l));
+            two_sum(s1, e1, hi, lo);
+            if (okc[j]) dst[j * args.ldc] = make_float2(hi, lo);
+        }
+    } else {
+        double *dst = static_cast<double *>(args.C) + row + colb * args.ldc;
+#pragma unroll
+        for (int j = 0; j < TC_EG; ++j) {
+            double v = static_cast<double>(__uint_as_float(a0[j])) +
+                       static_cast<double>(__uint_as_float(a1[j]));
+            if (nacc > 2)
+                v += static_cast<double>(__uint_as_float(a2[j])) +
+                     static_cast<double>(__uint_as_float(a3[j]));
+            v *= __longlong_as_double(static_cast<long long>(ksc[j] + 1023) << 52);  // 2^k, exact
+            if (args.beta != 0.0)
+                v = fma(args.beta, __longlong_as_double(static_cast<long long>(old[j])),
+                        args.alpha * v);
+            else if (args.alpha != 1.0)
+                v = args.alpha * v;
+            if (okc[j]) dst[j * args.ldc] = v;
+        }
+    }
+}
+
+template <int NACC>
+__global__ void __launch_bounds__(TC_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    TcGemmArgs args) {
     extern __shared__ uint8_t smem_raw[];
@@ -123,7 +272,7 @@ __global__ void __launch_bounds__(192, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], 4);
+            mbar_init(&tempty[b], TC_EPI_WARPS);
         }
         mbar_init(drain, 1);
         abort_flag = 0;
@@ -147,8 +296,12 @@ __global__ void __launch_bounds__(192, 1)
             const TileInfo ti = tile_at(args, t);
             if (ti.skip) continue;
             const int ra = ti.tm * TC_BM + args.a_row_off, rb = ti.tn * TC_BN + args.b_row_off;
+            const int nch = tile_chunks(args, ti.kb_lo, ti.kb_hi);
+            for (int c = 0; c < nch && ok; ++c) {
+            int clo, chi;
+            chunk_range(args, ti.kb_lo, ti.kb_hi, c, clo, chi);
             for (int p = 0; p < args.npairs && ok; ++p) {
-                for (int kb = ti.kb_lo; kb < ti.kb_hi; ++kb, ++it) {
+                for (int kb = clo; kb < chi; ++kb, ++it) {
                     const uint32_t s = it % TC_STAGES, use = it / TC_STAGES;
                     if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1)) {
                         ok = false;
@@ -165,6 +318,7 @@ __global__ void __launch_bounds__(192, 1)
                     tma_load_3d(a_s + TC_A_BYTES, &tmB, &full[s], args.b_k_off + kx, rb, args.pb[p]);
                 }
             }
+            }
         }
         if (!ok) abort_flag = 1;
         // drain: copies still in flight must land before the CTA exits
@@ -172,22 +326,26 @@ __global__ void __launch_bounds__(192, 1)
             mbar_wait(&full[j % TC_STAGES], (j / TC_STAGES) & 1);
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
-        constexpr uint32_t idesc = idesc_bf16_f32(TC_BM, TC_BN);
+        const uint32_t idesc = args.idesc;
         uint32_t it = 0, local = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
             const TileInfo ti = tile_at(args, t);
             if (ti.skip) continue;
-            const uint32_t buf = local & 1, u = local >> 1;
+            const int nch = tile_chunks(args, ti.kb_lo, ti.kb_hi);
+            for (int c = 0; c < nch && ok; ++c) {
+            int clo, chi;
+            chunk_range(args, ti.kb_lo, ti.kb_hi, c, clo, chi);
+            const uint32_t buf = local % args.nbuf, u = local / args.nbuf;
             if (u > 0 && !mbar_wait(&tempty[buf], (u - 1) & 1)) {
                 ok = false;
                 break;
             }
             tc_fence_after();
             for (int p = 0; p < args.npairs && ok; ++p) {
-                const uint32_t acc = tmem + (buf * 2 + (p > 0 ? 1 : 0)) * TC_BN;
-                const bool first_of_acc = (p <= 1);
-                for (int kb = ti.kb_lo; kb < ti.kb_hi; ++kb, ++it) {
+                const uint32_t acc = tmem + (buf * args.nacc + args.acc_of[p]) * TC_BN;
+                const bool first_of_acc = args.first_of[p] != 0;
+                for (int kb = clo; kb < chi; ++kb, ++it) {
                     const uint32_t s = it % TC_STAGES, use = it / TC_STAGES;
                     if (!mbar_wait(&full[s], use & 1)) {
                         ok = false;
@@ -198,96 +356,83 @@ __global__ void __launch_bounds__(192, 1)
                     const uint32_t b_addr = a_addr + TC_A_BYTES;
 #pragma unroll
                     for (int k = 0; k < TC_BK / 16; ++k) {
-                        const uint32_t accumulate = (first_of_acc && kb == ti.kb_lo && k == 0) ? 0u : 1u;
-                        mma_bf16_ss(acc, sdesc_sw128(a_addr + k * 32), sdesc_sw128(b_addr + k * 32),
-                                    idesc, accumulate);
+                        const uint32_t accumulate = (first_of_acc && kb == clo && k == 0) ? 0u : 1u;
+                        mma_f16_ss(acc, sdesc_sw128(a_addr + k * 32), sdesc_sw128(b_addr + k * 32),
+                                   idesc, accumulate);
                     }
                     mma_commit(&empty[s]);
                 }
             }
             mma_commit(&tfull[buf]);
             ++local;
+            }
         }
         if (!ok) abort_flag = 1;
         mma_commit(drain);
         mbar_wait(drain, 0);
     } else if (warp >= 2) {
         // ---------------- epilogue ----------------
-        const int q = warp & 3;  // TMEM lane quarter this warp may access
+        // warps 2-9: TMEM lane quarter q = warp % 4 (the quarter a warp may
+        // access), column half h; each warp owns 32 rows x 64 columns
+        const int q = warp & 3;
+        const int cbeg = ((warp - 2) >> 2) * (TC_BN / 2);
         uint32_t local = 0;
         const float alpha_f = static_cast<float>(args.alpha);
+        const bool need_old = args.out_mode == 2 || args.beta != 0.0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
             const TileInfo ti = tile_at(args, t);
             if (ti.skip) continue;
-            const uint32_t buf = local & 1, u = local >> 1;
+            const int nch = tile_chunks(args, ti.kb_lo, ti.kb_hi);
+            bool stop = false;
+            const int64_t row = (int64_t)ti.tm * TC_BM + q * 32 + lane;
+            const bool row_ok = row < args.M;
+            const int64_t col0 = (int64_t)ti.tn * TC_BN + cbeg;
+            for (int c = 0; c < nch; ++c) {
+            int clo, chi;
+            chunk_range(args, ti.kb_lo, ti.kb_hi, c, clo, chi);
+            const uint32_t buf = local % args.nbuf, u = local / args.nbuf;
+            unsigned long long cur[TC_EG], nxt[TC_EG];
+            fetch_old(args, need_old, row, row_ok, col0, cur);  // in flight during the MMAs
+            // row exponents of this flush's 512-deep chunk (normalized slices):
+            // this thread's A row, and the B rows of columns col0 + lane and
+            // col0 + 32 + lane, shuffled to the column steps below
+            int ea = 0, eb0 = 0, eb1 = 0;
+            if (args.ex_b && clo < chi) {
+                const int64_t cha = (args.a_k_off + (int64_t)clo * TC_BK) / TC_CHUNK_K;
+                const int64_t chb = (args.b_k_off + (int64_t)clo * TC_BK) / TC_CHUNK_K;
+                if (row_ok) ea = args.ex_a[(args.a_row_off + row) * args.ex_ld_a + cha];
+                const int64_t c0 = col0 + lane, c1 = col0 + 32 + lane;
+                if (c0 < args.N) eb0 = args.ex_b[(args.b_row_off + c0) * args.ex_ld_b + chb];
+                if (c1 < args.N) eb1 = args.ex_b[(args.b_row_off + c1) * args.ex_ld_b + chb];
+            }
             bool ok = mbar_wait(&tfull[buf], u & 1);
             ok = __all_sync(0xffffffffu, ok) && !abort_flag;
             if (!ok) {
                 if (lane == 0) abort_flag = 1;
+                stop = true;
                 break;
             }
             tc_fence_after();
-            const bool has_acc = ti.kb_lo < ti.kb_hi;
-            const bool has_lo = args.npairs > 1;
-            const int64_t row = (int64_t)ti.tm * TC_BM + q * 32 + lane;
-            const bool row_ok = row < args.M;
-            for (int c0 = 0; c0 < TC_BN; c0 += 32) {
-                uint32_t hi[32], lo[32];
-                if (has_acc) {
-                    const uint32_t base = tmem + (static_cast<uint32_t>(q * 32) << 16) + c0;
-                    tmem_ld_32x32b_x32(base + (buf * 2) * TC_BN, hi);
-                    if (has_lo) tmem_ld_32x32b_x32(base + (buf * 2 + 1) * TC_BN, lo);
-                    tmem_ld_wait();
-                }
-                float v[32];
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    float h = has_acc ? __uint_as_float(hi[j]) : 0.0f;
-                    float l = (has_acc && has_lo) ? __uint_as_float(lo[j]) : 0.0f;
-                    v[j] = h + l;
-                }
-                const int64_t colb = (int64_t)ti.tn * TC_BN + c0;
-                bool okc[32];
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int64_t col = colb + j;
-                    okc[j] = row_ok && col < args.N && (!args.lower || row + args.diag_off >= col);
-                }
-                if (args.fp32) {
-                    float *base = static_cast<float *>(args.C) + row + colb * args.ldc;
-                    float old[32];
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) old[j] = okc[j] ? base[j * args.ldc] : 0.0f;
-#pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        if (okc[j]) base[j * args.ldc] = fmaf(alpha_f, v[j], old[j]);
-                } else {
-                    double *base = static_cast<double *>(args.C) + row + colb * args.ldc;
-                    if (args.beta != 0.0) {
-                        double old[32];
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) old[j] = okc[j] ? base[j * args.ldc] : 0.0;
-#pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            if (okc[j])
-                                base[j * args.ldc] =
-                                    fma(args.beta, old[j], args.alpha * static_cast<double>(v[j]));
-                    } else if (args.alpha == 1.0 || args.alpha == -1.0) {
-                        const float sg = args.alpha > 0.0 ? 1.0f : -1.0f;
-#pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            if (okc[j]) base[j * args.ldc] = static_cast<double>(sg * v[j]);
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            if (okc[j]) base[j * args.ldc] = args.alpha * static_cast<double>(v[j]);
-                    }
-                }
+            const bool has_acc = clo < chi;
+            const uint32_t tmem_col = tmem + (static_cast<uint32_t>(q * 32) << 16) + cbeg +
+                                      buf * args.nacc * TC_BN;
+            // two named buffers, so that every array index is static
+            for (int g = 0; g < TC_BN / 2; g += 2 * TC_EG) {
+                fetch_old(args, need_old, row, row_ok, col0 + g + TC_EG, nxt);
+                const int ebr = g < 32 ? eb0 : eb1;
+                epilogue_group<NACC>(args, tmem_col + g, has_acc, row, row_ok, col0 + g, alpha_f,
+                                     ea, ebr, g & 31, cur);
+                if (g + 2 * TC_EG < TC_BN / 2)
+                    fetch_old(args, need_old, row, row_ok, col0 + g + 2 * TC_EG, cur);
+                epilogue_group<NACC>(args, tmem_col + g + TC_EG, has_acc, row, row_ok,
+                                     col0 + g + TC_EG, alpha_f, ea, ebr, (g + TC_EG) & 31, nxt);
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[buf]);
             ++local;
+            }
+            if (stop) break;
         }
     }
     tc_fence_before();
@@ -321,8 +466,10 @@ struct SplitArgs {
     int trans;
     int64_t diag_off;
     int lower_mask;
-    int S;
-    __nv_bfloat16 *dst;
+    int S;      // 3: normalized FP16 slices + row exponents; 5: scaled BF16 integer slices
+    uint16_t *dst;
+    int *dst_ex;
+    int64_t ex_ld;
     int64_t dst_rows, dst_kld, dst_row_off, dst_k_off;
 };
 
@@ -361,27 +508,58 @@ __device__ __forceinline__ void f64_hi_lo(unsigned long long u, float &hi, float
     }
 }
 
-// s0, s1, s2 for one entry, given the row's scale 2^{7-e} (sc) and 2^{e-7} (isc).
-__device__ __forceinline__ void split3(unsigned long long u, float sc, float isc,
-                                       __nv_bfloat16 (&s)[3]) {
+// Normalized slices of one entry (mixed form), given the row's scale
+// sc = 2^{7-e}: with y = x sc held as a double-float (exact scaling),
+// s0 = round(y) (an integer in [-128, 128]), s1 = fp16(y - s0),
+// s2 = fp16(y - s0 - s1); y is then carried to about 2^-25 (2^{e-32} of x).
+__device__ __forceinline__ void split3_norm(unsigned long long u, float sc, uint16_t (&s)[3]) {
     float xh, xl;
     f64_hi_lo(u, xh, xl);
-    const float q = rintf(xh * sc);
-    const float s0 = q * isc;
-    const float r1 = (xh - s0) + xl;
-    const __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
-    const float r2 = r1 - __bfloat162float(b1);
-    s[0] = __float2bfloat16_rn(s0);
-    s[1] = b1;
-    s[2] = __float2bfloat16_rn(r2);
+    const float yh = xh * sc, yl = xl * sc;
+    const float q = rintf(yh);
+    float t, e;
+    two_sum(__fsub_rn(yh, q), yl, t, e);  // yh - q is exact
+    const __half h1 = __float2half_rn(t);
+    const float rest = __fadd_rn(__fsub_rn(t, __half2float(h1)), e);  // t - h1 exact
+    s[0] = __half_as_ushort(__float2half_rn(q));
+    s[1] = __half_as_ushort(h1);
+    s[2] = __half_as_ushort(__float2half_rn(rest));
 }
 
-constexpr int64_t SPLIT_KCH = 512;  // K chunk of one CTA (and of one row bound)
+// Integer slices on the row grid (FP64-grade mode): with y = x 2^{7-e} held
+// as a double-float, q_p = round(y_p), y_{p+1} = 256 (y_p - q_p); slice p is
+// q_p 2^{e-7-8p} (|q_p| <= 256, exact in BF16).  Five slices carry x to
+// 2^{e-40}.  All products of slice group d = p + q are then integers times
+// one power of two per output entry, so the leading groups accumulate
+// exactly in FP32 (see the top of this file for the depth limits).
+__device__ __forceinline__ void split_ozaki(unsigned long long u, float sc, float isc,
+                                            uint16_t (&s)[5]) {
+    float xh, xl;
+    f64_hi_lo(u, xh, xl);
+    float yh = xh * sc, yl = xl * sc, w = isc;
+#pragma unroll
+    for (int p = 0; p < 5; ++p) {
+        const float q = rintf(yh);
+        s[p] = __bfloat16_as_ushort(__float2bfloat16_rn(q * w));
+        float h, l;
+        const float d = __fsub_rn(yh, q);  // exact
+        const float t = __fadd_rn(d, yl);
+        const float bb = __fsub_rn(t, d);
+        l = __fadd_rn(__fsub_rn(d, __fsub_rn(t, bb)), __fsub_rn(yl, bb));
+        h = t;
+        yh = h * 256.0f;
+        yl = l * 256.0f;
+        w *= (1.0f / 256.0f);
+    }
+}
+
+constexpr int64_t SPLIT_KCH = TC_CHUNK_K;  // K chunk of one CTA (and of one row bound)
+constexpr int SPLIT_MAX_S = 5;
 
 __global__ void __launch_bounds__(256) split_rows_kernel(SplitArgs a) {
     __shared__ unsigned long long pmax[8][32];
     __shared__ float sc_s[32], isc_s[32];
-    __shared__ unsigned short tile[3][32][33];
+    __shared__ unsigned short tile[SPLIT_MAX_S][32][33];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t r0 = (int64_t)blockIdx.x * 32;
     // this CTA's K chunk; each (row, chunk) gets its own bound 2^e
@@ -426,18 +604,29 @@ __global__ void __launch_bounds__(256) split_rows_kernel(SplitArgs a) {
         e = max(-100, min(e, 120));
         sc_s[threadIdx.x] = ldexpf(1.0f, 7 - e);
         isc_s[threadIdx.x] = ldexpf(1.0f, e - 7);
+        if (a.dst_ex && r0 + threadIdx.x < a.R)
+            a.dst_ex[(a.dst_row_off + r0 + threadIdx.x) * a.ex_ld + (a.dst_k_off + kb) / SPLIT_KCH] = e;
     }
     __syncthreads();
     const int64_t slice = a.dst_rows * a.dst_kld;
-    __nv_bfloat16 *d0 = a.dst + (a.dst_row_off + r0) * a.dst_kld + a.dst_k_off;
+    uint16_t *d0 = a.dst + (a.dst_row_off + r0) * a.dst_kld + a.dst_k_off;
     if (a.trans == 0) {
         for (int64_t kc = kb; kc < ke; kc += 32) {
             // lane = row: coalesced FP64 reads down each column
             for (int i = warp; i < 32; i += 8) {
-                __nv_bfloat16 s[3];
-                split3(split_get(a, r0 + lane, kc + i), sc_s[lane], isc_s[lane], s);
+                uint16_t s[SPLIT_MAX_S] = {0, 0, 0, 0, 0};
+                const unsigned long long u = split_get(a, r0 + lane, kc + i);
+                if (a.S == 5) {
+                    split_ozaki(u, sc_s[lane], isc_s[lane], s);
+                } else {
+                    uint16_t t3[3];
+                    split3_norm(u, sc_s[lane], t3);
+                    s[0] = t3[0];
+                    s[1] = t3[1];
+                    s[2] = t3[2];
+                }
 #pragma unroll
-                for (int p = 0; p < 3; ++p) tile[p][i][lane] = __bfloat16_as_ushort(s[p]);
+                for (int p = 0; p < SPLIT_MAX_S; ++p) tile[p][i][lane] = s[p];
             }
             __syncthreads();
             // lane = k: coalesced BF16 writes along each row
@@ -445,8 +634,7 @@ __global__ void __launch_bounds__(256) split_rows_kernel(SplitArgs a) {
                 const int64_t r = r0 + i, k = kc + lane;
                 if (r < a.R && k < ke) {
                     for (int p = 0; p < a.S; ++p)
-                        d0[p * slice + (int64_t)i * a.dst_kld + k] =
-                            __ushort_as_bfloat16(tile[p][lane][i]);
+                        d0[p * slice + (int64_t)i * a.dst_kld + k] = tile[p][lane][i];
                 }
             }
             __syncthreads();
@@ -456,8 +644,17 @@ __global__ void __launch_bounds__(256) split_rows_kernel(SplitArgs a) {
             const int64_t r = r0 + i;
             if (r >= a.R) continue;
             for (int64_t k = kb + lane; k < ke; k += 32) {
-                __nv_bfloat16 s[3];
-                split3(split_get(a, r, k), sc_s[i], isc_s[i], s);
+                uint16_t s[SPLIT_MAX_S] = {0, 0, 0, 0, 0};
+                const unsigned long long u = split_get(a, r, k);
+                if (a.S == 5) {
+                    split_ozaki(u, sc_s[i], isc_s[i], s);
+                } else {
+                    uint16_t t3[3];
+                    split3_norm(u, sc_s[i], t3);
+                    s[0] = t3[0];
+                    s[1] = t3[1];
+                    s[2] = t3[2];
+                }
                 for (int p = 0; p < a.S; ++p) d0[p * slice + (int64_t)i * a.dst_kld + k] = s[p];
             }
         }
@@ -465,19 +662,35 @@ __global__ void __launch_bounds__(256) split_rows_kernel(SplitArgs a) {
 }
 
 int split_rows(const double *src, int64_t ld, int64_t R, int64_t K, int64_t Kvalid, int trans,
-               int64_t diag_off, int lower_mask, int S, __nv_bfloat16 *dst, int64_t dst_rows,
-               int64_t dst_kld, int64_t dst_row_off, int64_t dst_k_off, cudaStream_t s) {
+               int64_t diag_off, int lower_mask, int S, uint16_t *dst, int *dst_ex,
+               int64_t dst_rows, int64_t dst_kld, int64_t dst_row_off, int64_t dst_k_off,
+               cudaStream_t s) {
     if (R <= 0 || K <= 0) return GP_OK;
-    if (S < 1 || S > 3 || dst_row_off + R > dst_rows || dst_k_off + K > dst_kld)
+    if ((S != 3 && S != 5) || (S == 3) != (dst_ex != nullptr) || dst_row_off + R > dst_rows ||
+        dst_k_off + K > dst_kld || dst_k_off % SPLIT_KCH)
         return GP_ERR_INVALID;
-    SplitArgs a{src, ld, R, K, Kvalid < K ? Kvalid : K, trans, diag_off, lower_mask, S, dst,
-                dst_rows, dst_kld, dst_row_off, dst_k_off};
+    SplitArgs a{src, ld, R, K, Kvalid < K ? Kvalid : K, trans, diag_off, lower_mask, S,
+                dst, dst_ex, tc_ex_ld(dst_kld), dst_rows, dst_kld, dst_row_off, dst_k_off};
     const int ev = prof_start(s);
     dim3 g((unsigned)ceil_div(R, 32), (unsigned)ceil_div(K, SPLIT_KCH));
     split_rows_kernel<<<g, 256, 0, s>>>(a);
     GP_LAUNCH_CHECK();
     prof_stop(ev, s, GP_PROF_PACK, 0.0, (double)R * K * (8.0 + 2.0 * S));
     return GP_OK;
+}
+
+// C = alpha (hi + lo) + beta C over the written entries of a chunked contraction.
+__global__ void acc2_to_f64_kernel(const float2 *acc, int64_t M, int64_t N, double alpha,
+                                   double beta, double *C, int64_t ldc, int lower,
+                                   int64_t diag_off) {
+    const int64_t c = blockIdx.x;  // columns on x: N can exceed the 65,535 limit of y
+    const int64_t r = blockIdx.y * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= M || c >= N) return;
+    if (lower && r + diag_off < c) return;
+    const float2 v = acc[r + c * M];
+    double x = alpha * (static_cast<double>(v.x) + static_cast<double>(v.y));
+    if (beta != 0.0) x = fma(beta, C[r + c * ldc], x);
+    C[r + c * ldc] = x;
 }
 
 // ---------------------------------------------------------------------------
@@ -504,8 +717,10 @@ static int make_slice_map(CUtensorMap *map, const TcOperand &op, int box_rows) {
     cuuint64_t strides[2] = {(cuuint64_t)op.Kld * 2, (cuuint64_t)(op.rows * op.Kld * 2)};
     cuuint32_t box[3] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16 *>(op.slices),
-                    dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    const CUtensorMapDataType dt =
+        op.S == 3 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    CUresult r = fn(map, dt, 3, const_cast<uint16_t *>(op.slices), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? GP_OK : GP_ERR_CUDA;
@@ -525,13 +740,24 @@ int tc_gemm(const TcOperand &A, const TcOperand &B, int64_t M, int64_t N, int64_
             const TcOut &out, int tri_k, int64_t tri_off, int64_t *info, cudaStream_t s) {
     if (M <= 0 || N <= 0) return GP_OK;
     if (K % TC_BK || A.k_off % TC_BK || B.k_off % TC_BK) return GP_ERR_INVALID;
-    if (A.k_off + K > A.Kld || B.k_off + K > B.Kld || A.S != B.S) return GP_ERR_INVALID;
-    static bool attr_set = false;
-    if (!attr_set) {
-        if (cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (A.k_off + K > A.Kld || B.k_off + K > B.Kld || A.S != B.S || (A.S != 3 && A.S != 5))
+        return GP_ERR_INVALID;
+    // normalized (three-slice) stores carry their row exponents; chunks of
+    // both operands must line up with the stores' 512-column chunks
+    const bool normalized = A.S == 3;
+    if (normalized && (!A.ex || !B.ex)) return GP_ERR_INVALID;
+    if (A.k_off % TC_CHUNK_K || B.k_off % TC_CHUNK_K) return GP_ERR_INVALID;
+    // the shared-memory opt-in is per device (setting it twice is harmless)
+    static bool attr_set[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return GP_ERR_CUDA;
+    if (!attr_set[dev]) {
+        if (cudaFuncSetAttribute(tc_gemm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 TC_SMEM) != cudaSuccess ||
+            cudaFuncSetAttribute(tc_gemm_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  TC_SMEM) != cudaSuccess)
             return GP_ERR_CUDA;
-        attr_set = true;
+        attr_set[dev] = true;
     }
     CUtensorMap ma, mb;
     GP_TRY(make_slice_map(&ma, A, TC_BM));
@@ -539,7 +765,7 @@ int tc_gemm(const TcOperand &A, const TcOperand &B, int64_t M, int64_t N, int64_
     TcGemmArgs a{};
     a.C = out.C;
     a.ldc = out.ldc;
-    a.fp32 = out.fp32;
+    a.out_mode = out.mode;
     a.alpha = out.alpha;
     a.beta = out.beta;
     a.lower = out.lower;
@@ -553,23 +779,76 @@ int tc_gemm(const TcOperand &A, const TcOperand &B, int64_t M, int64_t N, int64_
     a.kblocks = (int)(K / TC_BK);
     a.tri_k = tri_k;
     a.tri_off = tri_off;
+    a.kchunk = 0;
+    a.idesc = idesc_f16kind_f32(TC_BM, TC_BN, !normalized);
+    a.ex_a = normalized ? A.ex : nullptr;
+    a.ex_b = normalized ? B.ex : nullptr;
+    a.ex_ld_a = A.ex_ld;
+    a.ex_ld_b = B.ex_ld;
+    // Deep contractions: the operands' row bounds (and, normalized, their
+    // scales) change every 512 columns of K, so the accumulators are flushed
+    // per chunk: double-float outputs take each chunk directly, FP64 outputs
+    // through the double-float buffer acc2.
+    const bool deep = K > TC_CHUNK_K;
+    const bool via_acc2 = deep && out.mode == 0;
+    if (deep) a.kchunk = (int)(TC_CHUNK_K / TC_BK);
+    if (via_acc2) {
+        if (!out.acc2) return GP_ERR_INVALID;
+        if (N > 0x7fffffffLL || ceil_div(M, 256) > 65535) return GP_ERR_INVALID;
+        a.out_mode = 2;
+        a.C = out.acc2;
+        a.ldc = M;
+        a.alpha = 1.0;
+        a.beta = 0.0;
+        if (cudaMemsetAsync(out.acc2, 0, sizeof(float2) * (size_t)M * (size_t)N, s) != cudaSuccess)
+            return GP_ERR_CUDA;
+    }
     a.tiles_m = (int)ceil_div(M, TC_BM);
     a.tiles_n = (int)ceil_div(N, TC_BN);
     a.info = info;
+    // slice pairs grouped by accumulator.  With three slices the leading pair
+    // owns the exact "hi" accumulator and the rest share "lo" (two tile
+    // buffers); with more (integer slices) the groups d = 0, 1, 2 get one
+    // accumulator each and d >= 3 a fourth (one buffer).  Within a shared
+    // accumulator the groups go in order of increasing size (largest d
+    // first): the tensor core aligns each step's products to the largest
+    // exponent present and drops the bits below its window, so small
+    // products added onto an already large running sum lose a systematic
+    // share (the diagonal of a SYRK, where s1 s1 > 0, came out low by ~1e-8
+    // relative); added first, they lose only what the later large ones cut.
+    a.nacc = A.S >= 4 ? 4 : 2;
+    a.nbuf = a.nacc * 2 <= 4 ? 2 : 1;
     int np = 0;
-    for (int d = 0; d < A.S; ++d)      // pairs in order of decreasing size:
-        for (int p = 0; p <= d; ++p) { // (0,0) first, it owns the "hi" accumulator
-            a.pa[np] = p;
-            a.pb[np] = d - p;
-            ++np;
-        }
+    for (int acc = 0; acc < a.nacc; ++acc) {
+        const int dlo = acc, dhi = acc == a.nacc - 1 ? A.S - 1 : acc;
+        for (int d = dhi; d >= dlo; --d)
+            for (int p = 0; p <= d; ++p) {
+                if (np >= TC_MAX_PAIRS) return GP_ERR_INVALID;
+                a.pa[np] = p;
+                a.pb[np] = d - p;
+                a.acc_of[np] = acc;
+                a.first_of[np] = (np == 0 || a.acc_of[np - 1] != acc) ? 1 : 0;
+                ++np;
+            }
+    }
     a.npairs = np;
     const int64_t ntiles = (int64_t)a.tiles_m * a.tiles_n;
     const int sms = num_sms();
     const int grid = (int)(ntiles < sms ? ntiles : (sms > 0 ? sms : 148));
     const int ev = prof_start(s);
-    tc_gemm_kernel<<<grid, 192, TC_SMEM, s>>>(ma, mb, a);
+    if (a.nacc == 4)
+        tc_gemm_kernel<4><<<grid, TC_THREADS, TC_SMEM, s>>>(ma, mb, a);
+    else
+        tc_gemm_kernel<2><<<grid, TC_THREADS, TC_SMEM, s>>>(ma, mb, a);
     GP_LAUNCH_CHECK();
+    if (via_acc2) {
+        dim3 g2((unsigned)N, (unsigned)ceil_div(M, 256));
+        acc2_to_f64_kernel<<<g2, 256, 0, s>>>(static_cast<const float2 *>(out.acc2), M, N,
+                                               out.alpha, out.beta,
+                                               static_cast<double *>(out.C), out.ldc, out.lower,
+                                               out.diag_off);
+        GP_LAUNCH_CHECK();
+    }
     if (ev >= 0) {
         // slice-product flops over the useful output entries and K ranges
         double useful = 0.0;

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libgp.so")
 
 GP_OK, GP_ERR_NOT_PD, GP_ERR_INVALID, GP_ERR_CUDA, GP_ERR_TIMEOUT, GP_ERR_WORKSPACE = range(6)
 KERNELS = {"exp": 0, "matern32": 1, "matern52": 2}
-PRECISIONS = {"fp64": 0, "mixed_bf16": 1}
+PRECISIONS = {"fp64": 0, "mixed_f16": 1, "emu_fp64": 2}
 
 # Exported symbols, in the order include/gp.h declares them.
 SYMBOLS = [
@@ -226,7 +226,7 @@ class Batch:
         self.prm = (GpParams * self.nprob)(*prms)
 
 
-def gp_batched_workspace_bytes(ns, precision="mixed_bf16"):
+def gp_batched_workspace_bytes(ns, precision="mixed_f16"):
     arr = (ctypes.c_int64 * len(ns))(*[int(v) for v in ns])
     return lib().gp_batched_workspace_bytes(len(ns), ctypes.cast(arr, ctypes.c_void_p),
                                             _prec(precision))
@@ -242,7 +242,7 @@ def gp_loglik_grad_batched(batch, precision, ws, out, grad, info, stream=None):
         _ptr(info), _stream(stream)), "gp_loglik_grad_batched")
 
 
-def loglik_grad_batched(xs, ys, prms, precision="mixed_bf16", mus=None, ws=None):
+def loglik_grad_batched(xs, ys, prms, precision="mixed_f16", mus=None, ws=None):
     """Evaluate a batch on the device; returns dict(out (nprob x 4), grad
     (nprob x 3), info (nprob,), ws, batch).  prms: list of GpParams."""
     batch = Batch(xs, ys, prms, mus)
@@ -272,7 +272,7 @@ def gp_loglik_grad(x, y, mu, n, prm, precision, ws, out, alpha, grad, info, stre
                                 _f64(grad), _ptr(info), _stream(stream)), "gp_loglik_grad")
 
 
-def gp_syrk_workspace_bytes(m, k, precision="mixed_bf16"):
+def gp_syrk_workspace_bytes(m, k, precision="mixed_f16"):
     return lib().gp_syrk_workspace_bytes(int(m), int(k), _prec(precision))
 
 

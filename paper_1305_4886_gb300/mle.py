@@ -13,7 +13,7 @@ import torch
 from . import gp
 
 
-def fit(x, y, kernel="matern32", theta0=(0.0, np.log(0.1), np.log(0.1)), precision="mixed_bf16",
+def fit(x, y, kernel="matern32", theta0=(0.0, np.log(0.1), np.log(0.1)), precision="mixed_f16",
         mu=None, bounds=((-10, 10), (-12, 5), (-20, 5)), maxiter=60, tol=1e-9):
     """x: (n, 2) float64 CUDA tensor, y: (n,) float64 CUDA tensor.  Returns a
     dict with theta (log parameters), params (natural), loglik, grad, nfev,

@@ -52,7 +52,7 @@ def test_host_queries(libgp):
     assert libgp.gp_padded_order(129) == 256
     assert libgp.gp_padded_order(67275) == 67328
     assert libgp.gp_padded_order(0) == 0
-    for p in ["fp64", "mixed_bf16"]:
+    for p in ["fp64", "mixed_f16"]:
         b = libgp.gp_workspace_bytes(1024, p)
         assert b >= 1024 * 1024 * 8
         assert libgp.gp_workspace_bytes(0, p) == 0

@@ -19,7 +19,7 @@ def g():
     return gp
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed_bf16"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed_f16"])
 def test_autograd_matches_oracle_gradient(g, orc, precision):
     from paper_1305_4886_gb300.autograd import gp_marginal_loglik
     n = 700

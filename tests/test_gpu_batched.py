@@ -33,7 +33,7 @@ def small_batch():
     return probs
 
 
-@pytest.mark.parametrize("precision,tl,tg", [("fp64", 1e-10, 1e-9), ("mixed_bf16", 1e-6, 1e-6)])
+@pytest.mark.parametrize("precision,tl,tg", [("fp64", 1e-10, 1e-9), ("mixed_f16", 1e-6, 1e-6)])
 def test_batched_matches_oracle(g, orc, precision, tl, tg):
     probs = small_batch()
     ys = [inputs.std_normal(p.n, 40000 + i) for i, p in enumerate(probs)]
@@ -56,7 +56,7 @@ def test_batched_full_workload_and_graph(g):
     xs = [dev(p.x) for p in probs]
     zs = [dev(p.z) for p in probs]
     prms = [g.params(p.kernel, p.s2, p.rho, p.tau2) for p in probs]
-    r = g.loglik_grad_batched(xs, zs, prms, precision="mixed_bf16")
+    r = g.loglik_grad_batched(xs, zs, prms, precision="mixed_f16")
     torch.cuda.synchronize()
     assert np.all(r["info"].cpu().numpy() == 0)
     out = r["out"].cpu().numpy().copy()
@@ -65,7 +65,7 @@ def test_batched_full_workload_and_graph(g):
     # the single-problem entry point gives the same numbers (same kernels)
     for i in [0, 1, 77, 300, 511]:
         p = probs[i]
-        s = g.loglik_grad(xs[i], zs[i], p.kernel, p.s2, p.rho, p.tau2, precision="mixed_bf16")
+        s = g.loglik_grad(xs[i], zs[i], p.kernel, p.s2, p.rho, p.tau2, precision="mixed_f16")
         assert rel_err(out[i, 0], float(s["out"][0])) < 1e-12
         assert np.max(np.abs(grad[i] - s["grad"].cpu().numpy())) <= 1e-9 * np.max(np.abs(grad[i]))
     # capture the whole batch in one CUDA graph and replay it
@@ -78,7 +78,7 @@ def test_batched_full_workload_and_graph(g):
     with torch.cuda.stream(side):
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph, stream=side):
-            g.gp_loglik_grad_batched(batch, "mixed_bf16", ws, o2, g2, i2)
+            g.gp_loglik_grad_batched(batch, "mixed_f16", ws, o2, g2, i2)
     torch.cuda.current_stream().wait_stream(side)
     graph.replay()
     torch.cuda.synchronize()

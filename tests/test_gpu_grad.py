@@ -47,7 +47,7 @@ def test_grad_fp64_matches_oracle(g, orc, n, kern):
 def test_grad_mixed_matches_oracle(g, orc, n, kern):
     x = inputs.uniform_points(n, 12000 + n)
     y = inputs.std_normal(n, 12100 + n)
-    r = g.loglik_grad(dev(x), dev(y), kern, 1.1, 0.05, 0.1, precision="mixed_bf16")
+    r = g.loglik_grad(dev(x), dev(y), kern, 1.1, 0.05, 0.1, precision="mixed_f16")
     ref = orc.loglik_grad(x, y, kern, 1.1, 0.05, 0.1)
     out = r["out"].cpu().numpy()
     assert rel_err(out[0], ref["loglik"]) < 1e-6
@@ -79,7 +79,7 @@ def test_grad_trace_identity_device(g):
     n = 500
     x = inputs.uniform_points(n, 13100)
     y = inputs.std_normal(n, 13101)
-    for prec, tol in [("fp64", 1e-10), ("mixed_bf16", 1e-7)]:
+    for prec, tol in [("fp64", 1e-10), ("mixed_f16", 1e-7)]:
         r = g.loglik_grad(dev(x), dev(y), "exp", 1.3, 0.1, 0.2, precision=prec)
         gr = r["grad"].cpu().numpy()
         rhs = -n / 2 + 0.5 * float(np.dot(y, r["alpha"].cpu().numpy()))

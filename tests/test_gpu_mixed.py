@@ -36,10 +36,10 @@ def test_tc_syrk_matches_fp64(g, m, k):
     bound = np.abs(P) @ np.abs(P).T
     Cd = dev(C0.T.copy())          # column-major: storage (j, i)
     Pd = dev(P.T.copy())
-    ws = torch.empty(g.gp_syrk_workspace_bytes(m, k, "mixed_bf16"), dtype=torch.uint8,
+    ws = torch.empty(g.gp_syrk_workspace_bytes(m, k, "mixed_f16"), dtype=torch.uint8,
                      device="cuda")
     info = torch.zeros(1, dtype=torch.int64, device="cuda")
-    g.gp_syrk_lower(Cd.view(-1), m, Pd.view(-1), m, m, k, "mixed_bf16", ws, info)
+    g.gp_syrk_lower(Cd.view(-1), m, Pd.view(-1), m, m, k, "mixed_f16", ws, info)
     torch.cuda.synchronize()
     assert int(info.item()) == 0
     C = Cd.cpu().numpy().T
@@ -61,10 +61,10 @@ def test_mixed_chol_matches_oracle(g, orc, n):
     np_ = g.gp_padded_order(n)
     buf = torch.empty(np_ * np_, dtype=torch.float64, device="cuda")
     g.gp_cov_fill(dev(x), g.params("matern32", 1.0, 0.05, 0.1), buf, np_)
-    ws = torch.empty(max(1, g.gp_chol_workspace_bytes(n, "mixed_bf16")), dtype=torch.uint8,
+    ws = torch.empty(max(1, g.gp_chol_workspace_bytes(n, "mixed_f16")), dtype=torch.uint8,
                      device="cuda")
     info = torch.zeros(1, dtype=torch.int64, device="cuda")
-    g.gp_chol(buf, n, np_, "mixed_bf16", ws, info)
+    g.gp_chol(buf, n, np_, "mixed_f16", ws, info)
     torch.cuda.synchronize()
     assert int(info.item()) == 0
     L = np.tril(colmajor_to_numpy(buf, np_))
@@ -78,7 +78,7 @@ def test_mixed_chol_matches_oracle(g, orc, n):
 def test_mixed_loglik_matches_oracle(g, orc, n, kern):
     x = inputs.uniform_points(n, 8000 + n)
     y = inputs.std_normal(n, 8100 + n)
-    r = g.loglik(dev(x), dev(y), kern, 1.2, 0.06, 0.08, mu=0.1, precision="mixed_bf16")
+    r = g.loglik(dev(x), dev(y), kern, 1.2, 0.06, 0.08, mu=0.1, precision="mixed_f16")
     out = r["out"].cpu().numpy()
     ref = orc.loglik(x, y, kern, 1.2, 0.06, 0.08, mu=0.1)
     assert rel_err(out[0], ref["loglik"]) <= 1e-6
@@ -94,8 +94,8 @@ def test_mixed_not_pd(g):
     g.gp_cov_fill(dev(x), g.params("exp", 1.0, 0.1, 0.1), buf, np_)
     k = 600  # in the second outer block
     buf[k + k * np_] = -5.0
-    ws = torch.empty(g.gp_chol_workspace_bytes(n, "mixed_bf16"), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(g.gp_chol_workspace_bytes(n, "mixed_f16"), dtype=torch.uint8, device="cuda")
     info = torch.zeros(1, dtype=torch.int64, device="cuda")
-    g.gp_chol(buf, n, np_, "mixed_bf16", ws, info)
+    g.gp_chol(buf, n, np_, "mixed_f16", ws, info)
     torch.cuda.synchronize()
     assert int(info.item()) == k + 1

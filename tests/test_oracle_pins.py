@@ -314,3 +314,10 @@ def test_not_pd_reports_column(orc):
     assert e.value.info == 7
     with pytest.raises(ValueError):
         orc.loglik(x, np.ones(10), "exp", 1.0, 0.2, -0.1)
+
+
+def test_cov_rows_are_rows_of_the_fill(orc):
+    x = inputs.uniform_points(150, 61)
+    C = orc.cov_fill(x, "matern52", 1.3, 0.08, 0.2)
+    rows = np.array([0, 7, 149, 77])
+    assert np.array_equal(orc.cov_rows(x, rows, "matern52", 1.3, 0.08, 0.2), C[rows])
