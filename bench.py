@@ -191,11 +191,15 @@ def oracle_sample(n_target, budget_s, p_full=None):
         oracle.loglik_grad(p.x, p.z, p.kernel, p.s2, p.rho, p.tau2)
         return time.perf_counter() - t0
 
-    n0 = 384
+    run(256)  # first call: thread start-up and page faults
+    n0 = 768
     t0 = run(n0)
     n_s = int(n0 * (budget_s / max(t0, 1e-3)) ** (1.0 / 3.0))
-    n_s = max(n0, min(n_s, 6144, n_target))
+    n_s = max(n0, min(n_s, 8192, n_target))
     t_s = run(n_s)
+    if t_s < 0.4 * budget_s and n_s < min(8192, n_target):  # estimate was low: one more step
+        n_s = max(n_s, min(int(n_s * (budget_s / max(t_s, 1e-3)) ** (1.0 / 3.0)), 8192, n_target))
+        t_s = run(n_s)
     t_full = t_s * (n_target / n_s) ** 3
     desc = (f"oracle loglik+grad on the same recipe at n={n_s} ({t_s:.1f} s, {threads} threads), "
             f"extrapolated to n={n_target} by n^3")
@@ -407,6 +411,8 @@ def run_ours(args, rank, world, local):
         "error": err,
         "loglik_grad_alg_tflops": n ** 3 / (elapsed_ms / args.steps / 1e3) / 1e12,
         "per_step_ms": {c: prof[c][0] / args.steps for c in prof},
+        "per_step_launches": {c: prof[c][1] / args.steps for c in prof},
+        "contract_flops_per_step": fl_c / args.steps,
         "cholesky_alg_flop": chol_alg,
         "parallelism": "replicas" if world > 1 else "single GPU",
     }

@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define GP_ABI_VERSION 1
+#define GP_ABI_VERSION 2
 #define GP_PAD 128 /* padding granularity of n (rows/columns of one tile) */
 
 typedef enum {
@@ -116,8 +116,12 @@ size_t gp_chol_workspace_bytes(int64_t n, int precision);
 /* Covariance fill (Sec. 1: C = C_g + C_y; Sec. 2.3.5: entries built from a
  * covariance function at given indices).  Writes the lower tiles of the
  * n_p x n_p matrix d_C (ld = ldc): C_ij = sigma2 k(d_ij/rho) for i != j,
- * C_ii = sigma2 + tau2, identity in the padding.                           */
-int gp_cov_fill(const double *d_x, int64_t n, const gp_params *prm, double *d_C,
+ * C_ii = sigma2 + tau2, identity in the padding.  precision selects the
+ * evaluation the factorisations of that precision use: GP_FP64 in FP64;
+ * the tensor-core forms in double-float on the FP32 pipe (about 48
+ * significant bits: a few hundred FP64 ulps; entries with exp(-d/rho
+ * scaled) below 2^-125, all below 1e-33 sigma2, set to 0).                                                               */
+int gp_cov_fill(const double *d_x, int64_t n, const gp_params *prm, int precision, double *d_C,
                 int64_t ldc, void *stream);
 
 /* Cholesky factorisation L L^T = C in place (Sec. 1; block algorithm of

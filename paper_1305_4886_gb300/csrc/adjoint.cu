@@ -169,27 +169,34 @@ size_t grad_ws_bytes(int64_t np, int precision, int S) {
     return grad_layout(nullptr, np, precision, S).bytes;
 }
 
-// In place: A (lower L) -> X = L^{-1} (lower); fills w.XT with X^T.
-static int trtri_inplace(double *A, int64_t ld, int64_t np, GradWs &w, int64_t *info,
-                         cudaStream_t s) {
+// In place: A (lower L) -> X = L^{-1} (lower); fills w.XT with X^T.  winv
+// (nullable): the diagonal-block inverses the factorisation already formed
+// (GNB x GNB each, in block order), used instead of recomputing them.
+static int trtri_inplace(double *A, int64_t ld, int64_t np, GradWs &w, const double *winv,
+                         int64_t *info, cudaStream_t s) {
     for (int64_t k0 = 0; k0 < np; k0 += GNB) {
         const int64_t nb = (np - k0) < GNB ? (np - k0) : GNB;
         double *Akk = A + k0 + k0 * ld;
-        const int ev = prof_start(s);
-        GP_TRY(trtri_fp64_blocked(Akk, ld, nb, w.Wd, nb, w.tmp, info, s));
-        prof_stop(ev, s, GP_PROF_DIAGINV, (double)nb * nb * nb / 3.0, 0.0);
+        const double *Wd = w.Wd;
+        if (winv) {
+            Wd = winv + (k0 / GNB) * GNB * GNB;
+        } else {
+            const int ev = prof_start(s);
+            GP_TRY(trtri_fp64_blocked(Akk, ld, nb, w.Wd, nb, w.tmp, info, s));
+            prof_stop(ev, s, GP_PROF_DIAGINV, (double)nb * nb * nb / 3.0, 0.0);
+        }
         if (k0 > 0) {
             // T (nb x k0) = L[k, 0:k0] X[0:k0, 0:k0]
             GP_TRY(pack(w.SArow, A + k0, ld, nb, k0, k0, 0, 0, 0, 0, 0, s));
             GP_TRY(contract(w.SArow, 0, 0, w.XT, 0, 0, nb, k0, k0, 1.0, 0.0, w.T, nb, 0, 0, 1, 0,
                             w.acc2, info, s));
             // X[k, 0:k0] = -X_kk T
-            GP_TRY(pack(w.SW, w.Wd, nb, nb, nb, nb, 0, 0, 1, 0, 0, s));
+            GP_TRY(pack(w.SW, Wd, nb, nb, nb, nb, 0, 0, 1, 0, 0, s));
             GP_TRY(pack(w.ST, w.T, nb, k0, nb, nb, 1, 0, 0, 0, 0, s));
             GP_TRY(contract(w.SW, 0, 0, w.ST, 0, 0, nb, k0, nb, -1.0, 0.0, A + k0, ld, 0, 0, 0, 0,
                             w.acc2, info, s));
         }
-        copy_lower_kernel<<<dim3(1, (unsigned)nb), 256, 0, s>>>(w.Wd, nb, Akk, ld, nb, info);
+        copy_lower_kernel<<<dim3(1, (unsigned)nb), 256, 0, s>>>(Wd, nb, Akk, ld, nb, info);
         GP_LAUNCH_CHECK();
         // XT[j][l] = X[l][j] for l in block k, j < k0 + nb (zero above the diagonal)
         GP_TRY(pack(w.XT, A + k0, ld, k0 + nb, nb, nb, 1, k0, 1, 0, k0, s));
@@ -209,10 +216,10 @@ static int lauum_inplace(double *A, int64_t ld, int64_t np, GradWs &w, int64_t *
     return GP_OK;
 }
 
-int chol_inverse(double *A, int64_t ld, int64_t np, int precision, int S, void *ws, int64_t *info,
-                 cudaStream_t s) {
+int chol_inverse(double *A, int64_t ld, int64_t np, int precision, int S, void *ws,
+                 const double *winv, int64_t *info, cudaStream_t s) {
     GradWs w = grad_layout(ws, np, precision, S);
-    GP_TRY(trtri_inplace(A, ld, np, w, info, s));
+    GP_TRY(trtri_inplace(A, ld, np, w, winv, info, s));
     GP_TRY(lauum_inplace(A, ld, np, w, info, s));
     return GP_OK;
 }
@@ -287,6 +294,79 @@ __global__ void __launch_bounds__(256) grad_contract_kernel(const double2 *__res
     }
 }
 
+// The same contraction with C, dC/dlog rho and the weights a_i a_k - W_ik
+// in double-float on the FP32 pipe (tensor-core forms); W is split into
+// (hi, lo) by integer operations and the diagonal terms stay in FP64.
+__global__ void __launch_bounds__(256) grad_contract_df_kernel(const double2 *__restrict__ x,
+                                                               int64_t n, KernParams kp,
+                                                               const double *W, int64_t ld,
+                                                               const double *a, double *part,
+                                                               const int64_t *info) {
+    __shared__ float4 xc[TB];
+    __shared__ float2 tab[DF_TAB];
+    __shared__ float2 ac[TB];
+    __shared__ double red[3][8];
+    stage_df_table(kp.kd, tab);
+    if (failed(info)) return;
+    int64_t ti, tj;
+    lower_tile_coords(blockIdx.x, ti, tj);
+    const int64_t row0 = ti * TB, col0 = tj * TB;
+    const int tid = threadIdx.x;
+    if (tid < TB) {
+        const int64_t j = col0 + tid;
+        xc[tid] = df_point(j < n ? x[j] : make_double2(0.0, 0.0));
+        const dfl aj =
+            f64_to_df(static_cast<unsigned long long>(__double_as_longlong(j < n ? a[j] : 0.0)));
+        ac[tid] = make_float2(aj.h, aj.l);
+    }
+    __syncthreads();
+    const int r = tid & (TB - 1), cg = tid >> 6;
+    const int64_t i = row0 + r;
+    double g0 = 0.0, g2 = 0.0;
+    dfl h0{0.0f, 0.0f}, h1{0.0f, 0.0f};
+    if (i < n) {
+        const float4 xi = df_point(x[i]);
+        const double ai = a[i];
+        const dfl aid = f64_to_df(static_cast<unsigned long long>(__double_as_longlong(ai)));
+        for (int c = cg; c < TB; c += 4) {
+            const int64_t k = col0 + c;
+            if (k >= n || k > i) continue;
+            const double w = W[i + k * ld];
+            if (k == i) {
+                const double cb = 0.5 * (ai * ai - w);
+                g0 = fma(cb, kp.s2, g0);
+                g2 = fma(cb, kp.tau2, g2);
+            } else {
+                const dfl wd = f64_to_df(static_cast<unsigned long long>(__double_as_longlong(w)));
+                const dfl cb2 = df_add(df_mul(aid, dfl{ac[c].x, ac[c].y}), df_neg(wd));
+                dfl cv, dr;
+                df_cov<true>(kp.kind, kp.kd, df_dist(xi, xc[c]), tab, cv, dr);
+                h0 = df_add(h0, df_mul(cb2, cv));
+                h1 = df_add(h1, df_mul(cb2, dr));
+            }
+        }
+    }
+    g0 += df_to_double(h0);
+    double g1 = df_to_double(h1);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        g0 += __shfl_xor_sync(0xffffffffu, g0, o);
+        g1 += __shfl_xor_sync(0xffffffffu, g1, o);
+        g2 += __shfl_xor_sync(0xffffffffu, g2, o);
+    }
+    if ((tid & 31) == 0) {
+        red[0][tid >> 5] = g0;
+        red[1][tid >> 5] = g1;
+        red[2][tid >> 5] = g2;
+    }
+    __syncthreads();
+    if (tid < 3) {
+        double sum = 0.0;
+        for (int w8 = 0; w8 < 8; ++w8) sum += red[tid][w8];
+        part[3 * (int64_t)blockIdx.x + tid] = sum;
+    }
+}
+
 __global__ void __launch_bounds__(1024) grad_reduce_kernel(const double *part, int64_t ntiles,
                                                            double *grad, const int64_t *info) {
     __shared__ double ps[3][1024];
@@ -318,8 +398,12 @@ int grad_contract(const double *d_x, int64_t n, int64_t np, const KernParams &kp
     GradWs w = grad_layout(ws, np, precision, S);
     const int64_t nt = ntiles64(np);
     const int ev = prof_start(s);
-    grad_contract_kernel<<<(unsigned)nt, 256, 0, s>>>(reinterpret_cast<const double2 *>(d_x), n, kp,
-                                                       W, ld, alpha, w.part, info);
+    if (kp.use_df)
+        grad_contract_df_kernel<<<(unsigned)nt, 256, 0, s>>>(reinterpret_cast<const double2 *>(d_x),
+                                                              n, kp, W, ld, alpha, w.part, info);
+    else
+        grad_contract_kernel<<<(unsigned)nt, 256, 0, s>>>(reinterpret_cast<const double2 *>(d_x), n,
+                                                           kp, W, ld, alpha, w.part, info);
     GP_LAUNCH_CHECK();
     prof_stop(ev, s, GP_PROF_GRAD, 0.0, 8.0 * (double)np * (double)(np + 1) / 2.0);
     grad_reduce_kernel<<<1, 1024, 0, s>>>(w.part, nt, grad, info);

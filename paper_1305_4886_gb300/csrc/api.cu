@@ -62,6 +62,8 @@ struct LoglikWs {
     double *stats = nullptr;  // [0] refinement residual ratio
     int *conv = nullptr;      // refinement converged flag
     int *tsync = nullptr;     // ticket + flags of the single-launch solves
+    double *winv = nullptr;   // tensor-core forms with gradient: the factorisation's
+                              // diagonal-block inverses, reused by the inverse
     void *chol = nullptr;
     size_t bytes = 0;
 };
@@ -78,6 +80,7 @@ static LoglikWs loglik_ws_layout(void *base, int64_t n, int precision, int want_
     w.stats = c.take<double>(4);
     w.conv = c.take<int>(4);
     w.tsync = c.take<int>(trsv_sync_ints(np));
+    if (want_grad && precision != GP_FP64) w.winv = c.take<double>(chol_winv_doubles(np));
     size_t cb = chol_ws_bytes(np, precision);
     if (want_grad) {  // the inverse and contraction reuse the factorisation's scratch
         size_t gb = grad_ws_bytes(np, precision, slices_of(precision));
@@ -88,8 +91,8 @@ static LoglikWs loglik_ws_layout(void *base, int64_t n, int precision, int want_
     return w;
 }
 
-static int run_chol(double *A, int64_t np, int64_t ld, int precision, void *ws, int64_t *info,
-                    cudaStream_t s) {
+static int run_chol(double *A, int64_t np, int64_t ld, int precision, void *ws, double *winv,
+                    int64_t *info, cudaStream_t s) {
     if (precision == GP_FP64) {
         const int ev = prof_start(s);
         GP_TRY(chol_fp64_tiled(A, ld, np, 0, info, s));
@@ -97,7 +100,7 @@ static int run_chol(double *A, int64_t np, int64_t ld, int precision, void *ws, 
         return GP_OK;
     }
     if (precision == GP_MIXED_F16 || precision == GP_EMU_FP64)
-        return chol_mixed(A, ld, np, slices_of(precision), ws, info, s);
+        return chol_mixed(A, ld, np, slices_of(precision), ws, winv, info, s);
     return GP_ERR_INVALID;
 }
 
@@ -108,7 +111,7 @@ static int loglik_core(const double *d_x, const double *d_y, const double *d_mu,
     const int64_t np = padded(n);
     if (cudaMemsetAsync(d_info, 0, sizeof(int64_t), s) != cudaSuccess) return GP_ERR_CUDA;
     GP_TRY(launch_cov_fill(d_x, n, np, kp, w.A, np, d_info, s));
-    GP_TRY(run_chol(w.A, np, np, precision, w.chol, d_info, s));
+    GP_TRY(run_chol(w.A, np, np, precision, w.chol, w.winv, d_info, s));
     GP_TRY(launch_residual(d_y, d_mu, n, np, w.r, d_info, s));
     if (cudaMemcpyAsync(w.v, w.r, sizeof(double) * np, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return GP_ERR_CUDA;
@@ -163,10 +166,11 @@ size_t gp_workspace_bytes(int64_t n, int precision, int want_grad) {
     return loglik_ws_layout(nullptr, n, precision, want_grad).bytes;
 }
 
-int gp_cov_fill(const double *d_x, int64_t n, const gp_params *prm, double *d_C, int64_t ldc,
-                void *stream) {
-    if (n < 1 || !d_x || !d_C || !params_ok(prm) || ldc < padded(n)) return GP_ERR_INVALID;
-    KernParams kp = make_kern(*prm);
+int gp_cov_fill(const double *d_x, int64_t n, const gp_params *prm, int precision, double *d_C,
+                int64_t ldc, void *stream) {
+    if (n < 1 || !d_x || !d_C || !params_ok(prm) || !precision_ok(precision) || ldc < padded(n))
+        return GP_ERR_INVALID;
+    KernParams kp = make_kern(*prm, precision != GP_FP64);
     return launch_cov_fill(d_x, n, padded(n), kp, d_C, ldc, nullptr, (cudaStream_t)stream);
 }
 
@@ -178,7 +182,7 @@ int gp_chol(double *d_C, int64_t n, int64_t ldc, int precision, void *d_ws, size
     if (need > 0 && (!d_ws || ws_bytes < need)) return GP_ERR_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
     if (cudaMemsetAsync(d_info, 0, sizeof(int64_t), s) != cudaSuccess) return GP_ERR_CUDA;
-    return run_chol(d_C, padded(n), ldc, precision, d_ws, d_info, s);
+    return run_chol(d_C, padded(n), ldc, precision, d_ws, nullptr, d_info, s);
 }
 
 int gp_backsolve(const double *d_L, int64_t n, int64_t ldc, int trans, const double *d_b,
@@ -206,7 +210,7 @@ int gp_loglik(const double *d_x, const double *d_y, const double *d_mu, int64_t 
     LoglikWs w = loglik_ws_layout(d_ws, n, precision, 0);
     if (!d_ws || ws_bytes < w.bytes) return GP_ERR_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
-    KernParams kp = make_kern(*prm);
+    KernParams kp = make_kern(*prm, precision != GP_FP64);
     GP_TRY(loglik_core(d_x, d_y, d_mu, n, kp, precision, w, d_out, d_info, s));
     if (d_alpha &&
         cudaMemcpyAsync(d_alpha, w.v, sizeof(double) * n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
@@ -224,9 +228,9 @@ int gp_loglik_grad(const double *d_x, const double *d_y, const double *d_mu, int
     if (!d_ws || ws_bytes < w.bytes) return GP_ERR_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t np = padded(n);
-    KernParams kp = make_kern(*prm);
+    KernParams kp = make_kern(*prm, precision != GP_FP64);
     GP_TRY(loglik_core(d_x, d_y, d_mu, n, kp, precision, w, d_out, d_info, s));
-    GP_TRY(chol_inverse(w.A, np, np, precision, slices_of(precision), w.chol, d_info, s));
+    GP_TRY(chol_inverse(w.A, np, np, precision, slices_of(precision), w.chol, w.winv, d_info, s));
     GP_TRY(grad_contract(d_x, n, np, kp, w.A, np, w.v, w.chol, precision, slices_of(precision), d_grad,
                          d_info, s));
     if (d_alpha &&
@@ -336,12 +340,13 @@ int gp_loglik_grad_batched(int nprob, const int64_t *h_n, const double *const *h
             const int64_t n = h_n[i];
             const int64_t np = padded(n);
             LoglikWs w = loglik_ws_layout(static_cast<char *>(d_ws) + off[i], n, precision, 1);
-            KernParams kp = make_kern(h_prm[i]);
+            KernParams kp = make_kern(h_prm[i], precision != GP_FP64);
             const double *mu = h_dmu ? h_dmu[i] : nullptr;
             int st = loglik_core(h_dx[i], h_dy[i], mu, n, kp, precision, w, d_out + 4 * i,
                                  d_info + i, sk);
             if (st == GP_OK)
-                st = chol_inverse(w.A, np, np, precision, slices_of(precision), w.chol, d_info + i, sk);
+                st = chol_inverse(w.A, np, np, precision, slices_of(precision), w.chol, w.winv,
+                                  d_info + i, sk);
             if (st == GP_OK)
                 st = grad_contract(h_dx[i], n, np, kp, w.A, np, w.v, w.chol, precision,
                                    slices_of(precision), d_grad + 3 * i, d_info + i, sk);

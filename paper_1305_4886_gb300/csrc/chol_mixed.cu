@@ -62,6 +62,8 @@ static MixedWs mixed_layout(void *base, int64_t np, int S) {
 
 size_t chol_mixed_ws_bytes(int64_t np, int S) { return mixed_layout(nullptr, np, S).bytes; }
 
+size_t chol_winv_doubles(int64_t np) { return (size_t)ceil_div(np, NB) * NB * NB; }
+
 // A[r, c] += D.hi[r, c] + D.lo[r, c] (double-float pending updates).
 __global__ void fold_delta2_kernel(double *A, int64_t ld, const float2 *D, int64_t ldd,
                                    int64_t rows, int64_t cols, const int64_t *info) {
@@ -74,7 +76,8 @@ __global__ void fold_delta2_kernel(double *A, int64_t ld, const float2 *D, int64
     }
 }
 
-int chol_mixed(double *A, int64_t ld, int64_t np, int S, void *ws, int64_t *info, cudaStream_t s) {
+int chol_mixed(double *A, int64_t ld, int64_t np, int S, void *ws, double *winv, int64_t *info,
+               cudaStream_t s) {
     MixedWs w = mixed_layout(ws, np, S);
     if (cudaMemsetAsync(w.D, 0, sizeof(float2) * (size_t)np * (size_t)np, s) !=
         cudaSuccess)
@@ -94,13 +97,17 @@ int chol_mixed(double *A, int64_t ld, int64_t np, int S, void *ws, int64_t *info
         GP_TRY(chol_fp64_tiled(Akk, ld, nb, k0, info, s));
         prof_stop(ev, s, GP_PROF_DIAG, (double)nb * nb * nb / 3.0, 0.0);
         const int64_t m = np - k0 - nb;
+        if (m <= 0 && !winv) break;
+        // W = L_kk^{-1} (kept for the gradient's inverse when asked: then the
+        // last block's inverse is formed too)
+        double *W = winv ? winv + (k0 / NB) * NB * NB : w.W;
+        ev = prof_start(s);
+        GP_TRY(trtri_fp64_blocked(Akk, ld, nb, W, nb, w.tmp, info, s));
+        prof_stop(ev, s, GP_PROF_DIAGINV, (double)nb * nb * nb / 3.0, 0.0);
         if (m <= 0) break;
         double *P = Akk + nb;  // m x nb panel below the diagonal block
-        ev = prof_start(s);
-        GP_TRY(trtri_fp64_blocked(Akk, ld, nb, w.W, nb, w.tmp, info, s));
-        prof_stop(ev, s, GP_PROF_DIAGINV, (double)nb * nb * nb / 3.0, 0.0);
         int *exA = S == 3 ? w.exA : nullptr, *exB = S == 3 ? w.exB : nullptr;
-        GP_TRY(split_rows(w.W, nb, nb, nb, nb, 0, 0, 1, S, w.SB, exB, NB, NB, 0, 0, s));
+        GP_TRY(split_rows(W, nb, nb, nb, nb, 0, 0, 1, S, w.SB, exB, NB, NB, 0, 0, s));
         GP_TRY(split_rows(P, ld, m, nb, nb, 0, 0, 0, S, w.SA, exA, np, NB, 0, 0, s));
         TcOperand opA{w.SA, np, NB, S, 0, 0, exA, tc_ex_ld(NB)};
         TcOperand opW{w.SB, NB, NB, S, 0, 0, exB, tc_ex_ld(NB)};

@@ -19,19 +19,21 @@ namespace gp {
 // Cholesky of the 64 x 64 tile at A (column-major, ld), right-looking in
 // shared memory on the unscaled columns: step j subtracts a_rj a_cj / d_j
 // from the trailing lower triangle (d_j the current pivot), and the columns
-// are scaled by 1/sqrt(d_j) once at the end (L_rj = a_rj / sqrt(d_j)).  One
-// thread forms 1/d_j per step, so each step costs two barriers and no FP64
-// division or square root on the serial chain.  col_base is the global
-// column of the tile's first column (for the d_info convention).  A pivot
-// <= 0 or NaN stops the factorisation.
+// are scaled by 1/sqrt(d_j) once at the end (L_rj = a_rj / sqrt(d_j)).  Each
+// step costs one reciprocal, two barriers and one FMA per trailing lower
+// entry (a warp per column: the FP64 pipe of one SM, about two FMAs per
+// clock, is what bounds this kernel).  col_base is the global column of the
+// tile's first column (for the d_info convention).  A pivot <= 0 or NaN
+// stops the factorisation.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) potrf_tile_kernel(double *A, int64_t ld, int64_t col_base,
                                                          int64_t *info) {
     __shared__ double S[TB * (TB + 1)];
+    __shared__ double lj[TB];    // a_cj / d_j of the current step
     __shared__ double dinv[TB];
     __shared__ int bad;
     if (failed(info)) return;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int e = tid; e < TB * TB; e += blockDim.x) {
         int r = e & (TB - 1), c = e >> 6;
         S[c * (TB + 1) + r] = (r >= c) ? A[r + (int64_t)c * ld] : 0.0;
@@ -39,25 +41,30 @@ __global__ void __launch_bounds__(256) potrf_tile_kernel(double *A, int64_t ld, 
     if (tid == 0) bad = 0;
     __syncthreads();
     for (int j = 0; j < TB; ++j) {
-        if (tid == 0) {
-            const double d = S[j * (TB + 1) + j];
+        const double *cj = S + j * (TB + 1);
+        if (tid < TB) {
+            // every thread of the first two warps forms 1/d_j (one division's
+            // latency on the serial chain) and its own multiplier
+            const double d = cj[j];
             if (!(d > 0.0)) {
-                bad = 1;
-                set_info(info, col_base + j + 1);
+                if (tid == 0) {
+                    bad = 1;
+                    set_info(info, col_base + j + 1);
+                }
             } else {
-                dinv[j] = 1.0 / d;
+                const double inv = 1.0 / d;
+                if (tid == 0) dinv[j] = inv;
+                if (tid > j) lj[tid] = cj[tid] * inv;
             }
         }
         __syncthreads();
         if (bad) break;  // uniform
-        const double inv = dinv[j];
-        const double *cj = S + j * (TB + 1);
-        // a_rc -= a_rj a_cj / d_j for j < c <= r < 64
-        const int w = TB - 1 - j;
-        for (int e = tid; e < w * TB; e += blockDim.x) {
-            const int c = j + 1 + e / TB;
-            const int r = e & (TB - 1);
-            if (r >= c) S[c * (TB + 1) + r] -= cj[r] * (cj[c] * inv);
+        // a_rc -= a_rj a_cj / d_j on the trailing lower triangle j < c <= r:
+        // a warp per column, lanes down the rows (one FMA per entry)
+        for (int c = j + 1 + warp; c < TB; c += 8) {
+            const double l = lj[c];
+            double *sc = S + c * (TB + 1);
+            for (int r = c + lane; r < TB; r += 32) sc[r] = fma(-cj[r], l, sc[r]);
         }
         __syncthreads();
     }

@@ -54,14 +54,65 @@ __global__ void __launch_bounds__(256) cov_fill_kernel(const double2 *__restrict
     }
 }
 
+// The same tile fill with the off-diagonal entries evaluated in double-float
+// on the FP32 pipe (tensor-core forms); one FP64 add per entry assembles the
+// value.
+__global__ void __launch_bounds__(256) cov_fill_df_kernel(const double2 *__restrict__ x, int64_t n,
+                                                          KernParams kp, double *__restrict__ C,
+                                                          int64_t ldc, int64_t *info) {
+    __shared__ float4 xc[TB];
+    __shared__ float2 tab[DF_TAB];
+    stage_df_table(kp.kd, tab);
+    int64_t ti, tj;
+    lower_tile_coords(blockIdx.x, ti, tj);
+    const int64_t row0 = ti * TB, col0 = tj * TB;
+    const int tid = threadIdx.x;
+    if (tid < TB) {
+        const int64_t j = col0 + tid;
+        double2 p = make_double2(0.0, 0.0);
+        if (j < n) {
+            p = x[j];
+            if (info && (!isfinite(p.x) || !isfinite(p.y))) set_info(info, -2);
+        }
+        xc[tid] = df_point(p);
+    }
+    __syncthreads();
+    const int r = tid & (TB - 1);
+    const int cg = tid >> 6;  // 0..3
+    const int64_t i = row0 + r;
+    const float4 xi = df_point(i < n ? x[i] : make_double2(0.0, 0.0));
+    double *col = C + i;
+#pragma unroll 2
+    for (int c = cg; c < TB; c += 4) {
+        const int64_t j = col0 + c;
+        double v;
+        if (i < n && j < n) {
+            if (i == j) {
+                v = kp.diag;
+            } else {
+                dfl cv, unused;
+                df_cov<false>(kp.kind, kp.kd, df_dist(xi, xc[c]), tab, cv, unused);
+                v = df_to_double(cv);
+            }
+        } else {
+            v = (i == j) ? 1.0 : 0.0;
+        }
+        col[j * ldc] = v;
+    }
+}
+
 int launch_cov_fill(const double *d_x, int64_t n, int64_t np, const KernParams &kp, double *d_C,
                     int64_t ldc, int64_t *d_info, cudaStream_t s) {
     const int64_t T = np / TB;
     const int64_t ntiles = T * (T + 1) / 2;
     if (ntiles > 0x7fffffffLL) return GP_ERR_INVALID;
     const int ev = prof_start(s);
-    cov_fill_kernel<<<(unsigned)ntiles, 256, 0, s>>>(reinterpret_cast<const double2 *>(d_x), n, T,
-                                                     kp, d_C, ldc, d_info);
+    if (kp.use_df)
+        cov_fill_df_kernel<<<(unsigned)ntiles, 256, 0, s>>>(reinterpret_cast<const double2 *>(d_x), n,
+                                                            kp, d_C, ldc, d_info);
+    else
+        cov_fill_kernel<<<(unsigned)ntiles, 256, 0, s>>>(reinterpret_cast<const double2 *>(d_x), n,
+                                                         T, kp, d_C, ldc, d_info);
     GP_LAUNCH_CHECK();
     prof_stop(ev, s, GP_PROF_FILL, 0.0, 8.0 * (double)np * (double)(np + 1) / 2.0);
     return GP_OK;

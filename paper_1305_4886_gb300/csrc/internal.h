@@ -53,15 +53,19 @@ int trsv_persist(const double *L, int64_t ld, int64_t n, int trans, double *b, i
 
 // chol_mixed.cu
 size_t chol_mixed_ws_bytes(int64_t np, int S);
-int chol_mixed(double *A, int64_t ld, int64_t np, int S, void *ws, int64_t *info, cudaStream_t s);
+// winv (nullable, chol_winv_doubles(np) doubles): receives L_kk^{-1} of every
+// 512-column diagonal block (NB x NB each, in block order) for the inverse
+size_t chol_winv_doubles(int64_t np);
+int chol_mixed(double *A, int64_t ld, int64_t np, int S, void *ws, double *winv, int64_t *info,
+               cudaStream_t s);
 size_t syrk_ws_bytes(int64_t m, int64_t k, int precision, int S);
 int syrk_lower(double *C, int64_t ldc, const double *P, int64_t ldp, int64_t m, int64_t k,
                int precision, int S, void *ws, int64_t *info, cudaStream_t s);
 
 // adjoint.cu
 size_t grad_ws_bytes(int64_t np, int precision, int S);
-int chol_inverse(double *A, int64_t ld, int64_t np, int precision, int S, void *ws, int64_t *info,
-                 cudaStream_t s);
+int chol_inverse(double *A, int64_t ld, int64_t np, int precision, int S, void *ws,
+                 const double *winv, int64_t *info, cudaStream_t s);
 int grad_contract(const double *d_x, int64_t n, int64_t np, const KernParams &kp, const double *W,
                   int64_t ld, const double *alpha, void *ws, int precision, int S, double *grad,
                   const int64_t *info, cudaStream_t s);

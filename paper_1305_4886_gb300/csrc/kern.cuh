@@ -21,6 +21,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "kern_df.cuh"
 
 namespace gp {
 
@@ -33,10 +34,16 @@ struct KernParams {
     double diag;     // sigma2 + tau2
     double tau2;
     double tab[EXP_TAB];  // 2^(-j/64)
+    int use_df;           // evaluate off-diagonal entries in double-float (FP32 pipe)
+    KernDf kd;
 };
 
-inline KernParams make_kern(const gp_params &p) {
+// use_df: the tensor-core forms, whose operand slices carry 2^-32 of the row
+// bounds, take the double-float evaluation; the FP64 form stays in FP64.
+inline KernParams make_kern(const gp_params &p, bool use_df = false) {
     KernParams k;
+    k.use_df = use_df ? 1 : 0;
+    k.kd = make_kern_df(p);
     k.kind = p.kernel;
     k.s2 = p.sigma2;
     double c = 1.0;

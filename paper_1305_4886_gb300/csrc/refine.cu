@@ -74,6 +74,88 @@ __global__ void __launch_bounds__(256) cov_matvec_kernel(const double2 *__restri
     }
 }
 
+// The same symmetric tile matvec with the entries and products in
+// double-float on the FP32 pipe (tensor-core forms): row sums per thread,
+// column sums by warp shuffles of (hi, lo) pairs, one FP64 atomic per row
+// and column of the tile.
+__device__ __forceinline__ dfl df_shfl_xor(dfl v, int o) {
+    return {__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)};
+}
+
+__global__ void __launch_bounds__(256) cov_matvec_df_kernel(const double2 *__restrict__ x,
+                                                            int64_t n, KernParams kp,
+                                                            const double *__restrict__ a,
+                                                            double *acc, const int *skip,
+                                                            const int64_t *info) {
+    __shared__ float4 xc[TB];
+    __shared__ float2 tab[DF_TAB];
+    __shared__ float2 ac[TB];
+    __shared__ float2 colsum[2][TB];
+    __shared__ float2 rowsum[4][TB];
+    stage_df_table(kp.kd, tab);
+    if ((skip && *skip) || failed(info)) return;
+    int64_t ti, tj;
+    lower_tile_coords(blockIdx.x, ti, tj);
+    const int64_t row0 = ti * TB, col0 = tj * TB;
+    if (row0 >= n) return;
+    const int tid = threadIdx.x;
+    if (tid < TB) {
+        const int64_t j = col0 + tid;
+        xc[tid] = df_point(j < n ? x[j] : make_double2(0.0, 0.0));
+        const dfl aj = f64_to_df(static_cast<unsigned long long>(
+            __double_as_longlong(j < n ? a[j] : 0.0)));
+        ac[tid] = make_float2(aj.h, aj.l);
+        colsum[0][tid] = colsum[1][tid] = make_float2(0.0f, 0.0f);
+    }
+    __syncthreads();
+    const int r = tid & (TB - 1);
+    const int cg = tid >> 6;
+    const int half = (tid >> 5) & 1;
+    const int64_t i = row0 + r;
+    const bool diag = (ti == tj);
+    const bool row_ok = i < n;
+    const float4 xi = df_point(row_ok ? x[i] : make_double2(0.0, 0.0));
+    const dfl ai = f64_to_df(static_cast<unsigned long long>(__double_as_longlong(row_ok ? a[i] : 0.0)));
+    dfl rs{0.0f, 0.0f};
+    for (int c = cg; c < TB; c += 4) {
+        const int64_t j = col0 + c;
+        dfl v{0.0f, 0.0f};
+        if (row_ok && j < n) {
+            if (i == j) {
+                v = kp.kd.diag;
+            } else {
+                dfl unused;
+                df_cov<false>(kp.kind, kp.kd, df_dist(xi, xc[c]), tab, v, unused);
+            }
+        }
+        rs = df_add(rs, df_mul(v, dfl{ac[c].x, ac[c].y}));
+        if (!diag) {
+            dfl cs = df_mul(v, ai);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) cs = df_add(cs, df_shfl_xor(cs, o));
+            if ((tid & 31) == 0) colsum[half][c] = make_float2(cs.h, cs.l);  // one warp per (half, c)
+        }
+    }
+    rowsum[cg][r] = make_float2(rs.h, rs.l);
+    __syncthreads();
+    if (tid < TB) {
+        const int64_t ii = row0 + tid;
+        if (ii < n) {
+            dfl t{rowsum[0][tid].x, rowsum[0][tid].y};
+            for (int q = 1; q < 4; ++q) t = df_add(t, dfl{rowsum[q][tid].x, rowsum[q][tid].y});
+            atomicAdd(acc + ii, df_to_double(t));
+        }
+        if (!diag) {
+            const int64_t jj = col0 + tid;
+            if (jj < n) {
+                const dfl t = df_add(dfl{colsum[0][tid].x, colsum[0][tid].y},
+                                     dfl{colsum[1][tid].x, colsum[1][tid].y});
+                atomicAdd(acc + jj, df_to_double(t));
+            }
+        }
+    }
+}
+
 // s = r - acc over i < n; ||s||, ||r|| reduced in one CTA (deterministic);
 // stats[0] = ||s|| / ||r||.  Sets *conv when the ratio is <= tol (or r = 0).
 __global__ void __launch_bounds__(1024) refine_resid_kernel(const double *r, const double *acc,
@@ -118,8 +200,12 @@ int cov_matvec(const double *d_x, int64_t n, int64_t np, const KernParams &kp, c
     if (cudaMemsetAsync(acc, 0, sizeof(double) * n, s) != cudaSuccess) return GP_ERR_CUDA;
     const int64_t T = np / TB;
     const int ev = prof_start(s);
-    cov_matvec_kernel<<<(unsigned)(T * (T + 1) / 2), 256, 0, s>>>(
-        reinterpret_cast<const double2 *>(d_x), n, kp, a, acc, skip, info);
+    if (kp.use_df)
+        cov_matvec_df_kernel<<<(unsigned)(T * (T + 1) / 2), 256, 0, s>>>(
+            reinterpret_cast<const double2 *>(d_x), n, kp, a, acc, skip, info);
+    else
+        cov_matvec_kernel<<<(unsigned)(T * (T + 1) / 2), 256, 0, s>>>(
+            reinterpret_cast<const double2 *>(d_x), n, kp, a, acc, skip, info);
     GP_LAUNCH_CHECK();
     prof_stop(ev, s, GP_PROF_RESIDUAL, 0.0, 0.0);
     return GP_OK;

@@ -52,6 +52,7 @@
 #include <cudaTypedefs.h>
 
 #include "internal.h"
+#include "kern_df.cuh"
 #include "tc_gemm.h"
 #include "tc_ptx.cuh"
 
@@ -483,39 +484,13 @@ __device__ __forceinline__ unsigned long long split_get(const SplitArgs &a, int6
     return static_cast<unsigned long long>(__double_as_longlong(v));
 }
 
-// x = hi + lo with integer operations only (the FP64 pipe is the scarce one
-// on this part): hi keeps the top 24 significant bits (truncated), lo the
-// remaining 29 rounded to FP32.  Magnitudes below 2^-126 map to 0 and lo
-// parts below 2^-126 are dropped (negligible next to the row bounds used).
-__device__ __forceinline__ void f64_hi_lo(unsigned long long u, float &hi, float &lo) {
-    const unsigned int sign = static_cast<unsigned int>(u >> 32) & 0x80000000u;
-    const int E = static_cast<int>((u >> 52) & 0x7FF);
-    const int ef = E - 1023 + 127;
-    hi = 0.0f;
-    lo = 0.0f;
-    if (E == 0 || ef <= 0) return;
-    if (ef >= 255) {
-        hi = __int_as_float(sign | 0x7F800000u);
-        return;
-    }
-    const unsigned long long mant = u & 0x000FFFFFFFFFFFFFull;
-    hi = __int_as_float(sign | (static_cast<unsigned int>(ef) << 23) |
-                        static_cast<unsigned int>(mant >> 29));
-    const int es = E - 1075;  // weight of the mantissa's last bit
-    if (es >= -126) {
-        const float lf = __uint2float_rn(static_cast<unsigned int>(mant & 0x1FFFFFFFull));
-        lo = __int_as_float(__float_as_int(lf * __int_as_float((es + 127) << 23)) | sign);
-    }
-}
-
 // Normalized slices of one entry (mixed form), given the row's scale
 // sc = 2^{7-e}: with y = x sc held as a double-float (exact scaling),
 // s0 = round(y) (an integer in [-128, 128]), s1 = fp16(y - s0),
 // s2 = fp16(y - s0 - s1); y is then carried to about 2^-25 (2^{e-32} of x).
 __device__ __forceinline__ void split3_norm(unsigned long long u, float sc, uint16_t (&s)[3]) {
-    float xh, xl;
-    f64_hi_lo(u, xh, xl);
-    const float yh = xh * sc, yl = xl * sc;
+    const dfl x = f64_to_df(u);
+    const float yh = x.h * sc, yl = x.l * sc;
     const float q = rintf(yh);
     float t, e;
     two_sum(__fsub_rn(yh, q), yl, t, e);  // yh - q is exact
@@ -534,9 +509,8 @@ __device__ __forceinline__ void split3_norm(unsigned long long u, float sc, uint
 // exactly in FP32 (see the top of this file for the depth limits).
 __device__ __forceinline__ void split_ozaki(unsigned long long u, float sc, float isc,
                                             uint16_t (&s)[5]) {
-    float xh, xl;
-    f64_hi_lo(u, xh, xl);
-    float yh = xh * sc, yl = xl * sc, w = isc;
+    const dfl x = f64_to_df(u);
+    float yh = x.h * sc, yl = x.l * sc, w = isc;
 #pragma unroll
     for (int p = 0; p < 5; ++p) {
         const float q = rintf(yh);

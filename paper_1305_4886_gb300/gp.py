@@ -96,7 +96,7 @@ def lib():
             L.gp_workspace_bytes.restype = sz
             L.gp_chol_workspace_bytes.argtypes = [i64, ci]
             L.gp_chol_workspace_bytes.restype = sz
-            L.gp_cov_fill.argtypes = [p, i64, PP, p, i64, p]
+            L.gp_cov_fill.argtypes = [p, i64, PP, ci, p, i64, p]
             L.gp_chol.argtypes = [p, i64, i64, ci, p, sz, p, p]
             L.gp_backsolve.argtypes = [p, i64, i64, ci, p, p, p]
             L.gp_mult_chol.argtypes = [p, i64, i64, p, p, p]
@@ -181,11 +181,11 @@ def gp_chol_workspace_bytes(n, precision="fp64"):
     return lib().gp_chol_workspace_bytes(int(n), _prec(precision))
 
 
-def gp_cov_fill(x, prm, C, ldc=None, stream=None):
+def gp_cov_fill(x, prm, C, ldc=None, stream=None, precision="fp64"):
     n = x.shape[0]
     ldc = ldc if ldc is not None else C.shape[-1]
-    _check(lib().gp_cov_fill(_f64(x), n, ctypes.byref(prm), _f64(C), int(ldc), _stream(stream)),
-           "gp_cov_fill")
+    _check(lib().gp_cov_fill(_f64(x), n, ctypes.byref(prm), _prec(precision), _f64(C), int(ldc),
+                             _stream(stream)), "gp_cov_fill")
 
 
 def gp_chol(C, n, ldc, precision, ws, info, stream=None):

@@ -46,7 +46,7 @@ def test_exports_every_declared_symbol(libgp):
 
 def test_host_queries(libgp):
     L = libgp.lib()
-    assert L.gp_abi_version() == 1
+    assert L.gp_abi_version() == 2
     assert libgp.gp_padded_order(1) == 128
     assert libgp.gp_padded_order(128) == 128
     assert libgp.gp_padded_order(129) == 256
@@ -78,5 +78,6 @@ def test_invalid_arguments_rejected_before_any_device_work(libgp):
     assert L.gp_loglik(dummy, dummy, None, 1000, ctypes.byref(good), 0, dummy, 100, dummy,
                        None, dummy, None) == libgp.GP_ERR_WORKSPACE
     # leading dimension shorter than the padded order
-    assert L.gp_cov_fill(dummy, 200, ctypes.byref(good), dummy, 200, None) == libgp.GP_ERR_INVALID
+    assert L.gp_cov_fill(dummy, 200, ctypes.byref(good), 0, dummy, 200, None) == libgp.GP_ERR_INVALID
+    assert L.gp_cov_fill(dummy, 200, ctypes.byref(good), 7, dummy, 256, None) == libgp.GP_ERR_INVALID
     assert L.gp_backsolve(dummy, 10, 128, 2, dummy, dummy, None) == libgp.GP_ERR_INVALID
