@@ -167,7 +167,7 @@ def contraction_traffic(flops_per_launch, prec):
         if line.startswith("- ") and ":" in line:
             k, v = line[2:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
-    if vals.get("tc_gemm.cu sha256[:16]") != digest:
+    if vals.get("tc_gemm.cu sha256 prefix") != digest:
         return None
     key = f"bytes per slice-product flop ({prec})"
     if key not in vals or not flops_per_launch:
@@ -535,10 +535,12 @@ def run_batched(args, rank, world, local):
     line = {"metric": "batched GP loglik+grad evaluations/s (512 problems, n in [256, 4096])",
             "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64 + bf16 slices"
-            if prec == "mixed_f16" else "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"mixed_f16": "f64 + fp16 slices (fp32 accumulate)",
+                      "emu_fp64": "f64 + bf16 integer slices (fp32 accumulate)"}.get(prec, "f64"),
+            "data": "synthetic",
             "config": {"workload": "512 independent GPs, n log-uniform [256, 4096], 2-D uniform "
-                                   "locations, exp / Matern 3/2 alternating, y = L z",
+                                   "locations, exp / Matern 3/2 alternating, y ~ N(0, I)",
                        "precision": prec, "seed": 48865, "graph": "one CUDA graph per step"},
             "clocks": clk, "failed_problems": bad,
             "loglik_grad_alg_tflops": flops * args.steps / (ms / 1e3) / 1e12}
