@@ -246,9 +246,11 @@ int gp_loglik_grad(const double *d_x, const double *d_y, const double *d_mu, int
 // ---------------------------------------------------------------------------
 size_t gp_batched_workspace_bytes(int nprob, const int64_t *h_n, int precision) {
     if (nprob < 1 || !h_n || !precision_ok(precision)) return 0;
+    for (int i = 0; i < nprob; ++i)
+        if (h_n[i] < 1) return 0;
+    if (precision != GP_EMU_FP64) return dag_workspace_bytes(nprob, h_n, precision == GP_MIXED_F16);
     size_t tot = 0;
     for (int i = 0; i < nprob; ++i) {
-        if (h_n[i] < 1) return 0;
         tot += (loglik_ws_layout(nullptr, h_n[i], precision, 1).bytes + 255) & ~size_t(255);
     }
     return tot;
@@ -307,9 +309,16 @@ int gp_loglik_grad_batched(int nprob, const int64_t *h_n, const double *const *h
         if (h_n[i] < 1 || !h_dx[i] || !h_dy[i] || !params_ok(&h_prm[i])) return GP_ERR_INVALID;
     const size_t need = gp_batched_workspace_bytes(nprob, h_n, precision);
     if (!d_ws || ws_bytes < need) return GP_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (precision != GP_EMU_FP64) {
+        // one persistent task-graph launch (FP64 CUDA-core tiles, or tcgen05 slice tiles)
+        std::vector<KernParams> kps(nprob);
+        for (int i = 0; i < nprob; ++i) kps[i] = make_kern(h_prm[i], precision != GP_FP64);
+        return dag_run(nprob, h_n, h_dx, h_dy, h_dmu, kps.data(), precision == GP_MIXED_F16, d_ws,
+                       ws_bytes, d_out, d_grad, d_info, s);
+    }
     StreamPool *pool = nullptr;
     GP_TRY(batch_pool(&pool));
-    cudaStream_t s = (cudaStream_t)stream;
     // workspace offsets in problem order
     std::vector<size_t> off(nprob);
     size_t acc = 0;

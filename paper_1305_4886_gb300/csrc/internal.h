@@ -78,4 +78,10 @@ int refine_alpha(const double *d_x, int64_t n, int64_t np, const KernParams &kp,
                  double *stats, int *conv, int *tsync, int max_evals, double tol, int64_t *info,
                  cudaStream_t st);
 
+// batch_dag.cu / batch_dag_tc.cu (the batched evaluation as one persistent task-graph launch)
+size_t dag_workspace_bytes(int nprob, const int64_t *h_n, int mixed);
+int dag_run(int nprob, const int64_t *h_n, const double *const *h_dx, const double *const *h_dy,
+            const double *const *h_dmu, const KernParams *kps, int mixed, void *d_ws,
+            size_t ws_bytes, double *d_out, double *d_grad, int64_t *d_info, cudaStream_t s);
+
 }  // namespace gp

@@ -83,32 +83,42 @@ __device__ __forceinline__ double exp_neg(double a, const double *tab) {
     return __longlong_as_double(bits);
 }
 
-// sigma2 * k(d / rho) for a distinct pair at distance d.
-__device__ __forceinline__ double cov_offdiag(const KernParams &k, double d, const double *tab) {
-    const double a = d * k.scale;
+// sigma2 * k(d / rho) for a distinct pair at distance d (scale = sqrt(2 nu) / rho).
+__device__ __forceinline__ double cov_offdiag_s(int kind, double s2, double scale, double d,
+                                                const double *tab) {
+    const double a = d * scale;
     const double e = exp_neg(a, tab);
-    if (k.kind == GP_KERNEL_EXP) return k.s2 * e;
-    if (k.kind == GP_KERNEL_MATERN32) return k.s2 * fma(a, e, e);
-    return k.s2 * (1.0 + a + a * a * (1.0 / 3.0)) * e;
+    if (kind == GP_KERNEL_EXP) return s2 * e;
+    if (kind == GP_KERNEL_MATERN32) return s2 * fma(a, e, e);
+    return s2 * (1.0 + a + a * a * (1.0 / 3.0)) * e;
+}
+
+__device__ __forceinline__ double cov_offdiag(const KernParams &k, double d, const double *tab) {
+    return cov_offdiag_s(k.kind, k.s2, k.scale, d, tab);
 }
 
 // Off-diagonal entry and its derivative in log rho, -sigma2 u k'(u):
 //   exp: s2 a e^-a;  Matern 3/2: s2 a^2 e^-a;  Matern 5/2: s2 a^2 (1+a)/3 e^-a.
-__device__ __forceinline__ void cov_and_dlogrho(const KernParams &k, double d, double &c,
-                                                double &dr, const double *tab) {
-    const double a = d * k.scale;
+__device__ __forceinline__ void cov_and_dlogrho_s(int kind, double s2, double scale, double d,
+                                                  double &c, double &dr, const double *tab) {
+    const double a = d * scale;
     const double e = exp_neg(a, tab);
-    if (k.kind == GP_KERNEL_EXP) {
-        c = k.s2 * e;
+    if (kind == GP_KERNEL_EXP) {
+        c = s2 * e;
         dr = c * a;
-    } else if (k.kind == GP_KERNEL_MATERN32) {
-        c = k.s2 * fma(a, e, e);
-        dr = k.s2 * a * a * e;
+    } else if (kind == GP_KERNEL_MATERN32) {
+        c = s2 * fma(a, e, e);
+        dr = s2 * a * a * e;
     } else {
         const double p = 1.0 + a;
-        c = k.s2 * (p + a * a * (1.0 / 3.0)) * e;
-        dr = k.s2 * a * a * p * (1.0 / 3.0) * e;
+        c = s2 * (p + a * a * (1.0 / 3.0)) * e;
+        dr = s2 * a * a * p * (1.0 / 3.0) * e;
     }
+}
+
+__device__ __forceinline__ void cov_and_dlogrho(const KernParams &k, double d, double &c,
+                                                double &dr, const double *tab) {
+    cov_and_dlogrho_s(k.kind, k.s2, k.scale, d, c, dr, tab);
 }
 
 __device__ __forceinline__ double pair_dist(double2 p, double2 q) {

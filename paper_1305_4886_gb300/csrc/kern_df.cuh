@@ -156,10 +156,10 @@ __device__ __forceinline__ dfl df_exp_neg(dfl a, const float2 *tab) {
 //   exp: s2 e^-a, s2 a e^-a;  Matern 3/2: s2 (1+a) e^-a, s2 a^2 e^-a;
 //   Matern 5/2: s2 (1+a+a^2/3) e^-a, s2 a^2 (1+a)/3 e^-a.
 template <bool WANT_DR>
-__device__ __forceinline__ void df_cov(int kind, const KernDf &kd, dfl d, const float2 *tab,
-                                       dfl &c, dfl &dr) {
-    const dfl a = df_mul(d, kd.scale);
-    const dfl e = df_mul(df_exp_neg(a, tab), kd.s2);
+__device__ __forceinline__ void df_cov_s(int kind, dfl scale, dfl s2, dfl d, const float2 *tab,
+                                         dfl &c, dfl &dr) {
+    const dfl a = df_mul(d, scale);
+    const dfl e = df_mul(df_exp_neg(a, tab), s2);
     if (kind == GP_KERNEL_EXP) {
         c = e;
         if (WANT_DR) dr = df_mul(e, a);
@@ -173,6 +173,12 @@ __device__ __forceinline__ void df_cov(int kind, const KernDf &kd, dfl d, const 
         c = df_mul(df_add(p, a2_3), e);
         if (WANT_DR) dr = df_mul(df_mul(a2_3, p), e);
     }
+}
+
+template <bool WANT_DR>
+__device__ __forceinline__ void df_cov(int kind, const KernDf &kd, dfl d, const float2 *tab,
+                                       dfl &c, dfl &dr) {
+    df_cov_s<WANT_DR>(kind, kd.scale, kd.s2, d, tab, c, dr);
 }
 
 // FP64 x = hi + lo with integer operations only (no FP64 pipe): hi keeps

@@ -3,8 +3,9 @@
 Small batches of uneven n are checked problem by problem against the FP64
 oracle.  The full 512-problem workload (n log-uniform in [256, 4096],
 exponential / Matern 3/2 alternating) is checked against the single-problem
-entry point on a sample and for per-problem status; a CUDA-graph capture of
-the batch must reproduce the eager results exactly.
+FP64 entry point on a sample and for per-problem status; a CUDA-graph
+capture of the batch must reproduce the eager results exactly (the task
+graph's arithmetic does not depend on which CTA runs a task).
 """
 import math
 
@@ -62,12 +63,15 @@ def test_batched_full_workload_and_graph(g):
     out = r["out"].cpu().numpy().copy()
     grad = r["grad"].cpu().numpy().copy()
     assert np.all(np.isfinite(out[:, :3])) and np.all(np.isfinite(grad))
-    # the single-problem entry point gives the same numbers (same kernels)
+    # against the single-problem FP64 path on a sample (the batched mixed form
+    # runs its own tile tasks): the mixed-form bound, 1e-6 relative
     for i in [0, 1, 77, 300, 511]:
         p = probs[i]
-        s = g.loglik_grad(xs[i], zs[i], p.kernel, p.s2, p.rho, p.tau2, precision="mixed_f16")
-        assert rel_err(out[i, 0], float(s["out"][0])) < 1e-12
-        assert np.max(np.abs(grad[i] - s["grad"].cpu().numpy())) <= 1e-9 * np.max(np.abs(grad[i]))
+        s = g.loglik_grad(xs[i], zs[i], p.kernel, p.s2, p.rho, p.tau2, precision="fp64")
+        assert rel_err(out[i, 0], float(s["out"][0])) < 1e-6, (i, p.n)
+        ref = s["grad"].cpu().numpy()
+        assert np.max(np.abs(grad[i] - ref)) <= 1e-6 * np.max(np.abs(ref)), (i, p.n)
+        assert out[i, 3] <= 1e-10, (i, out[i, 3])  # refinement residual
     # capture the whole batch in one CUDA graph and replay it
     batch, ws = r["batch"], r["ws"]
     o2 = torch.zeros_like(r["out"])
