@@ -531,6 +531,23 @@ def run_batched(args, rank, world, local):
     ms = float(tm.item())
     bad = int((info != 0).sum().item())
     flops = sum(float(p.n) ** 3 for p in probs)
+    task_stats = None
+    if prec in ("fp64", "mixed_f16"):
+        # one more (untimed) batch with the task graph's cycle counters on:
+        # where the persistent launch spends its CTA time, per task class
+        gp.gp_batched_profile(True)
+        gp.gp_loglik_grad_batched(batch, prec, ws, out, grad, info)
+        torch.cuda.synchronize()
+        gp.gp_batched_profile(False)
+        st = gp.gp_batched_task_stats(ws)
+        mhz = clk.get("sm_mhz") or 2070.0
+        task_stats = {k: {"cta_ms": v["cycles"] / (mhz * 1e3), "wait_ms": v["wait_cycles"] / (mhz * 1e3),
+                          "tasks": v["tasks"]}
+                      for k, v in st.items() if k != "steps" and v["tasks"]}
+        if st["steps"]:
+            # one step: a 128 x 128 x 128 tile product, six 16-bit slice products
+            task_stats["tensor_steps"] = st["steps"]
+            task_stats["slice_tflops_per_step_time"] = st["steps"] * 6 * 2 * 128.0 ** 3 / (ms / args.steps / 1e3) / 1e12
     value = len(probs) * args.steps / (ms / 1e3)
     line = {"metric": "batched GP loglik+grad evaluations/s (512 problems, n in [256, 4096])",
             "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
@@ -544,6 +561,8 @@ def run_batched(args, rank, world, local):
                        "precision": prec, "seed": 48865, "graph": "one CUDA graph per step"},
             "clocks": clk, "failed_problems": bad,
             "loglik_grad_alg_tflops": flops * args.steps / (ms / 1e3) / 1e12}
+    if task_stats:
+        line["task_stats"] = task_stats
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -173,19 +173,37 @@ int gp_loglik_grad(const double *d_x, const double *d_y, const double *d_mu, int
  * h_n (sizes), h_dx / h_dy (device pointers to locations and data), h_dmu
  * (NULL, or device pointers to means, each NULL = 0), h_prm (parameters).
  * Device outputs: d_out (nprob x 4, as gp_loglik), d_grad (nprob x 3),
- * d_info (nprob, per-problem status as d_info of gp_loglik).  d_ws:
- * gp_batched_workspace_bytes; problem i owns a slice of it.
- * The problems run on a pool of library streams (created on the first
- * batched call on a device and kept for the process), largest first with a
- * longest-processing-time assignment; the pool forks from `stream` and
- * joins back to it with events, so every result is ordered after the call
- * on `stream`, and a capture of `stream` records the whole batch as one
- * CUDA graph (make the first call outside a capture).                      */
+ * d_info (nprob, per-problem status as d_info of gp_loglik; -1 also when
+ * the launch stopped on a wait limit).  d_ws: gp_batched_workspace_bytes
+ * (nprob <= 65535), owned by the caller and not read across calls.
+ * GP_FP64 and GP_MIXED_F16 run the whole batch as ONE persistent kernel
+ * over a task graph of tile tasks (fill, Cholesky, solves, refinement,
+ * inverse, gradient) of every problem, after a few small set-up kernels
+ * that copy the problem descriptors (as kernel parameters) and order the
+ * tasks; every launch is on `stream`, nothing is allocated and the host
+ * never waits, so a capture of `stream` records the batch as one CUDA
+ * graph.  GP_EMU_FP64 runs each problem's single-problem launch sequence
+ * on a pool of library streams (created on the first such call on a
+ * device, forked from and joined back to `stream` with events; make the
+ * first call outside a capture).                                          */
 size_t gp_batched_workspace_bytes(int nprob, const int64_t *h_n, int precision);
 int gp_loglik_grad_batched(int nprob, const int64_t *h_n, const double *const *h_dx,
                            const double *const *h_dy, const double *const *h_dmu,
                            const gp_params *h_prm, int precision, void *d_ws, size_t ws_bytes,
                            double *d_out, double *d_grad, int64_t *d_info, void *stream);
+
+/* Diagnostics of the persistent batched launch.  gp_batched_profile(1)
+ * makes later batched calls count SM cycles per task class (off by default,
+ * or on with GP_DAG_PROFILE=1 in the environment).  After a synchronisation,
+ * gp_batched_task_stats copies the counters of the last batched call on
+ * d_ws into h_out[31]: cycles [0..9], of which waiting for inputs [10..19],
+ * tasks [20..29] per class (0 off-diagonal Cholesky tile, 1 solve,
+ * 2 inverse tile, 3 inverse-product + gradient tile, 4 gradient sum,
+ * 5 refinement residual, 6 refinement correction, 7 log-likelihood,
+ * 8 diagonal Cholesky tile), then [30] tensor-core contraction steps.
+ * Synchronous (one device-to-host copy).                                  */
+void gp_batched_profile(int on);
+int gp_batched_task_stats(const void *d_ws, unsigned long long *h_out);
 
 /* Log-likelihood without any workspace or allocation (GP_FP64 only).  The
  * paper has no counterpart: this entry point serves callers that cannot

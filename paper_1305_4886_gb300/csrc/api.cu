@@ -369,6 +369,13 @@ int gp_loglik_grad_batched(int nprob, const int64_t *h_n, const double *const *h
     return status;
 }
 
+void gp_batched_profile(int on) { dag_set_profile(on); }
+
+int gp_batched_task_stats(const void *d_ws, unsigned long long *h_out) {
+    if (!d_ws || !h_out) return GP_ERR_INVALID;
+    return dag_stats(d_ws, h_out);
+}
+
 size_t gp_syrk_workspace_bytes(int64_t m, int64_t k, int precision) {
     if (m < 1 || k < 1 || !precision_ok(precision)) return 0;
     return syrk_ws_bytes(m, k, precision, slices_of(precision));

@@ -37,6 +37,8 @@
 #include "batch_dag.h"
 
 #include <algorithm>
+#include <atomic>
+#include <stdlib.h>
 #include <string.h>
 #include <vector>
 
@@ -50,8 +52,8 @@ __device__ bool task_chol(const DagProb &P, int i, int j, DagSmem &sm, DagHdr *h
         double acc[4][4];
         fill_tile(P, i, j, acc, sm);
         for (int k = 0; k < j; ++k) {
-            if (!dag_wait(Lf + tile_index(T, i, k), 1, h, P.info, &sm.ok)) return false;
-            if (i != j && !dag_wait(Lf + tile_index(T, j, k), 1, h, P.info, &sm.ok)) return false;
+            if (!dag_wait(Lf + tile_index(T, i, k), 1, h, P.info, sm.ok)) return false;
+            if (i != j && !dag_wait(Lf + tile_index(T, j, k), 1, h, P.info, sm.ok)) return false;
             tile_mma<0, 1, true>(acc, tile_ptr(P.A, T, i, k), tile_ptr(P.A, T, j, k), sm);
         }
         __syncthreads();
@@ -61,7 +63,7 @@ __device__ bool task_chol(const DagProb &P, int i, int j, DagSmem &sm, DagHdr *h
             potrf_inv_tile(P, j, tile_ptr(P.A, T, j, j), tile_ptr(P.X, T, j, j), P.part + j, sm);
         } else {
             // L_ij = A'_ij W_j^T, W_j = X_jj
-            if (!dag_wait(Lf + tile_index(T, j, j), 1, h, P.info, &sm.ok)) return false;
+            if (!dag_wait(Lf + tile_index(T, j, j), 1, h, P.info, sm.ok)) return false;
             stage_b<1>(tile_ptr(P.X, T, j, j), sm.sB);
             __syncthreads();
             double l[4][4];
@@ -101,11 +103,11 @@ __device__ bool task_solve(const DagProb &P, DagSmem &sm, DagHdr *h) {
         for (int i = 0; i < T; ++i) {
             double s = 0.0;
             for (int j = 0; j < i; ++j) {
-                if (!dag_wait(Lf + tile_index(T, i, j), 1, h, P.info, &sm.ok)) return false;
+                if (!dag_wait(Lf + tile_index(T, i, j), 1, h, P.info, sm.ok)) return false;
                 const double *L = tile_ptr(P.A, T, i, j);
                 for (int c = q; c < DB; c += 4) s = fma(__ldcg(L + row + DB * c), v[(int64_t)j * DB + c], s);
             }
-            if (!dag_wait(Lf + tile_index(T, i, i), 1, h, P.info, &sm.ok)) return false;
+            if (!dag_wait(Lf + tile_index(T, i, i), 1, h, P.info, sm.ok)) return false;
             sm.red[q][row] = s;
             __syncthreads();
             if (tid < DB) sm.vr[tid] = r[(int64_t)i * DB + tid] - (sm.red[0][tid] + sm.red[1][tid] + sm.red[2][tid] + sm.red[3][tid]);
@@ -166,11 +168,11 @@ __device__ bool task_trtri(const DagProb &P, int i, int k, DagSmem &sm, DagHdr *
         double acc[4][4];
         acc_zero(acc);
         for (int m = i; m > k; --m) {
-            if (!dag_wait(Xf + tile_index(T, i, m), 1, h, P.info, &sm.ok)) return false;
-            if (!dag_wait(Lf + tile_index(T, m, k), 1, h, P.info, &sm.ok)) return false;
+            if (!dag_wait(Xf + tile_index(T, i, m), 1, h, P.info, sm.ok)) return false;
+            if (!dag_wait(Lf + tile_index(T, m, k), 1, h, P.info, sm.ok)) return false;
             tile_mma<0, 0, false>(acc, tile_ptr(P.X, T, i, m), tile_ptr(P.A, T, m, k), sm);
         }
-        if (!dag_wait(Xf + tile_index(T, k, k), 1, h, P.info, &sm.ok)) return false;
+        if (!dag_wait(Xf + tile_index(T, k, k), 1, h, P.info, sm.ok)) return false;
         __syncthreads();
         acc_to_sA(acc, sm.sA);
         stage_b<0>(tile_ptr(P.X, T, k, k), sm.sB);
@@ -195,11 +197,11 @@ __device__ bool task_lg(const DagProb &P, int i, int j, DagSmem &sm, DagHdr *h) 
         double w[4][4];
         acc_zero(w);
         for (int mm = i; mm < T; ++mm) {
-            if (!dag_wait(Xf + tile_index(T, mm, i), 1, h, P.info, &sm.ok)) return false;
-            if (!dag_wait(Xf + tile_index(T, mm, j), 1, h, P.info, &sm.ok)) return false;
+            if (!dag_wait(Xf + tile_index(T, mm, i), 1, h, P.info, sm.ok)) return false;
+            if (!dag_wait(Xf + tile_index(T, mm, j), 1, h, P.info, sm.ok)) return false;
             tile_mma<1, 0, false>(w, tile_ptr(P.X, T, mm, i), tile_ptr(P.X, T, mm, j), sm);
         }
-        if (!dag_wait(solved, 1, h, P.info, &sm.ok)) return false;
+        if (!dag_wait(solved, 1, h, P.info, sm.ok)) return false;
         const double *al = P.vec + 2 * m;
         if (tid < DB) {
             const int64_t gi = (int64_t)i * DB + tid, gj = (int64_t)j * DB + tid;
@@ -259,7 +261,7 @@ __device__ bool task_final(const DagProb &P, DagSmem &sm, DagHdr *h) {
     const int T = P.T, tid = threadIdx.x;
     int *lgc = P.flag + dag_lg_flag(T, 0);
     const int nt = dag_ntiles(T);
-    if (!dag_wait(lgc, nt, h, P.info, &sm.ok)) return false;
+    if (!dag_wait(lgc, nt, h, P.info, sm.ok)) return false;
     // Neumaier sums per thread, then in thread order
     double s[3] = {0.0, 0.0, 0.0}, c[3] = {0.0, 0.0, 0.0};
     for (int t = tid; t < nt; t += DAG_THREADS)
@@ -301,6 +303,7 @@ __global__ void __launch_bounds__(DAG_THREADS, 2)
         const DagProb &P = probs[e.x];
         int i = 0, k = 0;
         const int type = dag_decode(P.T, 0, e.y, i, k);
+        const long long c0 = dag_stat_begin(h, sm.ok);
         bool ok = true;
         switch (type) {
             case DT_CHOL: ok = task_chol(P, i, k, sm, h); break;
@@ -309,6 +312,7 @@ __global__ void __launch_bounds__(DAG_THREADS, 2)
             case DT_LG: ok = task_lg(P, i, k, sm, h); break;
             default: ok = task_final(P, sm, h); break;
         }
+        dag_stat_end(h, (type == DT_CHOL && i == k) ? 8 : type, c0, sm.ok);
         if (!ok) break;
     }
 }
@@ -329,7 +333,7 @@ __global__ void dag_finish_kernel(const DagHdr *h, const DagProb *probs, int P) 
 // --------------------------------------------------------------------------
 constexpr int DAG_SETUP_CHUNK = 128;
 struct DagSetup {
-    int first, count;
+    int first, count, prof, pad_;
     double tab[EXP_TAB];
     float2 dftab[DF_TAB];
     DagProb p[DAG_SETUP_CHUNK];
@@ -337,13 +341,14 @@ struct DagSetup {
 static_assert(sizeof(DagSetup) <= 32000, "descriptor chunk exceeds the kernel-parameter limit");
 
 __global__ void dag_setup_kernel(const __grid_constant__ DagSetup s, DagProb *probs, double *tab,
-                                 float2 *dftab) {
+                                 float2 *dftab, void *hdr_raw) {
     const int t = threadIdx.x;
     if (t < s.count) {
         probs[s.first + t] = s.p[t];
         *s.p[t].info = 0;
     }
     if (s.first == 0) {
+        if (t == 0) reinterpret_cast<DagHdr *>(hdr_raw)->prof = s.prof;
         if (t < EXP_TAB) tab[t] = s.tab[t];
         for (int q = t; q < DF_TAB; q += blockDim.x) dftab[q] = s.dftab[q];
     }
@@ -422,7 +427,7 @@ struct DagLayout {
     size_t flags = 0, flags_bytes = 0, probs = 0, tab = 0, dftab = 0, list = 0, poff = 0, rtot = 0,
            roff = 0, scratch = 0;
     std::vector<int> T, ntasks, order;
-    std::vector<size_t> A, X, vec, part, flag, LSr, LSc, XSr, XSc, L32;
+    std::vector<size_t> A, X, vec, part, flag, LSr, LSc, XSr, XSc, L32, rp;
     size_t total = 0;
 };
 
@@ -468,7 +473,8 @@ static DagLayout dag_layout(int P, const int64_t *h_n, int mixed, int scratch_ct
     off = al1k(off + sizeof(int) * (L.R + 1));
     L.scratch = off;
     if (mixed) off = al1k(off + (size_t)scratch_ctas * QSCRATCH_DOUBLES * sizeof(double));
-    for (auto *v : {&L.A, &L.X, &L.vec, &L.part, &L.LSr, &L.LSc, &L.XSr, &L.XSc, &L.L32}) v->assign(P, 0);
+    for (auto *v : {&L.A, &L.X, &L.vec, &L.part, &L.LSr, &L.LSc, &L.XSr, &L.XSc, &L.L32, &L.rp})
+        v->assign(P, 0);
     for (int s = 0; s < P; ++s) {
         const size_t nt = dag_ntiles(L.T[s]);
         const size_t m = (size_t)L.T[s] * L.tb;
@@ -484,11 +490,13 @@ static DagLayout dag_layout(int P, const int64_t *h_n, int mixed, int scratch_ct
             }
             L.L32[s] = off;
             off = al1k(off + sizeof(float) * nt * QB * QB);
+            L.rp[s] = off;
+            off = al256(off + sizeof(double) * nt * 2 * QB);
         }
         L.vec[s] = off;
         off = al256(off + sizeof(double) * (mixed ? 4 : 3) * m);
         L.part[s] = off;
-        off = al256(off + sizeof(double) * (L.T[s] + 3 * nt + (mixed ? DAG_EVALS * L.T[s] + 4 : 0)));
+        off = al256(off + sizeof(double) * (L.T[s] + 3 * nt + (mixed ? 4 : 0)));
     }
     L.total = off;
     return L;
@@ -507,6 +515,20 @@ static int dag_tc_ctas() {
     return n;
 }
 
+// Per-class cycle counters of the batched launches (diagnostics): off unless
+// turned on by dag_set_profile or GP_DAG_PROFILE=1.
+static std::atomic<int> g_dag_prof{-1};
+void dag_set_profile(int on) { g_dag_prof.store(on ? 1 : 0); }
+static bool dag_profiling() {
+    int v = g_dag_prof.load();
+    if (v < 0) {
+        const char *e = getenv("GP_DAG_PROFILE");
+        v = (e && e[0] == '1') ? 1 : 0;
+        g_dag_prof.store(v);
+    }
+    return v == 1;
+}
+
 size_t dag_workspace_bytes(int nprob, const int64_t *h_n, int mixed) {
     return dag_layout(nprob, h_n, mixed, mixed ? std::max(dag_tc_ctas(), 1) : 0).total;
 }
@@ -515,6 +537,8 @@ int dag_run(int nprob, const int64_t *h_n, const double *const *h_dx, const doub
             const double *const *h_dmu, const KernParams *kps, int mixed, void *d_ws,
             size_t ws_bytes, double *d_out, double *d_grad, int64_t *d_info, cudaStream_t s) {
     if (nprob > 65535) return GP_ERR_INVALID;
+    for (int i = 0; i < nprob; ++i)  // tile indices of a problem stay below 2^15 per side
+        if (ceil_div(h_n[i], mixed ? QB : DB) > 8192) return GP_ERR_INVALID;
     const int tc_ctas = mixed ? dag_tc_ctas() : 0;
     if (mixed && tc_ctas < 1) return GP_ERR_CUDA;
     const DagLayout L = dag_layout(nprob, h_n, mixed, tc_ctas);
@@ -543,6 +567,7 @@ int dag_run(int nprob, const int64_t *h_n, const double *const *h_dx, const doub
         memset(&su, 0, sizeof(su));
         su.first = s0;
         su.count = std::min(DAG_SETUP_CHUNK, nprob - s0);
+        su.prof = dag_profiling() ? 1 : 0;
         for (int q = 0; q < EXP_TAB; ++q) su.tab[q] = kps[0].tab[q];
         for (int q = 0; q < DF_TAB; ++q) su.dftab[q] = kps[0].kd.tab[q];
         for (int q = 0; q < su.count; ++q) {
@@ -560,6 +585,7 @@ int dag_run(int nprob, const int64_t *h_n, const double *const *h_dx, const doub
                 d.XSr = reinterpret_cast<uint8_t *>(base + L.XSr[sidx]);
                 d.XSc = reinterpret_cast<uint8_t *>(base + L.XSc[sidx]);
                 d.L32 = reinterpret_cast<float *>(base + L.L32[sidx]);
+                d.rp = reinterpret_cast<double *>(base + L.rp[sidx]);
             }
             d.vec = reinterpret_cast<double *>(base + L.vec[sidx]);
             d.part = reinterpret_cast<double *>(base + L.part[sidx]);
@@ -580,7 +606,7 @@ int dag_run(int nprob, const int64_t *h_n, const double *const *h_dx, const doub
             d.ds2 = kps[o].kd.s2;
             d.ddiag = kps[o].kd.diag;
         }
-        dag_setup_kernel<<<1, DAG_SETUP_CHUNK, 0, s>>>(su, probs, tab, dftab);
+        dag_setup_kernel<<<1, DAG_SETUP_CHUNK, 0, s>>>(su, probs, tab, dftab, hdr);
         GP_LAUNCH_CHECK();
     }
     int *poff = reinterpret_cast<int *>(base + L.poff);
@@ -611,6 +637,20 @@ int dag_run(int nprob, const int64_t *h_n, const double *const *h_dx, const doub
     }
     dag_finish_kernel<<<(unsigned)ceil_div(nprob, 128), 128, 0, s>>>(hdr, probs, nprob);
     GP_LAUNCH_CHECK();
+    return GP_OK;
+}
+
+// Copy the counters of the last batched launch on this workspace (after a
+// synchronisation): per class cycles, wait cycles, tasks; then steps.
+int dag_stats(const void *d_ws, unsigned long long *h_out) {
+    DagHdr hd;
+    if (cudaMemcpy(&hd, d_ws, sizeof(hd), cudaMemcpyDeviceToHost) != cudaSuccess) return GP_ERR_CUDA;
+    for (int q = 0; q < DAG_NSTAT; ++q) {
+        h_out[q] = hd.cyc[q];
+        h_out[DAG_NSTAT + q] = hd.wait[q];
+        h_out[2 * DAG_NSTAT + q] = hd.cnt[q];
+    }
+    h_out[3 * DAG_NSTAT] = hd.steps;
     return GP_OK;
 }
 

@@ -36,6 +36,7 @@ struct DagProb {
     uint8_t *LSr, *LSc;  // mixed: slice stores of the L tiles (rows / columns as K-major rows)
     uint8_t *XSr, *XSc;  // mixed: slice stores of the L^{-1} tiles (diagonal: W_j)
     float *L32;          // mixed: FP32 tiles for the correction solves (L_ij, diagonal W_j)
+    double *rp;          // mixed: residual partials per tile, C_ij a_j and C_ij^T a_i (2 x 128)
     int64_t n;
     int T;
     int ntasks;
@@ -46,10 +47,18 @@ struct DagProb {
     int pad_;
 };
 
+constexpr int DAG_NSTAT = 10;  // task classes of the optional cycle counters
+
 struct DagHdr {
     int next;   // ticket of the next task in the global list
     int abort;  // a wait timed out: every CTA stops
-    int pad_[14];
+    int prof;   // count cycles per task class (diagnostics)
+    int pad_[13];
+    unsigned long long cyc[DAG_NSTAT];   // SM cycles inside tasks of the class
+    unsigned long long wait[DAG_NSTAT];  // of which spent waiting for inputs
+    unsigned long long cnt[DAG_NSTAT];   // tasks
+    unsigned long long steps;            // tensor-core contraction steps (mixed)
+    unsigned long long pad2_[7];
 };
 
 __host__ __device__ inline int dag_ntiles(int T) { return T * (T + 1) / 2; }
@@ -58,7 +67,8 @@ constexpr int DAG_CHAIN = 2 * DAG_EVALS;  // chain stages: RES(e), CORR(e) ..., 
 
 __host__ __device__ inline int dag_ntasks(int T, int mixed) {
     if (!mixed) return dag_ntiles(T) + 1 + T * (T - 1) / 2 + dag_ntiles(T) + 1;
-    return dag_ntiles(T) + 1 + T * (T - 1) / 2 + DAG_EVALS * T + DAG_EVALS + dag_ntiles(T) + 1;
+    return dag_ntiles(T) + 1 + T * (T - 1) / 2 + DAG_EVALS * dag_ntiles(T) + DAG_EVALS +
+           dag_ntiles(T) + 1;
 }
 
 // Flags per problem.  FP64: L (ntiles), X (ntiles), solve, LG count.
@@ -91,9 +101,10 @@ __device__ inline void dag_decode_xt(int T, int q, int &i, int &k) {
 // Local task q of a problem with T tiles -> (type, i, k).  Order: CHOL by
 // tile columns (diagonal first), SOLVE, TRTRI by columns from the right,
 // LG by columns from the right, FINAL.  The mixed form threads its
-// refinement chain (RES(e, i) for every tile row, then CORR(e); after the
-// last evaluation FINLL) through the TRTRI tasks in DAG_CHAIN segments, so
-// that each stage of the chain sits well after the one it waits for.
+// refinement chain (RES(e) for every lower tile, then CORR(e); after the last
+// evaluation FINLL) through the TRTRI tasks in DAG_CHAIN segments, so that
+// each stage of the chain sits well after the one it waits for.  A RES task
+// returns its tile as i = row | (column << 16) and the evaluation in k.
 __device__ inline int dag_decode(int T, int mixed, int q, int &i, int &k) {
     const int nc = dag_ntiles(T);
     if (q < nc) {
@@ -126,11 +137,17 @@ __device__ inline int dag_decode(int T, int mixed, int q, int &i, int &k) {
                 return DT_TRTRI;
             }
             q -= seg;
-            const int st = (s & 1) ? 1 : T;  // RES(e): T tasks; CORR(e) / FINLL: 1
+            const int st = (s & 1) ? 1 : nc;  // RES(e): one task per tile; CORR(e) / FINLL: 1
             if (q < st) {
                 k = s >> 1;  // evaluation
-                i = q;       // tile row (RES)
-                return (s & 1) ? (s == DAG_CHAIN - 1 ? DT_FINLL : DT_CORR) : DT_RES;
+                if (s & 1) return s == DAG_CHAIN - 1 ? DT_FINLL : DT_CORR;
+                int jj = 0;  // RES tile (i, jj) in column order; jj returned through k's pair
+                while (q >= T - jj) {
+                    q -= T - jj;
+                    ++jj;
+                }
+                i = (jj + q) | (jj << 16);
+                return DT_RES;
             }
             q -= st;
         }
@@ -176,10 +193,11 @@ struct DagSmem {
     double dinv[DB];
     double lj[DB];
     double wred[3][8];
-    int ok;
     int bad;
     int badcol;
     int task;
+    int pad_;
+    int ok[4];  // verdict of the last wait, spin cycles (as one 64-bit value at ok + 2)
 };
 
 // --------------------------------------------------------------------------
@@ -198,11 +216,14 @@ __device__ __forceinline__ int ld_relaxed_gpu(const int *p) {
 }
 
 // Wait (thread 0, bounded) until *f >= target; every thread gets the verdict.
+// okslot[0]: the verdict; okslot[2..3]: cycles spent spinning (accumulated
+// for the optional counters).
 static __device__ bool dag_wait(const int *f, int target, DagHdr *h, int64_t *info, int *okslot) {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
         if (ld_acquire_gpu(f) < target) {
+            const long long c0 = clock64();
             const uint64_t t0 = globaltimer_ns();
             for (uint32_t it = 0;; ++it) {
                 if (ld_acquire_gpu(f) >= target) break;
@@ -219,11 +240,25 @@ static __device__ bool dag_wait(const int *f, int target, DagHdr *h, int64_t *in
                     break;
                 }
             }
+            *reinterpret_cast<long long *>(okslot + 2) += clock64() - c0;
         }
         *okslot = ok;
     }
     __syncthreads();
     return *okslot != 0;
+}
+
+// Optional per-class cycle counters around one task (thread 0).
+__device__ __forceinline__ long long dag_stat_begin(const DagHdr *h, int *okslot) {
+    if (!h->prof || threadIdx.x != 0) return 0;
+    *reinterpret_cast<long long *>(okslot + 2) = 0;
+    return clock64();
+}
+__device__ __forceinline__ void dag_stat_end(DagHdr *h, int cls, long long c0, const int *okslot) {
+    if (!h->prof || threadIdx.x != 0) return;
+    atomicAdd(&h->cyc[cls], (unsigned long long)(clock64() - c0));
+    atomicAdd(&h->wait[cls], (unsigned long long)*reinterpret_cast<const long long *>(okslot + 2));
+    atomicAdd(&h->cnt[cls], 1ull);
 }
 
 // All of the CTA's writes so far, then *f += 1 with release semantics.

@@ -151,6 +151,7 @@ __device__ void tc_issue(const TcCtx &c) {
             }
     }
     mma_commit(c.mbar);
+    if (c.h->prof) atomicAdd(&c.h->steps, 1ull);
 }
 
 // Every thread waits for the step's MMAs (bounded; a second bounded wait
@@ -572,49 +573,102 @@ __device__ bool tc_trtri(TcCtx &c, const DagProb &P, int i, int k) {
 
 // FP32 solves by the low-precision factor: b <- L^{-T} L^{-1} b on the
 // problem's padded vector (FP64 storage), tile rows with W_i on the diagonal.
+// Every FP32 tile streams through two shared-memory buffers (cp.async,
+// columns padded to 132 floats): the forward sweep reads tile columns
+// (lanes = rows), the backward sweep tile rows as float4 (lanes = columns),
+// both without bank conflicts.
+constexpr int SLD = 132;                    // padded column stride (floats)
+constexpr int SBUF = QB * SLD * 4;          // one staged tile (bytes)
+
+__device__ __forceinline__ void stage_l32(float *dst, const float *src) {
+    for (int e = threadIdx.x; e < QB * 32; e += QTHREADS) {
+        const int col = e >> 5, q = e & 31;
+        cp_async16(dst + col * SLD + 4 * q, src + col * QB + 4 * q);
+    }
+    cp_async_commit();
+}
+
 __device__ void lowp_solve(TcCtx &c, const DagProb &P, double *b, double *t) {
     const int T = P.T, tid = threadIdx.x, r = tid & (QB - 1), h = tid >> 7;
+    float *buf0 = reinterpret_cast<float *>(c.opA), *buf1 = reinterpret_cast<float *>(c.opA + SBUF);
     float *red = reinterpret_cast<float *>(c.red);  // [2][128]
     float *tv = red + 2 * QB;                       // [128]
-    // forward: t_i = W_i (b_i - sum_{j<i} L_ij t_j)
+    // forward: t_i = W_i (b_i - sum_{j<i} L_ij t_j); steps j = 0..i-1, then W_i
     for (int i = 0; i < T; ++i) {
         float s = 0.0f;
-        for (int j = 0; j < i; ++j) {
-            const float *L = l32_tile(P, i, j);
-            const double *tj = t + (int64_t)j * QB;
-            for (int col = 64 * h; col < 64 * h + 64; ++col) s = fmaf(__ldcg(L + r + QB * col), (float)tj[col], s);
+        __syncthreads();
+        stage_l32(buf0, l32_tile(P, i, i == 0 ? 0 : 0));
+        for (int st = 0; st <= i; ++st) {
+            float *cur = (st & 1) ? buf1 : buf0;
+            if (st < i) {
+                stage_l32((st & 1) ? buf0 : buf1, l32_tile(P, i, st + 1));
+                asm volatile("cp.async.wait_group 1;" ::: "memory");
+            } else {
+                cp_async_wait_all();
+            }
+            __syncthreads();
+            if (st < i) {
+                const double *tj = t + (int64_t)st * QB;
+#pragma unroll 8
+                for (int col = 64 * h; col < 64 * h + 64; ++col) s = fmaf(cur[col * SLD + r], (float)tj[col], s);
+            } else {
+                red[h * QB + r] = s;
+                __syncthreads();
+                if (tid < QB) tv[tid] = (float)__ldcg(b + (int64_t)i * QB + tid) - (red[tid] + red[QB + tid]);
+                __syncthreads();
+                float u = 0.0f;
+                for (int col = 64 * h; col < 64 * h + 64 && col <= r; ++col) u = fmaf(cur[col * SLD + r], tv[col], u);
+                red[h * QB + r] = u;
+                __syncthreads();
+                if (tid < QB) t[(int64_t)i * QB + tid] = red[tid] + red[QB + tid];
+            }
+            __syncthreads();
         }
-        red[h * QB + r] = s;
-        __syncthreads();
-        if (tid < QB) tv[tid] = (float)__ldcg(b + (int64_t)i * QB + tid) - (red[tid] + red[QB + tid]);
-        __syncthreads();
-        const float *W = l32_tile(P, i, i);
-        float u = 0.0f;
-        for (int col = 64 * h; col < 64 * h + 64 && col <= r; ++col) u = fmaf(__ldcg(W + r + QB * col), tv[col], u);
-        red[h * QB + r] = u;
-        __syncthreads();
-        if (tid < QB) t[(int64_t)i * QB + tid] = red[tid] + red[QB + tid];
-        __syncthreads();
     }
-    // backward: b_i = W_i^T (t_i - sum_{j>i} L_ji^T b_j)
+    // backward: b_i = W_i^T (t_i - sum_{j>i} L_ji^T b_j); steps j = T-1..i+1, then W_i
     for (int i = T - 1; i >= 0; --i) {
         float s = 0.0f;
-        for (int j = i + 1; j < T; ++j) {
-            const float *L = l32_tile(P, j, i) + QB * r;
-            const double *bj = b + (int64_t)j * QB;
-            for (int col = 64 * h; col < 64 * h + 64; ++col) s = fmaf(__ldcg(L + col), (float)bj[col], s);
+        const int nst = T - 1 - i;  // off-diagonal steps
+        __syncthreads();
+        stage_l32(buf0, l32_tile(P, nst > 0 ? T - 1 : i, i));
+        for (int st = 0; st <= nst; ++st) {
+            float *cur = (st & 1) ? buf1 : buf0;
+            if (st < nst) {
+                const int jn = T - 2 - st;  // next tile row: T-2, ..., i+1, then i (W_i)
+                stage_l32((st & 1) ? buf0 : buf1, l32_tile(P, jn > i ? jn : i, i));
+                asm volatile("cp.async.wait_group 1;" ::: "memory");
+            } else {
+                cp_async_wait_all();
+            }
+            __syncthreads();
+            if (st < nst) {
+                const int j = T - 1 - st;
+                const double *bj = b + (int64_t)j * QB;
+                // (L_ji^T b_j)[r] = sum_c L_ji(c, r) b_j(c): row r of the staged tile's transpose
+                const float4 *col_r = reinterpret_cast<const float4 *>(cur + r * SLD + 64 * h);
+#pragma unroll 4
+                for (int q = 0; q < 16; ++q) {
+                    const float4 v = col_r[q];
+                    const int c0 = 64 * h + 4 * q;
+                    s = fmaf(v.x, (float)bj[c0], s);
+                    s = fmaf(v.y, (float)bj[c0 + 1], s);
+                    s = fmaf(v.z, (float)bj[c0 + 2], s);
+                    s = fmaf(v.w, (float)bj[c0 + 3], s);
+                }
+            } else {
+                red[h * QB + r] = s;
+                __syncthreads();
+                if (tid < QB) tv[tid] = (float)t[(int64_t)i * QB + tid] - (red[tid] + red[QB + tid]);
+                __syncthreads();
+                // b_i(r) = sum_{c >= r} W_i(c, r) tv(c)
+                float u = 0.0f;
+                for (int col = max(64 * h, r); col < 64 * h + 64; ++col) u = fmaf(cur[r * SLD + col], tv[col], u);
+                red[h * QB + r] = u;
+                __syncthreads();
+                if (tid < QB) b[(int64_t)i * QB + tid] = red[tid] + red[QB + tid];
+            }
+            __syncthreads();
         }
-        red[h * QB + r] = s;
-        __syncthreads();
-        if (tid < QB) tv[tid] = (float)t[(int64_t)i * QB + tid] - (red[tid] + red[QB + tid]);
-        __syncthreads();
-        const float *W = l32_tile(P, i, i) + QB * r;
-        float u = 0.0f;
-        for (int col = max(64 * h, r); col < 64 * h + 64; ++col) u = fmaf(__ldcg(W + col), tv[col], u);
-        red[h * QB + r] = u;
-        __syncthreads();
-        if (tid < QB) b[(int64_t)i * QB + tid] = red[tid] + red[QB + tid];
-        __syncthreads();
     }
 }
 
@@ -646,7 +700,7 @@ __device__ bool tc_solve(TcCtx &c, const DagProb &P) {
             rr = fma(v, v, rr);
         }
         const double rn = tc_block_sum(c, rr);
-        if (tid == 0) P.part[T + 3 * dag_ntiles(T) + DAG_EVALS * T + 1] = rn;  // ||r||^2
+        if (tid == 0) P.part[T + 3 * dag_ntiles(T) + 1] = rn;  // ||r||^2
         __syncthreads();
         lowp_solve(c, P, al, tt);
     }
@@ -654,78 +708,120 @@ __device__ bool tc_solve(TcCtx &c, const DagProb &P) {
     return true;
 }
 
-// s_i = r_i - sum_j C_ij alpha_j (double-float entries), ||s_i||^2
-__device__ bool tc_res(TcCtx &c, const DagProb &P, int e, int i) {
+// Residual partials of one lower tile (i, j) for evaluation e: with the
+// tile's entries C_ij in double-float (evaluated once),
+//   rp[t][0][r] = sum_c C_ij(r, c) alpha_j(c),   rp[t][1][c] = sum_r C_ij(r, c) alpha_i(r)
+// (the second for i > j only: C is symmetric).  Rows and columns beyond n
+// contribute nothing.
+__device__ bool tc_res(TcCtx &c, const DagProb &P, int e, int i, int j) {
     const int T = P.T, tid = threadIdx.x;
     const int64_t m = (int64_t)T * QB;
-    const double *r = P.vec, *al = P.vec + m;
-    double *s = P.vec + 2 * m;
+    const double *al = P.vec + m;
     int *wait_f = e == 0 ? f_solved(P) : f_corr(P, e - 1);
     if (!dag_wait(wait_f, 1, c.h, P.info, c.ok)) return false;
     if (!failed(P.info) && !*reinterpret_cast<volatile int *>(f_conv(P))) {
-        const int row = tid & (QB - 1), h = tid >> 7;
-        const int64_t gi = (int64_t)i * QB + row;
+        float2 *stg = reinterpret_cast<float2 *>(c.opA);
+        float2 *avr = reinterpret_cast<float2 *>(c.opA + 2 * QOPER - 4096);  // alpha of the rows
+        float2 *pr = reinterpret_cast<float2 *>(c.red);                      // [2][128]
+        __syncthreads();
+        if (tid < QB) {
+            const int64_t gc = (int64_t)j * QB + tid, gr = (int64_t)i * QB + tid;
+            c.xs[tid] = df_point(gc < P.n ? P.x[gc] : make_double2(0.0, 0.0));
+            const dfl ac = d2df(gc < P.n ? __ldcg(al + gc) : 0.0);
+            c.av[tid] = make_float2(ac.h, ac.l);
+            const dfl ar = d2df(gr < P.n ? __ldcg(al + gr) : 0.0);
+            avr[tid] = make_float2(ar.h, ar.l);
+        }
+        __syncthreads();
+        const int r = tid & (QB - 1), h = tid >> 7;
+        const int64_t gi = (int64_t)i * QB + r;
         const bool row_ok = gi < P.n;
         const float4 xi = df_point(row_ok ? P.x[gi] : make_double2(0.0, 0.0));
-        dfl acc{0.0f, 0.0f};
-        for (int j = 0; j < T; ++j) {
-            __syncthreads();
-            if (tid < QB) {
-                const int64_t g = (int64_t)j * QB + tid;
-                c.xs[tid] = df_point(g < P.n ? P.x[g] : make_double2(0.0, 0.0));
-                const dfl a = d2df(g < P.n ? __ldcg(al + g) : 0.0);
-                c.av[tid] = make_float2(a.h, a.l);
-            }
-            __syncthreads();
-            if (!row_ok) continue;
-            for (int col = 64 * h; col < 64 * h + 64; ++col) {
-                const int64_t gc = (int64_t)j * QB + col;
-                if (gc >= P.n) break;
-                dfl v;
-                if (gc == gi) v = P.ddiag;
-                else {
-                    dfl unused;
-                    df_cov_s<false>(P.kind, P.dscale, P.ds2, df_dist(xi, c.xs[col]), c.tab, v, unused);
+        // rows: two independent chains (even / odd columns)
+        dfl a0{0.0f, 0.0f}, a1{0.0f, 0.0f};
+        for (int col = 64 * h; col < 64 * h + 64; col += 2) {
+            dfl v[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int64_t gc = (int64_t)j * QB + col + u;
+                v[u] = dfl{0.0f, 0.0f};
+                if (row_ok && gc < P.n) {
+                    if (gc == gi) v[u] = P.ddiag;
+                    else {
+                        dfl unused;
+                        df_cov_s<false>(P.kind, P.dscale, P.ds2, df_dist(xi, c.xs[col + u]), c.tab,
+                                        v[u], unused);
+                    }
                 }
-                acc = df_add(acc, df_mul(v, dfl{c.av[col].x, c.av[col].y}));
+                stg[r * QSTG_LD + col + u] = make_float2(v[u].h, v[u].l);
             }
+            a0 = df_add(a0, df_mul(v[0], dfl{c.av[col].x, c.av[col].y}));
+            a1 = df_add(a1, df_mul(v[1], dfl{c.av[col + 1].x, c.av[col + 1].y}));
         }
-        float2 *pr = reinterpret_cast<float2 *>(c.red);  // [2][128]
+        const dfl a = df_add(a0, a1);
+        pr[h * QB + r] = make_float2(a.h, a.l);
         __syncthreads();
-        pr[h * QB + row] = make_float2(acc.h, acc.l);
-        __syncthreads();
-        double sq = 0.0;
+        double *rp = P.rp + (size_t)tile_index(T, i, j) * (2 * QB);
         if (tid < QB) {
             const dfl t = df_add(dfl{pr[tid].x, pr[tid].y}, dfl{pr[QB + tid].x, pr[QB + tid].y});
-            const int64_t g = (int64_t)i * QB + tid;
-            const double sv = g < P.n ? __ldcg(r + g) - df_to_double(t) : 0.0;
-            s[g] = sv;
-            sq = sv * sv;
+            rp[tid] = df_to_double(t);
         }
-        const double tot = tc_block_sum(c, sq);
-        if (tid == 0) P.part[T + 3 * dag_ntiles(T) + e * T + i] = tot;
+        if (i != j) {
+            // columns: thread (column r, rows 64h..)
+            __syncthreads();
+            dfl b0{0.0f, 0.0f}, b1{0.0f, 0.0f};
+            for (int row = 64 * h; row < 64 * h + 64; row += 2) {
+                const float2 v0 = stg[row * QSTG_LD + r], v1 = stg[(row + 1) * QSTG_LD + r];
+                b0 = df_add(b0, df_mul(dfl{v0.x, v0.y}, dfl{avr[row].x, avr[row].y}));
+                b1 = df_add(b1, df_mul(dfl{v1.x, v1.y}, dfl{avr[row + 1].x, avr[row + 1].y}));
+            }
+            const dfl b = df_add(b0, b1);
+            __syncthreads();
+            pr[h * QB + r] = make_float2(b.h, b.l);
+            __syncthreads();
+            if (tid < QB) {
+                const dfl t = df_add(dfl{pr[tid].x, pr[tid].y}, dfl{pr[QB + tid].x, pr[QB + tid].y});
+                rp[QB + tid] = df_to_double(t);
+            }
+        }
     }
     dag_signal(f_res(P, e));
     return true;
 }
 
-__device__ double res_ratio(const DagProb &P, int e) {
-    const int T = P.T;
-    const double *pr = P.part + T + 3 * dag_ntiles(T);
-    double s = 0.0;
-    for (int i = 0; i < T; ++i) s += __ldcg(pr + e * T + i);
-    const double rn = __ldcg(pr + DAG_EVALS * T + 1);
-    return rn > 0.0 ? sqrt(s / rn) : 0.0;
+// s = r - C alpha from the tile partials (fixed order: deterministic),
+// ||s|| / ||r|| returned to every thread.
+__device__ double tc_combine(TcCtx &c, const DagProb &P) {
+    const int T = P.T, tid = threadIdx.x;
+    const int64_t m = (int64_t)T * QB;
+    const double *r = P.vec;
+    double *s = P.vec + 2 * m;
+    double sq = 0.0;
+    for (int64_t g = tid; g < m; g += QTHREADS) {
+        const int I = (int)(g / QB), rr = (int)(g % QB);
+        double acc = 0.0;
+        if (g < P.n) {
+            for (int jj = 0; jj <= I; ++jj) acc += __ldcg(P.rp + (size_t)tile_index(T, I, jj) * (2 * QB) + rr);
+            for (int ii = I + 1; ii < T; ++ii)
+                acc += __ldcg(P.rp + (size_t)tile_index(T, ii, I) * (2 * QB) + QB + rr);
+        }
+        const double sv = g < P.n ? __ldcg(r + g) - acc : 0.0;
+        s[g] = sv;
+        sq = fma(sv, sv, sq);
+    }
+    const double tot = tc_block_sum(c, sq);
+    const double rn = __ldcg(P.part + T + 3 * dag_ntiles(T) + 1);
+    return rn > 0.0 ? sqrt(tot / rn) : 0.0;
 }
 
 __device__ bool tc_corr(TcCtx &c, const DagProb &P, int e) {
     const int T = P.T, tid = threadIdx.x;
     const int64_t m = (int64_t)T * QB;
-    if (!dag_wait(f_res(P, e), T, c.h, P.info, c.ok)) return false;
+    if (!dag_wait(f_res(P, e), dag_ntiles(T), c.h, P.info, c.ok)) return false;
     int *conv = f_conv(P);
     if (!failed(P.info) && !*reinterpret_cast<volatile int *>(conv)) {
-        const double ratio = res_ratio(P, e);
-        double *stat = P.part + T + 3 * dag_ntiles(T) + DAG_EVALS * T;
+        const double ratio = tc_combine(c, P);
+        double *stat = P.part + T + 3 * dag_ntiles(T);
         if (ratio <= QREFINE_TOL) {
             if (tid == 0) {
                 *stat = ratio;
@@ -733,6 +829,7 @@ __device__ bool tc_corr(TcCtx &c, const DagProb &P, int e) {
             }
         } else {
             double *al = P.vec + m, *s = P.vec + 2 * m, *tt = P.vec + 3 * m;
+            __syncthreads();
             lowp_solve(c, P, s, tt);
             for (int64_t q = tid; q < m; q += QTHREADS) al[q] += s[q];
         }
@@ -744,11 +841,11 @@ __device__ bool tc_corr(TcCtx &c, const DagProb &P, int e) {
 __device__ bool tc_finll(TcCtx &c, const DagProb &P) {
     const int T = P.T, tid = threadIdx.x;
     const int64_t m = (int64_t)T * QB;
-    if (!dag_wait(f_res(P, DAG_EVALS - 1), T, c.h, P.info, c.ok)) return false;
+    if (!dag_wait(f_res(P, DAG_EVALS - 1), dag_ntiles(T), c.h, P.info, c.ok)) return false;
     if (!failed(P.info)) {
-        double *stat = P.part + T + 3 * dag_ntiles(T) + DAG_EVALS * T;
+        double *stat = P.part + T + 3 * dag_ntiles(T);
         const bool conv = *reinterpret_cast<volatile int *>(f_conv(P)) != 0;
-        const double ratio = conv ? __ldcg(stat) : res_ratio(P, DAG_EVALS - 1);
+        const double ratio = conv ? __ldcg(stat) : tc_combine(c, P);
         const double *r = P.vec, *al = P.vec + m;
         double q = 0.0;
         for (int64_t e = tid; e < P.n; e += QTHREADS) q = fma(__ldcg(r + e), __ldcg(al + e), q);
@@ -923,17 +1020,19 @@ __global__ void __launch_bounds__(QTHREADS, 1)
         const DagProb &P = probs[e.x];
         int i = 0, k = 0;
         const int type = dag_decode(P.T, 1, e.y, i, k);
+        const long long c0 = dag_stat_begin(h, c.ok);
         bool ok = true;
         switch (type) {
             case DT_CHOL: ok = tc_chol(c, P, i, k); break;
             case DT_SOLVE: ok = tc_solve(c, P); break;
             case DT_TRTRI: ok = tc_trtri(c, P, i, k); break;
-            case DT_RES: ok = tc_res(c, P, k, i); break;
+            case DT_RES: ok = tc_res(c, P, k, i & 0xffff, i >> 16); break;
             case DT_CORR: ok = tc_corr(c, P, k); break;
             case DT_FINLL: ok = tc_finll(c, P); break;
             case DT_LG: ok = tc_lg(c, P, i, k); break;
             default: ok = tc_final(c, P); break;
         }
+        dag_stat_end(h, (type == DT_CHOL && i == k) ? 8 : type, c0, c.ok);
         if (!ok) break;
     }
     cp_async_wait_all();

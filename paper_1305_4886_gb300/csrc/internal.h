@@ -83,5 +83,7 @@ size_t dag_workspace_bytes(int nprob, const int64_t *h_n, int mixed);
 int dag_run(int nprob, const int64_t *h_n, const double *const *h_dx, const double *const *h_dy,
             const double *const *h_dmu, const KernParams *kps, int mixed, void *d_ws,
             size_t ws_bytes, double *d_out, double *d_grad, int64_t *d_info, cudaStream_t s);
+int dag_stats(const void *d_ws, unsigned long long *h_out);
+void dag_set_profile(int on);
 
 }  // namespace gp

@@ -39,6 +39,8 @@ SYMBOLS = [
     "gp_launch_count",
     "gp_prof_enable",
     "gp_prof_read",
+    "gp_batched_profile",
+    "gp_batched_task_stats",
 ]
 
 
@@ -117,6 +119,10 @@ def lib():
                                        ctypes.POINTER(ctypes.c_int64),
                                        ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double)]
+            L.gp_batched_profile.argtypes = [ci]
+            L.gp_batched_profile.restype = None
+            L.gp_batched_task_stats.argtypes = [p, ctypes.POINTER(ctypes.c_uint64)]
+            L.gp_batched_task_stats.restype = ci
             for name in ["gp_cov_fill", "gp_chol", "gp_backsolve", "gp_mult_chol", "gp_loglik",
                          "gp_loglik_grad", "gp_syrk_lower", "gp_prof_enable", "gp_prof_read"]:
                 getattr(L, name).restype = ci
@@ -255,6 +261,26 @@ def loglik_grad_batched(xs, ys, prms, precision="mixed_f16", mus=None, ws=None):
     info = torch.zeros(batch.nprob, dtype=torch.int64, device=dev)
     gp_loglik_grad_batched(batch, precision, ws, out, grad, info)
     return dict(out=out, grad=grad, info=info, ws=ws, batch=batch)
+
+
+BATCH_TASK_CLASSES = ["chol_offdiag", "solve", "inverse", "inverse_product_grad", "grad_sum",
+                      "refine_residual", "refine_correction", "loglik", "chol_diag"]
+
+
+def gp_batched_profile(on):
+    lib().gp_batched_profile(1 if on else 0)
+
+
+def gp_batched_task_stats(ws):
+    """Counters of the last batched call on ws (see gp.h): per task class
+    cycles, waiting cycles and task counts, plus tensor-core steps."""
+    buf = (ctypes.c_uint64 * 31)()
+    _check(lib().gp_batched_task_stats(_ptr(ws), buf), "gp_batched_task_stats")
+    v = list(buf)
+    out = {name: {"cycles": v[q], "wait_cycles": v[10 + q], "tasks": v[20 + q]}
+           for q, name in enumerate(BATCH_TASK_CLASSES)}
+    out["steps"] = v[30]
+    return out
 
 
 def gp_loglik_noalloc(x, y, mu, n, prm, out, alpha, info, stream=None):
