@@ -50,6 +50,8 @@ def parse():
                          "integer slices (15 products, FP64-grade); fp64: CUDA-core FP64")
     ap.add_argument("--workload", default="single", choices=["single", "batched"],
                     help="single: the n=67,275 problem (default); batched: 512 small problems")
+    ap.add_argument("--nprob", type=int, default=512,
+                    help="batched workload: number of problems (exploration only; 512 is the workload)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-error", action="store_true",
                     help="skip the untimed comparison with the FP64-grade form")
@@ -479,7 +481,7 @@ def run_batched(args, rank, world, local):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    probs = inputs.config5()
+    probs = inputs.config5(nprob=args.nprob)
     # longest-processing-time partition of the problems over ranks
     order = sorted(range(len(probs)), key=lambda i: -probs[i].n)
     loads = [0.0] * world
@@ -499,6 +501,14 @@ def run_batched(args, rank, world, local):
     torch.cuda.synchronize()
     batch, ws = r["batch"], r["ws"]
     out, grad, info = r["out"], r["grad"], r["info"]
+    tile_policy = None
+    if prec == "mixed_f16":
+        # the tile autotuner: FP64 64 x 64 tiles below a size threshold,
+        # tensor-core 128 x 128 tiles above it, chosen by timing this batch
+        choice, cand_ms = gp.gp_batched_autotune(batch, prec, ws, out, grad, info)
+        torch.cuda.synchronize()
+        tile_policy = {"fp64_tiles_up_to_n": choice,
+                       "candidates_ms": {str(k): round(v, 3) for k, v in cand_ms.items()}}
     for _ in range(max(0, args.warmup - 1)):
         gp.gp_loglik_grad_batched(batch, prec, ws, out, grad, info)
     torch.cuda.synchronize()
@@ -530,6 +540,7 @@ def run_batched(args, rank, world, local):
         dist.all_reduce(tm, op=dist.ReduceOp.MAX)
     ms = float(tm.item())
     bad = int((info != 0).sum().item())
+    rres = out[:, 3].double().cpu().numpy()
     flops = sum(float(p.n) ** 3 for p in probs)
     task_stats = None
     if prec in ("fp64", "mixed_f16"):
@@ -549,7 +560,7 @@ def run_batched(args, rank, world, local):
             task_stats["tensor_steps"] = st["steps"]
             task_stats["slice_tflops_per_step_time"] = st["steps"] * 6 * 2 * 128.0 ** 3 / (ms / args.steps / 1e3) / 1e12
     value = len(probs) * args.steps / (ms / 1e3)
-    line = {"metric": "batched GP loglik+grad evaluations/s (512 problems, n in [256, 4096])",
+    line = {"metric": f"batched GP loglik+grad evaluations/s ({len(probs)} problems, n in [256, 4096])",
             "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
@@ -558,8 +569,10 @@ def run_batched(args, rank, world, local):
             "data": "synthetic",
             "config": {"workload": "512 independent GPs, n log-uniform [256, 4096], 2-D uniform "
                                    "locations, exp / Matern 3/2 alternating, y ~ N(0, I)",
-                       "precision": prec, "seed": 48865, "graph": "one CUDA graph per step"},
+                       "precision": prec, "seed": 48865, "graph": "one CUDA graph per step",
+                       "tiles": tile_policy or "FP64 64 x 64"},
             "clocks": clk, "failed_problems": bad,
+            "refine_resid": {"max": float(np.max(rres)), "median": float(np.median(rres))},
             "loglik_grad_alg_tflops": flops * args.steps / (ms / 1e3) / 1e12}
     if task_stats:
         line["task_stats"] = task_stats

@@ -205,6 +205,26 @@ int gp_loglik_grad_batched(int nprob, const int64_t *h_n, const double *const *h
 void gp_batched_profile(int on);
 int gp_batched_task_stats(const void *d_ws, unsigned long long *h_out);
 
+/* Tile policy of the GP_MIXED_F16 batched launch (per device): problems with
+ * n <= fp64_max_n run on FP64 64 x 64 tiles (CUDA cores), the others on
+ * 128 x 128 tensor-core tiles, in the same launch.  Default 0 (every problem
+ * on tensor-core tiles).  gp_batched_autotune chooses it by measurement:
+ * it runs the caller's batch (same arguments as gp_loglik_grad_batched,
+ * precision GP_MIXED_F16) with each candidate threshold (0 and those of
+ * 256, 384, 512, 768, 1024, 1536 below the largest n), one warm-up and two
+ * timed launches each, sets the fastest as the policy and returns it in
+ * *h_choice; h_ms (nullable, up to 8 entries) receives each candidate's
+ * best time in ms, in the order above, and *h_ncand (nullable) their
+ * number.  The autotuner synchronises the stream (call it outside a graph
+ * capture); the outputs of the last run are left in d_out / d_grad.     */
+int gp_batched_set_tile_policy(int64_t fp64_max_n);
+int64_t gp_batched_tile_policy(void);
+int gp_batched_autotune(int nprob, const int64_t *h_n, const double *const *h_dx,
+                        const double *const *h_dy, const double *const *h_dmu,
+                        const gp_params *h_prm, int precision, void *d_ws, size_t ws_bytes,
+                        double *d_out, double *d_grad, int64_t *d_info, void *stream,
+                        int64_t *h_choice, double *h_ms, int *h_ncand);
+
 /* Log-likelihood without any workspace or allocation (GP_FP64 only).  The
  * paper has no counterpart: this entry point serves callers that cannot
  * allocate device memory when they need a log-likelihood -- code running

@@ -314,8 +314,9 @@ int gp_loglik_grad_batched(int nprob, const int64_t *h_n, const double *const *h
         // one persistent task-graph launch (FP64 CUDA-core tiles, or tcgen05 slice tiles)
         std::vector<KernParams> kps(nprob);
         for (int i = 0; i < nprob; ++i) kps[i] = make_kern(h_prm[i], precision != GP_FP64);
-        return dag_run(nprob, h_n, h_dx, h_dy, h_dmu, kps.data(), precision == GP_MIXED_F16, d_ws,
-                       ws_bytes, d_out, d_grad, d_info, s);
+        const int mixed = precision == GP_MIXED_F16;
+        return dag_run(nprob, h_n, h_dx, h_dy, h_dmu, kps.data(), mixed, mixed ? dag_fp64_max_n() : 0,
+                       d_ws, ws_bytes, d_out, d_grad, d_info, s);
     }
     StreamPool *pool = nullptr;
     GP_TRY(batch_pool(&pool));
@@ -370,6 +371,71 @@ int gp_loglik_grad_batched(int nprob, const int64_t *h_n, const double *const *h
 }
 
 void gp_batched_profile(int on) { dag_set_profile(on); }
+
+int gp_batched_set_tile_policy(int64_t fp64_max_n) {
+    if (fp64_max_n < 0) return GP_ERR_INVALID;
+    dag_set_fp64_max_n(fp64_max_n);
+    return GP_OK;
+}
+
+int64_t gp_batched_tile_policy(void) { return dag_fp64_max_n(); }
+
+// The tile autotuner of the mixed batched launch: time the caller's batch
+// with every candidate threshold (problems with n <= threshold on FP64
+// 64 x 64 tiles, the others on tensor-core 128 x 128 tiles), one warm-up
+// and two timed launches each, keep the fastest as this device's policy.
+int gp_batched_autotune(int nprob, const int64_t *h_n, const double *const *h_dx,
+                        const double *const *h_dy, const double *const *h_dmu,
+                        const gp_params *h_prm, int precision, void *d_ws, size_t ws_bytes,
+                        double *d_out, double *d_grad, int64_t *d_info, void *stream,
+                        int64_t *h_choice, double *h_ms, int *h_ncand) {
+    if (nprob < 1 || !h_n || !h_dx || !h_dy || !h_prm || !d_out || !d_grad || !d_info ||
+        !h_choice || precision != GP_MIXED_F16)
+        return GP_ERR_INVALID;
+    for (int i = 0; i < nprob; ++i)
+        if (h_n[i] < 1 || !h_dx[i] || !h_dy[i] || !params_ok(&h_prm[i])) return GP_ERR_INVALID;
+    if (!d_ws || ws_bytes < gp_batched_workspace_bytes(nprob, h_n, precision)) return GP_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<KernParams> kps(nprob);
+    for (int i = 0; i < nprob; ++i) kps[i] = make_kern(h_prm[i], true);
+    int64_t nmax = 0;
+    for (int i = 0; i < nprob; ++i) nmax = std::max(nmax, h_n[i]);
+    std::vector<int64_t> cand{0};
+    for (int64_t t : {256, 384, 512, 768, 1024, 1536})
+        if (t < nmax) cand.push_back(t);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return GP_ERR_CUDA;
+    int status = GP_OK;
+    double best_ms = 1e300;
+    int64_t best = 0;
+    for (size_t q = 0; q < cand.size() && status == GP_OK; ++q) {
+        double ms_min = 1e300;
+        for (int rep = 0; rep < 3 && status == GP_OK; ++rep) {
+            if (cudaEventRecord(e0, s) != cudaSuccess) status = GP_ERR_CUDA;
+            if (status == GP_OK)
+                status = dag_run(nprob, h_n, h_dx, h_dy, h_dmu, kps.data(), 1, cand[q], d_ws, ws_bytes,
+                                 d_out, d_grad, d_info, s);
+            if (status == GP_OK && (cudaEventRecord(e1, s) != cudaSuccess ||
+                                    cudaEventSynchronize(e1) != cudaSuccess))
+                status = GP_ERR_CUDA;
+            float ms = 0.0f;
+            if (status == GP_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) status = GP_ERR_CUDA;
+            if (rep > 0) ms_min = std::min(ms_min, (double)ms);  // the first run warms up
+        }
+        if (h_ms && q < 8) h_ms[q] = ms_min;
+        if (ms_min < best_ms) {
+            best_ms = ms_min;
+            best = cand[q];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (status != GP_OK) return status;
+    if (h_ncand) *h_ncand = (int)std::min<size_t>(cand.size(), 8);
+    dag_set_fp64_max_n(best);
+    *h_choice = best;
+    return GP_OK;
+}
 
 int gp_batched_task_stats(const void *d_ws, unsigned long long *h_out) {
     if (!d_ws || !h_out) return GP_ERR_INVALID;

@@ -44,248 +44,6 @@
 
 namespace gp {
 
-__device__ bool task_chol(const DagProb &P, int i, int j, DagSmem &sm, DagHdr *h) {
-    const int T = P.T;
-    int *Lf = P.flag, *Xf = P.flag + dag_ntiles(T);
-    const int tij = tile_index(T, i, j);
-    if (!failed(P.info)) {
-        double acc[4][4];
-        fill_tile(P, i, j, acc, sm);
-        for (int k = 0; k < j; ++k) {
-            if (!dag_wait(Lf + tile_index(T, i, k), 1, h, P.info, sm.ok)) return false;
-            if (i != j && !dag_wait(Lf + tile_index(T, j, k), 1, h, P.info, sm.ok)) return false;
-            tile_mma<0, 1, true>(acc, tile_ptr(P.A, T, i, k), tile_ptr(P.A, T, j, k), sm);
-        }
-        __syncthreads();
-        acc_to_sA(acc, sm.sA);
-        __syncthreads();
-        if (i == j) {
-            potrf_inv_tile(P, j, tile_ptr(P.A, T, j, j), tile_ptr(P.X, T, j, j), P.part + j, sm);
-        } else {
-            // L_ij = A'_ij W_j^T, W_j = X_jj
-            if (!dag_wait(Lf + tile_index(T, j, j), 1, h, P.info, sm.ok)) return false;
-            stage_b<1>(tile_ptr(P.X, T, j, j), sm.sB);
-            __syncthreads();
-            double l[4][4];
-            acc_zero(l);
-            mma_smem<false>(l, sm.sA, sm.sB);
-            acc_store(l, tile_ptr(P.A, T, i, j));
-        }
-    }
-    dag_signal(Lf + tij);
-    if (i == j) dag_signal(Xf + tij);
-    return true;
-}
-
-// Block sum of one value per thread (deterministic order); result in thread 0.
-__device__ double block_sum(double v, DagSmem &sm) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) sm.wred[0][threadIdx.x >> 5] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < DAG_THREADS / 32; ++w) s += sm.wred[0][w];
-    return s;
-}
-
-__device__ bool task_solve(const DagProb &P, DagSmem &sm, DagHdr *h) {
-    const int T = P.T, tid = threadIdx.x;
-    const int64_t m = (int64_t)T * DB;
-    int *Lf = P.flag;
-    int *solved = P.flag + dag_solved_flag(T);
-    double *r = P.vec, *v = P.vec + m, *al = P.vec + 2 * m;
-    if (!failed(P.info)) {
-        for (int64_t e = tid; e < m; e += DAG_THREADS)
-            r[e] = e < P.n ? P.y[e] - (P.mu ? P.mu[e] : 0.0) : 0.0;
-        const int row = tid & (DB - 1), q = tid >> 6;
-        // forward: v_i = W_i (r_i - sum_{j<i} L_ij v_j)
-        for (int i = 0; i < T; ++i) {
-            double s = 0.0;
-            for (int j = 0; j < i; ++j) {
-                if (!dag_wait(Lf + tile_index(T, i, j), 1, h, P.info, sm.ok)) return false;
-                const double *L = tile_ptr(P.A, T, i, j);
-                for (int c = q; c < DB; c += 4) s = fma(__ldcg(L + row + DB * c), v[(int64_t)j * DB + c], s);
-            }
-            if (!dag_wait(Lf + tile_index(T, i, i), 1, h, P.info, sm.ok)) return false;
-            sm.red[q][row] = s;
-            __syncthreads();
-            if (tid < DB) sm.vr[tid] = r[(int64_t)i * DB + tid] - (sm.red[0][tid] + sm.red[1][tid] + sm.red[2][tid] + sm.red[3][tid]);
-            __syncthreads();
-            const double *W = tile_ptr(P.X, T, i, i);
-            double t = 0.0;
-            for (int c = q; c <= row; c += 4) t = fma(__ldcg(W + row + DB * c), sm.vr[c], t);
-            sm.red[q][row] = t;
-            __syncthreads();
-            if (tid < DB) v[(int64_t)i * DB + tid] = sm.red[0][tid] + sm.red[1][tid] + sm.red[2][tid] + sm.red[3][tid];
-            __syncthreads();
-        }
-        // logdet and q = v^T v
-        double qs = 0.0;
-        for (int64_t e = tid; e < P.n; e += DAG_THREADS) qs = fma(v[e], v[e], qs);
-        const double quad = block_sum(qs, sm);
-        // backward: alpha_i = W_i^T (v_i - sum_{j>i} L_ji^T alpha_j)
-        for (int i = T - 1; i >= 0; --i) {
-            double s = 0.0;
-            for (int j = i + 1; j < T; ++j) {
-                const double *L = tile_ptr(P.A, T, j, i);
-                for (int c = q; c < DB; c += 4) s = fma(__ldcg(L + c + DB * row), al[(int64_t)j * DB + c], s);
-            }
-            sm.red[q][row] = s;
-            __syncthreads();
-            if (tid < DB) sm.vr[tid] = v[(int64_t)i * DB + tid] - (sm.red[0][tid] + sm.red[1][tid] + sm.red[2][tid] + sm.red[3][tid]);
-            __syncthreads();
-            const double *W = tile_ptr(P.X, T, i, i);
-            double t = 0.0;
-            for (int c = row + q; c < DB; c += 4) t = fma(__ldcg(W + c + DB * row), sm.vr[c], t);
-            sm.red[q][row] = t;
-            __syncthreads();
-            if (tid < DB) al[(int64_t)i * DB + tid] = sm.red[0][tid] + sm.red[1][tid] + sm.red[2][tid] + sm.red[3][tid];
-            __syncthreads();
-        }
-        if (tid == 0) {
-            double ld = 0.0;
-            for (int i = 0; i < T; ++i) ld += __ldcg(P.part + i);
-            const double logdet = 2.0 * ld;
-            const double LOG_2PI = 1.8378770664093454836;
-            const bool bad = failed(P.info);
-            P.out[0] = bad ? nan("") : -0.5 * logdet - 0.5 * quad - 0.5 * (double)P.n * LOG_2PI;
-            P.out[1] = bad ? nan("") : logdet;
-            P.out[2] = bad ? nan("") : quad;
-            P.out[3] = bad ? nan("") : 0.0;
-        }
-    } else if (tid == 0) {
-        P.out[0] = P.out[1] = P.out[2] = P.out[3] = nan("");
-    }
-    dag_signal(solved);
-    return true;
-}
-
-__device__ bool task_trtri(const DagProb &P, int i, int k, DagSmem &sm, DagHdr *h) {
-    const int T = P.T;
-    int *Lf = P.flag, *Xf = P.flag + dag_ntiles(T);
-    if (!failed(P.info)) {
-        double acc[4][4];
-        acc_zero(acc);
-        for (int m = i; m > k; --m) {
-            if (!dag_wait(Xf + tile_index(T, i, m), 1, h, P.info, sm.ok)) return false;
-            if (!dag_wait(Lf + tile_index(T, m, k), 1, h, P.info, sm.ok)) return false;
-            tile_mma<0, 0, false>(acc, tile_ptr(P.X, T, i, m), tile_ptr(P.A, T, m, k), sm);
-        }
-        if (!dag_wait(Xf + tile_index(T, k, k), 1, h, P.info, sm.ok)) return false;
-        __syncthreads();
-        acc_to_sA(acc, sm.sA);
-        stage_b<0>(tile_ptr(P.X, T, k, k), sm.sB);
-        __syncthreads();
-        double x[4][4];
-        acc_zero(x);
-        mma_smem<true>(x, sm.sA, sm.sB);
-        acc_store(x, tile_ptr(P.X, T, i, k));
-    }
-    dag_signal(Xf + tile_index(T, i, k));
-    return true;
-}
-
-__device__ bool task_lg(const DagProb &P, int i, int j, DagSmem &sm, DagHdr *h) {
-    const int T = P.T, tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    int *Xf = P.flag + dag_ntiles(T);
-    int *solved = P.flag + dag_solved_flag(T);
-    int *lgc = P.flag + dag_lg_flag(T, 0);
-    const int64_t m = (int64_t)T * DB;
-    double g0 = 0.0, g1 = 0.0, g2 = 0.0;
-    if (!failed(P.info)) {
-        double w[4][4];
-        acc_zero(w);
-        for (int mm = i; mm < T; ++mm) {
-            if (!dag_wait(Xf + tile_index(T, mm, i), 1, h, P.info, sm.ok)) return false;
-            if (!dag_wait(Xf + tile_index(T, mm, j), 1, h, P.info, sm.ok)) return false;
-            tile_mma<1, 0, false>(w, tile_ptr(P.X, T, mm, i), tile_ptr(P.X, T, mm, j), sm);
-        }
-        if (!dag_wait(solved, 1, h, P.info, sm.ok)) return false;
-        const double *al = P.vec + 2 * m;
-        if (tid < DB) {
-            const int64_t gi = (int64_t)i * DB + tid, gj = (int64_t)j * DB + tid;
-            sm.xr[tid] = gi < P.n ? P.x[gi] : make_double2(0.0, 0.0);
-            sm.xc[tid] = gj < P.n ? P.x[gj] : make_double2(0.0, 0.0);
-            sm.vr[tid] = __ldcg(al + gi);
-            sm.vc[tid] = __ldcg(al + gj);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            const int64_t gi = (int64_t)i * DB + tx + 16 * a;
-            if (gi >= P.n) continue;
-            const double ai = sm.vr[tx + 16 * a];
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                const int64_t gj = (int64_t)j * DB + ty + 16 * b;
-                if (gj >= P.n || gj > gi) continue;
-                if (gj == gi) {
-                    const double cb = 0.5 * (ai * ai - w[a][b]);
-                    g0 = fma(cb, P.s2, g0);
-                    g2 = fma(cb, P.tau2, g2);
-                } else {
-                    const double cb2 = fma(ai, sm.vc[ty + 16 * b], -w[a][b]);
-                    double cv, dr;
-                    cov_and_dlogrho_s(P.kind, P.s2, P.scale,
-                                      pair_dist(sm.xr[tx + 16 * a], sm.xc[ty + 16 * b]), cv, dr,
-                                      sm.tab);
-                    g0 = fma(cb2, cv, g0);
-                    g1 = fma(cb2, dr, g1);
-                }
-            }
-        }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        g0 += __shfl_xor_sync(0xffffffffu, g0, o);
-        g1 += __shfl_xor_sync(0xffffffffu, g1, o);
-        g2 += __shfl_xor_sync(0xffffffffu, g2, o);
-    }
-    __syncthreads();
-    if ((tid & 31) == 0) {
-        sm.wred[0][tid >> 5] = g0;
-        sm.wred[1][tid >> 5] = g1;
-        sm.wred[2][tid >> 5] = g2;
-    }
-    __syncthreads();
-    if (tid < 3) {
-        double s = 0.0;
-        for (int w8 = 0; w8 < DAG_THREADS / 32; ++w8) s += sm.wred[tid][w8];
-        P.part[T + 3 * tile_index(T, i, j) + tid] = s;
-    }
-    dag_signal(lgc);
-    return true;
-}
-
-__device__ bool task_final(const DagProb &P, DagSmem &sm, DagHdr *h) {
-    const int T = P.T, tid = threadIdx.x;
-    int *lgc = P.flag + dag_lg_flag(T, 0);
-    const int nt = dag_ntiles(T);
-    if (!dag_wait(lgc, nt, h, P.info, sm.ok)) return false;
-    // Neumaier sums per thread, then in thread order
-    double s[3] = {0.0, 0.0, 0.0}, c[3] = {0.0, 0.0, 0.0};
-    for (int t = tid; t < nt; t += DAG_THREADS)
-        for (int q = 0; q < 3; ++q) {
-            const double x = __ldcg(P.part + T + 3 * t + q), u = s[q] + x;
-            c[q] += (fabs(s[q]) >= fabs(x)) ? (s[q] - u) + x : (x - u) + s[q];
-            s[q] = u;
-        }
-    __syncthreads();
-    // 256 partials -> shared memory (sB as scratch)
-    for (int q = 0; q < 3; ++q) sm.sB[q * DAG_THREADS + tid] = s[q] + c[q];
-    __syncthreads();
-    if (tid < 3) {
-        double S = 0.0, C = 0.0;
-        for (int t = 0; t < DAG_THREADS; ++t) {
-            const double x = sm.sB[tid * DAG_THREADS + t], u = S + x;
-            C += (fabs(S) >= fabs(x)) ? (S - u) + x : (x - u) + S;
-            S = u;
-        }
-        P.grad[tid] = failed(P.info) ? nan("") : S + C;
-    }
-    return true;
-}
-
 __global__ void __launch_bounds__(DAG_THREADS, 2)
     dag_kernel(DagHdr *h, const DagProb *probs, const int2 *list, int ntot, const double *tab) {
     extern __shared__ __align__(16) unsigned char dag_smem_raw[];
@@ -422,36 +180,69 @@ static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 static size_t al1k(size_t x) { return (x + 1023) & ~size_t(1023); }
 
 struct DagLayout {
-    int P = 0, R = DAG_ROUNDS, maxN = 0, mixed = 0, tb = DB;
+    int P = 0, R = DAG_ROUNDS, maxN = 0, mixed = 0;
     int64_t ntot = 0;
     size_t flags = 0, flags_bytes = 0, probs = 0, tab = 0, dftab = 0, list = 0, poff = 0, rtot = 0,
            roff = 0, scratch = 0;
-    std::vector<int> T, ntasks, order;
+    std::vector<int> T, ntasks, order, tc;  // tc: the problem runs on tensor-core tiles
     std::vector<size_t> A, X, vec, part, flag, LSr, LSc, XSr, XSc, L32, rp;
     size_t total = 0;
 };
 
-static DagLayout dag_layout(int P, const int64_t *h_n, int mixed, int scratch_ctas) {
+// Bytes of one problem's own storage: FP64 tiles (64 x 64) or tensor-core
+// tiles (128 x 128, slice stores of L and L^{-1} in both orientations, FP32
+// tiles, residual partials).
+static size_t prob_bytes(int64_t n, bool tc) {
+    const int tb = tc ? QB : DB;
+    const size_t T = (size_t)ceil_div(n, tb), nt = T * (T + 1) / 2, m = T * tb;
+    size_t b = 0;
+    if (!tc) {
+        b += 2 * al256(sizeof(double) * nt * DB * DB);
+    } else {
+        b += 4 * al1k(nt * QSTRIDE) + al1k(sizeof(float) * nt * QB * QB) +
+             al256(sizeof(double) * nt * 2 * QB);
+    }
+    b += al256(sizeof(double) * (tc ? 4 : 3) * m) + al256(sizeof(double) * (T + 3 * nt + (tc ? 4 : 0)));
+    return b + 1024;  // alignment slack
+}
+
+// mixed: problems with n > fp64_max_n run on tensor-core tiles, the others
+// on FP64 tiles in the same launch.  reserve: size every problem for the
+// larger of its two layouts (so that any threshold fits the workspace).
+static DagLayout dag_layout(int P, const int64_t *h_n, int mixed, int scratch_ctas,
+                            int64_t fp64_max_n, bool reserve = false) {
     DagLayout L;
     L.P = P;
     L.mixed = mixed;
-    L.tb = mixed ? QB : DB;
     L.T.resize(P);
     L.ntasks.resize(P);
     L.order.resize(P);
+    L.tc.resize(P);
     for (int i = 0; i < P; ++i) L.order[i] = i;
     // largest problems first within every round
     std::stable_sort(L.order.begin(), L.order.end(), [&](int a, int b) { return h_n[a] > h_n[b]; });
     size_t nflag = 0;
     L.flag.resize(P);
     for (int s = 0; s < P; ++s) {
-        const int T = (int)ceil_div(h_n[L.order[s]], L.tb);
+        const int64_t n = h_n[L.order[s]];
+        const int tc = (mixed && n > fp64_max_n) ? 1 : 0;
+        const int T = (int)ceil_div(n, tc ? QB : DB);
+        L.tc[s] = tc;
         L.T[s] = T;
-        L.ntasks[s] = dag_ntasks(T, mixed);
+        L.ntasks[s] = dag_ntasks(T, tc);
         L.ntot += L.ntasks[s];
         L.maxN = std::max(L.maxN, L.ntasks[s]);
         L.flag[s] = nflag;
-        nflag += (size_t)dag_nflags(T, mixed);
+        nflag += (size_t)std::max(dag_nflags(T, tc),
+                                  reserve ? dag_nflags((int)ceil_div(n, DB), 0) : 0);
+    }
+    if (reserve) {  // task list sized for the larger task count of either layout
+        L.ntot = 0;
+        for (int s = 0; s < P; ++s) {
+            const int64_t n = h_n[L.order[s]];
+            L.ntot += std::max(dag_ntasks((int)ceil_div(n, DB), 0),
+                               mixed ? dag_ntasks((int)ceil_div(n, QB), 1) : 0);
+        }
     }
     size_t off = 0;
     L.flags = off;
@@ -476,9 +267,12 @@ static DagLayout dag_layout(int P, const int64_t *h_n, int mixed, int scratch_ct
     for (auto *v : {&L.A, &L.X, &L.vec, &L.part, &L.LSr, &L.LSc, &L.XSr, &L.XSc, &L.L32, &L.rp})
         v->assign(P, 0);
     for (int s = 0; s < P; ++s) {
+        const int64_t n = h_n[L.order[s]];
+        const size_t start = off;
         const size_t nt = dag_ntiles(L.T[s]);
-        const size_t m = (size_t)L.T[s] * L.tb;
-        if (!mixed) {
+        const size_t m = (size_t)L.T[s] * (L.tc[s] ? QB : DB);
+        off = al1k(off);
+        if (!L.tc[s]) {
             L.A[s] = off;
             off = al256(off + sizeof(double) * nt * DB * DB);
             L.X[s] = off;
@@ -494,9 +288,13 @@ static DagLayout dag_layout(int P, const int64_t *h_n, int mixed, int scratch_ct
             off = al256(off + sizeof(double) * nt * 2 * QB);
         }
         L.vec[s] = off;
-        off = al256(off + sizeof(double) * (mixed ? 4 : 3) * m);
+        off = al256(off + sizeof(double) * (L.tc[s] ? 4 : 3) * m);
         L.part[s] = off;
-        off = al256(off + sizeof(double) * (L.T[s] + 3 * nt + (mixed ? 4 : 0)));
+        off = al256(off + sizeof(double) * (L.T[s] + 3 * nt + (L.tc[s] ? 4 : 0)));
+        if (reserve) {
+            const size_t want = start + std::max(prob_bytes(n, false), mixed ? prob_bytes(n, true) : 0);
+            off = std::max(off, want);
+        }
     }
     L.total = off;
     return L;
@@ -529,19 +327,33 @@ static bool dag_profiling() {
     return v == 1;
 }
 
+// Largest problem on FP64 tiles in the mixed launch, per device (the tile
+// policy; gp_batched_autotune measures it, gp_batched_set_tile_policy sets it).
+static std::atomic<int64_t> g_fp64_max_n[64];
+void dag_set_fp64_max_n(int64_t v) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64) g_fp64_max_n[dev].store(v);
+}
+int64_t dag_fp64_max_n() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    return g_fp64_max_n[dev].load();
+}
+
 size_t dag_workspace_bytes(int nprob, const int64_t *h_n, int mixed) {
-    return dag_layout(nprob, h_n, mixed, mixed ? std::max(dag_tc_ctas(), 1) : 0).total;
+    return dag_layout(nprob, h_n, mixed, mixed ? std::max(dag_tc_ctas(), 1) : 0, 0, true).total;
 }
 
 int dag_run(int nprob, const int64_t *h_n, const double *const *h_dx, const double *const *h_dy,
-            const double *const *h_dmu, const KernParams *kps, int mixed, void *d_ws,
-            size_t ws_bytes, double *d_out, double *d_grad, int64_t *d_info, cudaStream_t s) {
+            const double *const *h_dmu, const KernParams *kps, int mixed, int64_t fp64_max_n,
+            void *d_ws, size_t ws_bytes, double *d_out, double *d_grad, int64_t *d_info,
+            cudaStream_t s) {
     if (nprob > 65535) return GP_ERR_INVALID;
     for (int i = 0; i < nprob; ++i)  // tile indices of a problem stay below 2^15 per side
         if (ceil_div(h_n[i], mixed ? QB : DB) > 8192) return GP_ERR_INVALID;
     const int tc_ctas = mixed ? dag_tc_ctas() : 0;
     if (mixed && tc_ctas < 1) return GP_ERR_CUDA;
-    const DagLayout L = dag_layout(nprob, h_n, mixed, tc_ctas);
+    const DagLayout L = dag_layout(nprob, h_n, mixed, tc_ctas, fp64_max_n);
     if (L.total > ws_bytes) return GP_ERR_WORKSPACE;
     if (L.ntot >= (1ll << 31)) return GP_ERR_INVALID;
     char *base = static_cast<char *>(d_ws);
@@ -576,7 +388,7 @@ int dag_run(int nprob, const int64_t *h_n, const double *const *h_dx, const doub
             d.x = reinterpret_cast<const double2 *>(h_dx[o]);
             d.y = h_dy[o];
             d.mu = h_dmu ? h_dmu[o] : nullptr;
-            if (!mixed) {
+            if (!L.tc[sidx]) {
                 d.A = reinterpret_cast<double *>(base + L.A[sidx]);
                 d.X = reinterpret_cast<double *>(base + L.X[sidx]);
             } else {
@@ -597,7 +409,7 @@ int dag_run(int nprob, const int64_t *h_n, const double *const *h_dx, const doub
             d.T = L.T[sidx];
             d.ntasks = L.ntasks[sidx];
             d.kind = kps[o].kind;
-            d.mixed = mixed;
+            d.mixed = L.tc[sidx];
             d.s2 = kps[o].s2;
             d.scale = kps[o].scale;
             d.diag = kps[o].diag;
@@ -632,7 +444,7 @@ int dag_run(int nprob, const int64_t *h_n, const double *const *h_dx, const doub
         GP_LAUNCH_CHECK();
     } else {
         const int grid = (int)std::min<int64_t>(tc_ctas, L.ntot);
-        GP_TRY(dag_tc_launch(grid, hdr, probs, list, (int)L.ntot, dftab,
+        GP_TRY(dag_tc_launch(grid, hdr, probs, list, (int)L.ntot, tab, dftab,
                              reinterpret_cast<double *>(base + L.scratch), s));
     }
     dag_finish_kernel<<<(unsigned)ceil_div(nprob, 128), 128, 0, s>>>(hdr, probs, nprob);

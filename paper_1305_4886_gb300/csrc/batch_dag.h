@@ -181,7 +181,7 @@ constexpr int QSCRATCH_DOUBLES = 7 * 64 * 64;  // per-CTA FP64 blocks of a diago
 
 struct DagHdr;
 int dag_tc_launch(int grid, DagHdr *hdr, const DagProb *probs, const int2 *list, int ntot,
-                  const float2 *dftab, double *scratch, cudaStream_t s);
+                  const double *tab, const float2 *dftab, double *scratch, cudaStream_t s);
 
 struct DagSmem {
     double sA[DB * DLD];
@@ -458,6 +458,253 @@ static __device__ void potrf_inv_tile(const DagProb &P, int j, double *G, double
         const int r = e & (DB - 1), c = e >> 6;
         Wg[e] = (r >= c) ? sm.sB[c * DLD + r] * sm.lj[c] : 0.0;
     }
+}
+
+// --------------------------------------------------------------------------
+// FP64 tile tasks (64 x 64 tiles, 256 threads; shared memory: DagSmem).
+// They run in the FP64 launch and, for the problems given FP64 tiles, in the
+// tensor-core launch.
+// --------------------------------------------------------------------------
+static __device__ bool task_chol(const DagProb &P, int i, int j, DagSmem &sm, DagHdr *h) {
+    const int T = P.T;
+    int *Lf = P.flag, *Xf = P.flag + dag_ntiles(T);
+    const int tij = tile_index(T, i, j);
+    if (!failed(P.info)) {
+        double acc[4][4];
+        fill_tile(P, i, j, acc, sm);
+        for (int k = 0; k < j; ++k) {
+            if (!dag_wait(Lf + tile_index(T, i, k), 1, h, P.info, sm.ok)) return false;
+            if (i != j && !dag_wait(Lf + tile_index(T, j, k), 1, h, P.info, sm.ok)) return false;
+            tile_mma<0, 1, true>(acc, tile_ptr(P.A, T, i, k), tile_ptr(P.A, T, j, k), sm);
+        }
+        __syncthreads();
+        acc_to_sA(acc, sm.sA);
+        __syncthreads();
+        if (i == j) {
+            potrf_inv_tile(P, j, tile_ptr(P.A, T, j, j), tile_ptr(P.X, T, j, j), P.part + j, sm);
+        } else {
+            // L_ij = A'_ij W_j^T, W_j = X_jj
+            if (!dag_wait(Lf + tile_index(T, j, j), 1, h, P.info, sm.ok)) return false;
+            stage_b<1>(tile_ptr(P.X, T, j, j), sm.sB);
+            __syncthreads();
+            double l[4][4];
+            acc_zero(l);
+            mma_smem<false>(l, sm.sA, sm.sB);
+            acc_store(l, tile_ptr(P.A, T, i, j));
+        }
+    }
+    dag_signal(Lf + tij);
+    if (i == j) dag_signal(Xf + tij);
+    return true;
+}
+
+// Block sum of one value per thread (deterministic order); result in thread 0.
+static __device__ double block_sum(double v, DagSmem &sm) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sm.wred[0][threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < DAG_THREADS / 32; ++w) s += sm.wred[0][w];
+    return s;
+}
+
+static __device__ bool task_solve(const DagProb &P, DagSmem &sm, DagHdr *h) {
+    const int T = P.T, tid = threadIdx.x;
+    const int64_t m = (int64_t)T * DB;
+    int *Lf = P.flag;
+    int *solved = P.flag + dag_solved_flag(T);
+    double *r = P.vec, *v = P.vec + m, *al = P.vec + 2 * m;
+    if (!failed(P.info)) {
+        for (int64_t e = tid; e < m; e += DAG_THREADS)
+            r[e] = e < P.n ? P.y[e] - (P.mu ? P.mu[e] : 0.0) : 0.0;
+        const int row = tid & (DB - 1), q = tid >> 6;
+        // forward: v_i = W_i (r_i - sum_{j<i} L_ij v_j)
+        for (int i = 0; i < T; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < i; ++j) {
+                if (!dag_wait(Lf + tile_index(T, i, j), 1, h, P.info, sm.ok)) return false;
+                const double *L = tile_ptr(P.A, T, i, j);
+                for (int c = q; c < DB; c += 4) s = fma(__ldcg(L + row + DB * c), v[(int64_t)j * DB + c], s);
+            }
+            if (!dag_wait(Lf + tile_index(T, i, i), 1, h, P.info, sm.ok)) return false;
+            sm.red[q][row] = s;
+            __syncthreads();
+            if (tid < DB) sm.vr[tid] = r[(int64_t)i * DB + tid] - (sm.red[0][tid] + sm.red[1][tid] + sm.red[2][tid] + sm.red[3][tid]);
+            __syncthreads();
+            const double *W = tile_ptr(P.X, T, i, i);
+            double t = 0.0;
+            for (int c = q; c <= row; c += 4) t = fma(__ldcg(W + row + DB * c), sm.vr[c], t);
+            sm.red[q][row] = t;
+            __syncthreads();
+            if (tid < DB) v[(int64_t)i * DB + tid] = sm.red[0][tid] + sm.red[1][tid] + sm.red[2][tid] + sm.red[3][tid];
+            __syncthreads();
+        }
+        // logdet and q = v^T v
+        double qs = 0.0;
+        for (int64_t e = tid; e < P.n; e += DAG_THREADS) qs = fma(v[e], v[e], qs);
+        const double quad = block_sum(qs, sm);
+        // backward: alpha_i = W_i^T (v_i - sum_{j>i} L_ji^T alpha_j)
+        for (int i = T - 1; i >= 0; --i) {
+            double s = 0.0;
+            for (int j = i + 1; j < T; ++j) {
+                const double *L = tile_ptr(P.A, T, j, i);
+                for (int c = q; c < DB; c += 4) s = fma(__ldcg(L + c + DB * row), al[(int64_t)j * DB + c], s);
+            }
+            sm.red[q][row] = s;
+            __syncthreads();
+            if (tid < DB) sm.vr[tid] = v[(int64_t)i * DB + tid] - (sm.red[0][tid] + sm.red[1][tid] + sm.red[2][tid] + sm.red[3][tid]);
+            __syncthreads();
+            const double *W = tile_ptr(P.X, T, i, i);
+            double t = 0.0;
+            for (int c = row + q; c < DB; c += 4) t = fma(__ldcg(W + c + DB * row), sm.vr[c], t);
+            sm.red[q][row] = t;
+            __syncthreads();
+            if (tid < DB) al[(int64_t)i * DB + tid] = sm.red[0][tid] + sm.red[1][tid] + sm.red[2][tid] + sm.red[3][tid];
+            __syncthreads();
+        }
+        if (tid == 0) {
+            double ld = 0.0;
+            for (int i = 0; i < T; ++i) ld += __ldcg(P.part + i);
+            const double logdet = 2.0 * ld;
+            const double LOG_2PI = 1.8378770664093454836;
+            const bool bad = failed(P.info);
+            P.out[0] = bad ? nan("") : -0.5 * logdet - 0.5 * quad - 0.5 * (double)P.n * LOG_2PI;
+            P.out[1] = bad ? nan("") : logdet;
+            P.out[2] = bad ? nan("") : quad;
+            P.out[3] = bad ? nan("") : 0.0;
+        }
+    } else if (tid == 0) {
+        P.out[0] = P.out[1] = P.out[2] = P.out[3] = nan("");
+    }
+    dag_signal(solved);
+    return true;
+}
+
+static __device__ bool task_trtri(const DagProb &P, int i, int k, DagSmem &sm, DagHdr *h) {
+    const int T = P.T;
+    int *Lf = P.flag, *Xf = P.flag + dag_ntiles(T);
+    if (!failed(P.info)) {
+        double acc[4][4];
+        acc_zero(acc);
+        for (int m = i; m > k; --m) {
+            if (!dag_wait(Xf + tile_index(T, i, m), 1, h, P.info, sm.ok)) return false;
+            if (!dag_wait(Lf + tile_index(T, m, k), 1, h, P.info, sm.ok)) return false;
+            tile_mma<0, 0, false>(acc, tile_ptr(P.X, T, i, m), tile_ptr(P.A, T, m, k), sm);
+        }
+        if (!dag_wait(Xf + tile_index(T, k, k), 1, h, P.info, sm.ok)) return false;
+        __syncthreads();
+        acc_to_sA(acc, sm.sA);
+        stage_b<0>(tile_ptr(P.X, T, k, k), sm.sB);
+        __syncthreads();
+        double x[4][4];
+        acc_zero(x);
+        mma_smem<true>(x, sm.sA, sm.sB);
+        acc_store(x, tile_ptr(P.X, T, i, k));
+    }
+    dag_signal(Xf + tile_index(T, i, k));
+    return true;
+}
+
+static __device__ bool task_lg(const DagProb &P, int i, int j, DagSmem &sm, DagHdr *h) {
+    const int T = P.T, tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    int *Xf = P.flag + dag_ntiles(T);
+    int *solved = P.flag + dag_solved_flag(T);
+    int *lgc = P.flag + dag_lg_flag(T, 0);
+    const int64_t m = (int64_t)T * DB;
+    double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+    if (!failed(P.info)) {
+        double w[4][4];
+        acc_zero(w);
+        for (int mm = i; mm < T; ++mm) {
+            if (!dag_wait(Xf + tile_index(T, mm, i), 1, h, P.info, sm.ok)) return false;
+            if (!dag_wait(Xf + tile_index(T, mm, j), 1, h, P.info, sm.ok)) return false;
+            tile_mma<1, 0, false>(w, tile_ptr(P.X, T, mm, i), tile_ptr(P.X, T, mm, j), sm);
+        }
+        if (!dag_wait(solved, 1, h, P.info, sm.ok)) return false;
+        const double *al = P.vec + 2 * m;
+        if (tid < DB) {
+            const int64_t gi = (int64_t)i * DB + tid, gj = (int64_t)j * DB + tid;
+            sm.xr[tid] = gi < P.n ? P.x[gi] : make_double2(0.0, 0.0);
+            sm.xc[tid] = gj < P.n ? P.x[gj] : make_double2(0.0, 0.0);
+            sm.vr[tid] = __ldcg(al + gi);
+            sm.vc[tid] = __ldcg(al + gj);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int64_t gi = (int64_t)i * DB + tx + 16 * a;
+            if (gi >= P.n) continue;
+            const double ai = sm.vr[tx + 16 * a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int64_t gj = (int64_t)j * DB + ty + 16 * b;
+                if (gj >= P.n || gj > gi) continue;
+                if (gj == gi) {
+                    const double cb = 0.5 * (ai * ai - w[a][b]);
+                    g0 = fma(cb, P.s2, g0);
+                    g2 = fma(cb, P.tau2, g2);
+                } else {
+                    const double cb2 = fma(ai, sm.vc[ty + 16 * b], -w[a][b]);
+                    double cv, dr;
+                    cov_and_dlogrho_s(P.kind, P.s2, P.scale,
+                                      pair_dist(sm.xr[tx + 16 * a], sm.xc[ty + 16 * b]), cv, dr,
+                                      sm.tab);
+                    g0 = fma(cb2, cv, g0);
+                    g1 = fma(cb2, dr, g1);
+                }
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        g0 += __shfl_xor_sync(0xffffffffu, g0, o);
+        g1 += __shfl_xor_sync(0xffffffffu, g1, o);
+        g2 += __shfl_xor_sync(0xffffffffu, g2, o);
+    }
+    __syncthreads();
+    if ((tid & 31) == 0) {
+        sm.wred[0][tid >> 5] = g0;
+        sm.wred[1][tid >> 5] = g1;
+        sm.wred[2][tid >> 5] = g2;
+    }
+    __syncthreads();
+    if (tid < 3) {
+        double s = 0.0;
+        for (int w8 = 0; w8 < DAG_THREADS / 32; ++w8) s += sm.wred[tid][w8];
+        P.part[T + 3 * tile_index(T, i, j) + tid] = s;
+    }
+    dag_signal(lgc);
+    return true;
+}
+
+static __device__ bool task_final(const DagProb &P, DagSmem &sm, DagHdr *h) {
+    const int T = P.T, tid = threadIdx.x;
+    int *lgc = P.flag + dag_lg_flag(T, 0);
+    const int nt = dag_ntiles(T);
+    if (!dag_wait(lgc, nt, h, P.info, sm.ok)) return false;
+    // Neumaier sums per thread, then in thread order
+    double s[3] = {0.0, 0.0, 0.0}, c[3] = {0.0, 0.0, 0.0};
+    for (int t = tid; t < nt; t += DAG_THREADS)
+        for (int q = 0; q < 3; ++q) {
+            const double x = __ldcg(P.part + T + 3 * t + q), u = s[q] + x;
+            c[q] += (fabs(s[q]) >= fabs(x)) ? (s[q] - u) + x : (x - u) + s[q];
+            s[q] = u;
+        }
+    __syncthreads();
+    // 256 partials -> shared memory (sB as scratch)
+    for (int q = 0; q < 3; ++q) sm.sB[q * DAG_THREADS + tid] = s[q] + c[q];
+    __syncthreads();
+    if (tid < 3) {
+        double S = 0.0, C = 0.0;
+        for (int t = 0; t < DAG_THREADS; ++t) {
+            const double x = sm.sB[tid * DAG_THREADS + t], u = S + x;
+            C += (fabs(S) >= fabs(x)) ? (S - u) + x : (x - u) + S;
+            S = u;
+        }
+        P.grad[tid] = failed(P.info) ? nan("") : S + C;
+    }
+    return true;
 }
 
 }  // namespace gp

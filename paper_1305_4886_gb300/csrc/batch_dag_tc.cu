@@ -974,7 +974,7 @@ __device__ bool tc_final(TcCtx &c, const DagProb &P) {
 }
 
 __global__ void __launch_bounds__(QTHREADS, 1)
-    dag_tc_kernel(DagHdr *h, const DagProb *probs, const int2 *list, int ntot,
+    dag_tc_kernel(DagHdr *h, const DagProb *probs, const int2 *list, int ntot, const double *tab,
                   const float2 *dftab, double *scratch) {
     extern __shared__ uint8_t q_smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(q_smem_raw) + 1023) &
@@ -1019,7 +1019,27 @@ __global__ void __launch_bounds__(QTHREADS, 1)
         const int2 e = list[t];
         const DagProb &P = probs[e.x];
         int i = 0, k = 0;
-        const int type = dag_decode(P.T, 1, e.y, i, k);
+        const int type = dag_decode(P.T, P.mixed, e.y, i, k);
+        if (!P.mixed) {
+            // a problem on FP64 tiles: the FP64 tasks, their shared memory
+            // laid over the operand buffers
+            DagSmem &dsm = *reinterpret_cast<DagSmem *>(c.opA);
+            __syncthreads();
+            if (tid < EXP_TAB) dsm.tab[tid] = tab[tid];
+            __syncthreads();
+            const long long c0 = dag_stat_begin(h, dsm.ok);
+            bool ok = true;
+            switch (type) {
+                case DT_CHOL: ok = task_chol(P, i, k, dsm, h); break;
+                case DT_SOLVE: ok = task_solve(P, dsm, h); break;
+                case DT_TRTRI: ok = task_trtri(P, i, k, dsm, h); break;
+                case DT_LG: ok = task_lg(P, i, k, dsm, h); break;
+                default: ok = task_final(P, dsm, h); break;
+            }
+            dag_stat_end(h, (type == DT_CHOL && i == k) ? 8 : type, c0, dsm.ok);
+            if (!ok) break;
+            continue;
+        }
         const long long c0 = dag_stat_begin(h, c.ok);
         bool ok = true;
         switch (type) {
@@ -1045,7 +1065,7 @@ __global__ void __launch_bounds__(QTHREADS, 1)
 }
 
 int dag_tc_launch(int grid, DagHdr *hdr, const DagProb *probs, const int2 *list, int ntot,
-                  const float2 *dftab, double *scratch, cudaStream_t s) {
+                  const double *tab, const float2 *dftab, double *scratch, cudaStream_t s) {
     static bool attr_set[64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return GP_ERR_CUDA;
@@ -1055,7 +1075,7 @@ int dag_tc_launch(int grid, DagHdr *hdr, const DagProb *probs, const int2 *list,
             return GP_ERR_CUDA;
         attr_set[dev] = true;
     }
-    dag_tc_kernel<<<grid, QTHREADS, QS_DYN, s>>>(hdr, probs, list, ntot, dftab, scratch);
+    dag_tc_kernel<<<grid, QTHREADS, QS_DYN, s>>>(hdr, probs, list, ntot, tab, dftab, scratch);
     GP_LAUNCH_CHECK();
     return GP_OK;
 }

@@ -81,8 +81,11 @@ int refine_alpha(const double *d_x, int64_t n, int64_t np, const KernParams &kp,
 // batch_dag.cu / batch_dag_tc.cu (the batched evaluation as one persistent task-graph launch)
 size_t dag_workspace_bytes(int nprob, const int64_t *h_n, int mixed);
 int dag_run(int nprob, const int64_t *h_n, const double *const *h_dx, const double *const *h_dy,
-            const double *const *h_dmu, const KernParams *kps, int mixed, void *d_ws,
-            size_t ws_bytes, double *d_out, double *d_grad, int64_t *d_info, cudaStream_t s);
+            const double *const *h_dmu, const KernParams *kps, int mixed, int64_t fp64_max_n,
+            void *d_ws, size_t ws_bytes, double *d_out, double *d_grad, int64_t *d_info,
+            cudaStream_t s);
+void dag_set_fp64_max_n(int64_t v);
+int64_t dag_fp64_max_n();
 int dag_stats(const void *d_ws, unsigned long long *h_out);
 void dag_set_profile(int on);
 

@@ -41,6 +41,9 @@ SYMBOLS = [
     "gp_prof_read",
     "gp_batched_profile",
     "gp_batched_task_stats",
+    "gp_batched_set_tile_policy",
+    "gp_batched_tile_policy",
+    "gp_batched_autotune",
 ]
 
 
@@ -123,6 +126,14 @@ def lib():
             L.gp_batched_profile.restype = None
             L.gp_batched_task_stats.argtypes = [p, ctypes.POINTER(ctypes.c_uint64)]
             L.gp_batched_task_stats.restype = ci
+            L.gp_batched_set_tile_policy.argtypes = [i64]
+            L.gp_batched_set_tile_policy.restype = ci
+            L.gp_batched_tile_policy.restype = i64
+            L.gp_batched_autotune.argtypes = [ci, p, p, p, p, p, ci, p, sz, p, p, p, p,
+                                              ctypes.POINTER(ctypes.c_int64),
+                                              ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_int)]
+            L.gp_batched_autotune.restype = ci
             for name in ["gp_cov_fill", "gp_chol", "gp_backsolve", "gp_mult_chol", "gp_loglik",
                          "gp_loglik_grad", "gp_syrk_lower", "gp_prof_enable", "gp_prof_read"]:
                 getattr(L, name).restype = ci
@@ -246,6 +257,36 @@ def gp_loglik_grad_batched(batch, precision, ws, out, grad, info, stream=None):
         ctypes.cast(batch.pmu, v) if batch.pmu is not None else None,
         ctypes.cast(batch.prm, v), _prec(precision), _ptr(ws), wsb, _f64(out), _f64(grad),
         _ptr(info), _stream(stream)), "gp_loglik_grad_batched")
+
+
+def gp_batched_set_tile_policy(fp64_max_n):
+    _check(lib().gp_batched_set_tile_policy(int(fp64_max_n)), "gp_batched_set_tile_policy")
+
+
+def gp_batched_tile_policy():
+    return int(lib().gp_batched_tile_policy())
+
+
+AUTOTUNE_CANDIDATES = [0, 256, 384, 512, 768, 1024, 1536]
+
+
+def gp_batched_autotune(batch, precision, ws, out, grad, info, stream=None):
+    """Time the batch with each candidate tile threshold and keep the fastest
+    as the device's policy (gp.h); returns (choice, {threshold: ms})."""
+    wsb = ws.numel() * ws.element_size()
+    v = ctypes.c_void_p
+    choice = ctypes.c_int64(0)
+    ms = (ctypes.c_double * 8)()
+    ncand = ctypes.c_int(0)
+    _check(lib().gp_batched_autotune(
+        batch.nprob, ctypes.cast(batch.n, v), ctypes.cast(batch.px, v), ctypes.cast(batch.py, v),
+        ctypes.cast(batch.pmu, v) if batch.pmu is not None else None,
+        ctypes.cast(batch.prm, v), _prec(precision), _ptr(ws), wsb, _f64(out), _f64(grad),
+        _ptr(info), _stream(stream), ctypes.byref(choice), ms, ctypes.byref(ncand)),
+        "gp_batched_autotune")
+    nmax = max(batch.n[i] for i in range(batch.nprob))
+    cands = [t for t in AUTOTUNE_CANDIDATES if t == 0 or t < nmax][:ncand.value]
+    return int(choice.value), {t: ms[q] for q, t in enumerate(cands)}
 
 
 def loglik_grad_batched(xs, ys, prms, precision="mixed_f16", mus=None, ws=None):

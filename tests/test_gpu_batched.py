@@ -89,3 +89,34 @@ def test_batched_full_workload_and_graph(g):
     assert np.all(i2.cpu().numpy() == 0)
     np.testing.assert_allclose(o2.cpu().numpy()[:, 0], out[:, 0], rtol=1e-12)
     np.testing.assert_allclose(g2.cpu().numpy(), grad, rtol=1e-9, atol=1e-9)
+
+
+def test_batched_mixed_tile_policy_and_autotune(g, orc):
+    """Problems at or below the tile threshold run on FP64 64 x 64 tiles inside
+    the tensor-core launch; every problem must still match the oracle, and the
+    autotuner must pick one of its candidates and leave it as the policy."""
+    probs = small_batch()
+    ys = [inputs.std_normal(p.n, 41000 + i) for i, p in enumerate(probs)]
+    xs = [dev(p.x) for p in probs]
+    prms = [g.params(p.kernel, p.s2, p.rho, p.tau2) for p in probs]
+    old = g.gp_batched_tile_policy()
+    try:
+        g.gp_batched_set_tile_policy(400)  # the smaller problems on FP64 tiles
+        r = g.loglik_grad_batched(xs, [dev(y) for y in ys], prms, precision="mixed_f16")
+        torch.cuda.synchronize()
+        assert np.all(r["info"].cpu().numpy() == 0)
+        out, grad = r["out"].cpu().numpy(), r["grad"].cpu().numpy()
+        for i, (p, y) in enumerate(zip(probs, ys)):
+            ref = orc.loglik_grad(p.x, y, p.kernel, p.s2, p.rho, p.tau2)
+            tol = 1e-10 if p.n <= 400 else 1e-6  # FP64 tiles: the FP64 bound
+            assert rel_err(out[i, 0], ref["loglik"]) < tol, (i, p.n)
+            gerr = np.max(np.abs(grad[i] - ref["grad"])) / max(np.max(np.abs(ref["grad"])), 1e-300)
+            assert gerr < (1e-9 if p.n <= 400 else 1e-6), (i, p.n, gerr)
+        choice, ms = g.gp_batched_autotune(r["batch"], "mixed_f16", r["ws"], r["out"], r["grad"],
+                                           r["info"])
+        torch.cuda.synchronize()
+        assert choice in ms and ms[choice] == min(ms.values()) and len(ms) >= 2
+        assert g.gp_batched_tile_policy() == choice
+        assert np.all(r["info"].cpu().numpy() == 0)
+    finally:
+        g.gp_batched_set_tile_policy(old)
