@@ -187,11 +187,22 @@ __device__ void tc_drain(const TcCtx &c, int buf, bool first) {
             tmem_ld_32x32b_x16(tb + 3 * QB + col0, rl);
         }
         tmem_ld_wait();
+        // the step's hi part (an exact integer sum times a power of two) goes
+        // in through one double-float add, the lo part (below 2^-8 of it)
+        // straight into the low word: its rounding there is below 2^-48 of
+        // the running value
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
             const float f = __fmul_rn(fa, pow2f(c.exB[buf * QB + col0 + j] - 7));
-            dfl v = df_two_sum(__fmul_rn(__uint_as_float(hi[j]), f), __fmul_rn(__uint_as_float(lo[j]), f));
-            if (!first) v = df_add(dfl{__uint_as_float(rh[j]), __uint_as_float(rl[j])}, v);
+            const float a = __fmul_rn(__uint_as_float(hi[j]), f);
+            const float b = __fmul_rn(__uint_as_float(lo[j]), f);
+            dfl v;
+            if (first) {
+                v = df_two_sum(a, b);
+            } else {
+                v = df_add_f(dfl{__uint_as_float(rh[j]), __uint_as_float(rl[j])}, a);
+                v.l = __fadd_rn(v.l, b);
+            }
             rh[j] = __float_as_uint(v.h);
             rl[j] = __float_as_uint(v.l);
         }
@@ -411,47 +422,93 @@ __device__ void stage_points(TcCtx &c, const DagProb &P, int tile) {
     }
 }
 
+// 64 x 64 FP64 product on staged operands (sA [t][r], sB [t][c]) with a
+// blocked thread mapping (rows 4 tx.., columns 4 ty..) over t in [tlo, thi):
+// the diagonal tile's products have triangular factors, and a thread skips
+// the t range where its factor block vanishes.  FP64-pipe bound, so the
+// shared-memory access pattern does not matter.
+template <bool NEG>
+__device__ __forceinline__ void blk_mma(double (&acc)[4][4], const double *sA, const double *sB,
+                                        int tlo, int thi) {
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll 2
+    for (int t = tlo; t < thi; ++t) {
+        double av[4], bv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) av[a] = NEG ? -sA[t * DLD + 4 * tx + a] : sA[t * DLD + 4 * tx + a];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) bv[b] = sB[t * DLD + 4 * ty + b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+    }
+}
+
+__device__ __forceinline__ void blk_store(const double (&acc)[4][4], double *G) {
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) G[(4 * tx + a) + DB * (4 * ty + b)] = acc[a][b];
+}
+
 // FP64 factor and inverse of the diagonal tile held in the scratch (blocks
 // 0 = A11, 1 = A21, 3 = A22): L11, W11; L21 = A21 W11^T; L22, W22 from
-// A22 - L21 L21^T; W21 = -W22 (L21 W11).  Returns the tile's log-det share.
+// A22 - L21 L21^T (lower half); W21 = -W22 (L21 W11).  Returns the tile's
+// log-det share.
 __device__ double diag_factor(TcCtx &c, const DagProb &P, int j) {
     DagSmem &dsm = *reinterpret_cast<DagSmem *>(c.opA);
     double *B = c.scr;
     const int D = 64 * 64;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     double *ld = c.red;  // two shares
+    double acc[4][4];
     __syncthreads();
     stage_a<0>(B + 0 * D, dsm.sA);
     __syncthreads();
     potrf_inv_tile(P, 2 * j, B + 0 * D, B + 4 * D, ld + 0, dsm);
     cta_gsync();
-    double acc[4][4];
+    // L21 = A21 W11^T: W11(c, t) = 0 for t > c
+    stage_a<0>(B + 1 * D, dsm.sA);
+    stage_b<1>(B + 4 * D, dsm.sB);
+    __syncthreads();
     acc_zero(acc);
-    tile_mma<0, 1, false>(acc, B + 1 * D, B + 4 * D, dsm);  // A21 W11^T
-    __syncthreads();
-    acc_store(acc, B + 1 * D);
+    blk_mma<false>(acc, dsm.sA, dsm.sB, 0, 4 * ty + 4);
+    blk_store(acc, B + 1 * D);
     cta_gsync();
-    {
-        const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    // A22 - L21 L21^T on the blocks that touch the lower half
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] = __ldcg(B + 3 * D + (tx + 16 * a) + 64 * (ty + 16 * b));
-    }
-    tile_mma<0, 1, true>(acc, B + 1 * D, B + 1 * D, dsm);  // A22 - L21 L21^T
+        for (int b = 0; b < 4; ++b) acc[a][b] = __ldcg(B + 3 * D + (4 * tx + a) + 64 * (4 * ty + b));
+    stage_a<0>(B + 1 * D, dsm.sA);
+    stage_b<1>(B + 1 * D, dsm.sB);
     __syncthreads();
-    acc_to_sA(acc, dsm.sA);
+    if (tx >= ty) blk_mma<true>(acc, dsm.sA, dsm.sB, 0, DB);
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) dsm.sA[(4 * ty + b) * DLD + 4 * tx + a] = acc[a][b];
     __syncthreads();
     potrf_inv_tile(P, 2 * j + 1, B + 3 * D, B + 6 * D, ld + 1, dsm);
     cta_gsync();
-    acc_zero(acc);
-    tile_mma<0, 0, false>(acc, B + 1 * D, B + 4 * D, dsm);  // L21 W11
+    // L21 W11: W11(t, c) = 0 for t < c
+    stage_a<0>(B + 1 * D, dsm.sA);
+    stage_b<0>(B + 4 * D, dsm.sB);
     __syncthreads();
-    acc_store(acc, B + 2 * D);
+    acc_zero(acc);
+    blk_mma<false>(acc, dsm.sA, dsm.sB, 4 * ty, DB);
+    blk_store(acc, B + 2 * D);
     cta_gsync();
-    acc_zero(acc);
-    tile_mma<0, 0, true>(acc, B + 6 * D, B + 2 * D, dsm);  // -W22 (L21 W11)
+    // W21 = -W22 (L21 W11): W22(r, t) = 0 for t > r
+    stage_a<0>(B + 6 * D, dsm.sA);
+    stage_b<0>(B + 2 * D, dsm.sB);
     __syncthreads();
-    acc_store(acc, B + 5 * D);
+    acc_zero(acc);
+    blk_mma<true>(acc, dsm.sA, dsm.sB, 0, 4 * tx + 4);
+    blk_store(acc, B + 5 * D);
     cta_gsync();
     return ld[0] + ld[1];
 }
@@ -737,27 +794,27 @@ __device__ bool tc_res(TcCtx &c, const DagProb &P, int e, int i, int j) {
         const int64_t gi = (int64_t)i * QB + r;
         const bool row_ok = gi < P.n;
         const float4 xi = df_point(row_ok ? P.x[gi] : make_double2(0.0, 0.0));
-        // rows: two independent chains (even / odd columns)
-        dfl a0{0.0f, 0.0f}, a1{0.0f, 0.0f};
-        for (int col = 64 * h; col < 64 * h + 64; col += 2) {
-            dfl v[2];
+        // rows: four independent chains (columns mod 4)
+        dfl a0{0.0f, 0.0f}, a1{0.0f, 0.0f}, a2{0.0f, 0.0f}, a3{0.0f, 0.0f};
+        for (int col = 64 * h; col < 64 * h + 64; col += 4) {
+            dfl v[4];
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
+            for (int u = 0; u < 4; ++u) {
                 const int64_t gc = (int64_t)j * QB + col + u;
-                v[u] = dfl{0.0f, 0.0f};
-                if (row_ok && gc < P.n) {
-                    if (gc == gi) v[u] = P.ddiag;
-                    else {
-                        dfl unused;
-                        df_cov_s<false>(P.kind, P.dscale, P.ds2, df_dist(xi, c.xs[col + u]), c.tab,
-                                        v[u], unused);
-                    }
-                }
+                dfl cv, unused;
+                df_cov_s<false>(P.kind, P.dscale, P.ds2, df_dist(xi, c.xs[col + u]), c.tab, cv,
+                                unused);
+                const bool in = row_ok && gc < P.n;
+                v[u] = !in ? dfl{0.0f, 0.0f} : (gc == gi ? P.ddiag : cv);
                 stg[r * QSTG_LD + col + u] = make_float2(v[u].h, v[u].l);
             }
             a0 = df_add(a0, df_mul(v[0], dfl{c.av[col].x, c.av[col].y}));
             a1 = df_add(a1, df_mul(v[1], dfl{c.av[col + 1].x, c.av[col + 1].y}));
+            a2 = df_add(a2, df_mul(v[2], dfl{c.av[col + 2].x, c.av[col + 2].y}));
+            a3 = df_add(a3, df_mul(v[3], dfl{c.av[col + 3].x, c.av[col + 3].y}));
         }
+        a0 = df_add(a0, a2);
+        a1 = df_add(a1, a3);
         const dfl a = df_add(a0, a1);
         pr[h * QB + r] = make_float2(a.h, a.l);
         __syncthreads();
@@ -900,27 +957,36 @@ __device__ bool tc_lg(TcCtx &c, const DagProb &P, int i, int j) {
         const float4 xi = df_point(row_ok ? P.x[gi] : make_double2(0.0, 0.0));
         const double ai = row_ok ? __ldcg(al + gi) : 0.0;
         const dfl aid = d2df(ai);
+        dfl h2{0.0f, 0.0f}, h3{0.0f, 0.0f};
         for (int g = 0; g < 4; ++g) {
             dfl wv[16];
             run_ld16(c, ch * 64 + g * 16, wv);  // every lane: tcgen05.ld is warp-collective
-            if (!row_ok) continue;
+#pragma unroll 4
             for (int jj = 0; jj < 16; ++jj) {
                 const int col = ch * 64 + g * 16 + jj;
                 const int64_t gc = (int64_t)j * QB + col;
-                if (gc >= P.n || gc > gi) continue;
-                if (gc == gi) {
+                dfl cv, dr;
+                df_cov_s<true>(P.kind, P.dscale, P.ds2, df_dist(xi, c.xs[col]), c.tab, cv, dr);
+                const bool off = row_ok && gc < gi && gc < P.n;
+                if (row_ok && gc == gi) {
                     const double cb = 0.5 * (ai * ai - df_to_double(wv[jj]));
                     g0 = fma(cb, P.s2, g0);
                     g2 = fma(cb, P.tau2, g2);
+                }
+                const dfl cb2 = df_add(df_mul(aid, dfl{c.av[col].x, c.av[col].y}), df_neg(wv[jj]));
+                const dfl t0 = off ? df_mul(cb2, cv) : dfl{0.0f, 0.0f};
+                const dfl t1 = off ? df_mul(cb2, dr) : dfl{0.0f, 0.0f};
+                if (jj & 1) {
+                    h2 = df_add(h2, t0);
+                    h3 = df_add(h3, t1);
                 } else {
-                    const dfl cb2 = df_add(df_mul(aid, dfl{c.av[col].x, c.av[col].y}), df_neg(wv[jj]));
-                    dfl cv, dr;
-                    df_cov_s<true>(P.kind, P.dscale, P.ds2, df_dist(xi, c.xs[col]), c.tab, cv, dr);
-                    h0 = df_add(h0, df_mul(cb2, cv));
-                    h1 = df_add(h1, df_mul(cb2, dr));
+                    h0 = df_add(h0, t0);
+                    h1 = df_add(h1, t1);
                 }
             }
         }
+        h0 = df_add(h0, h2);
+        h1 = df_add(h1, h3);
     }
     g0 += df_to_double(h0);
     double g1 = df_to_double(h1);
