@@ -420,10 +420,12 @@ static __device__ void potrf_inv_tile(const DagProb &P, int j, double *G, double
         if (tid == 0) set_info(P.info, (int64_t)j * DB + sm.badcol + 1);
         return;
     }
-    // L_rc = a_rc sqrt(1 / d_c); write L and keep it in S
+    // L_rc = a_rc sqrt(1 / d_c), one square root per column; write L and keep it in S
+    if (tid < DB) sm.dinv[tid] = sqrt(sm.dinv[tid]);
+    __syncthreads();
     for (int e = tid; e < DB * DB; e += DAG_THREADS) {
         const int r = e & (DB - 1), c = e >> 6;
-        const double v = (r >= c) ? S[c * DLD + r] * sqrt(sm.dinv[c]) : 0.0;
+        const double v = (r >= c) ? S[c * DLD + r] * sm.dinv[c] : 0.0;
         S[c * DLD + r] = v;
         G[e] = v;
     }

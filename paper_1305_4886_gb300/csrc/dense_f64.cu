@@ -69,10 +69,12 @@ __global__ void __launch_bounds__(256) potrf_tile_kernel(double *A, int64_t ld, 
         __syncthreads();
     }
     if (bad) return;
-    // L_rj = a_rj / sqrt(d_j):  a_rj * sqrt(1/d_j)
+    // L_rj = a_rj / sqrt(d_j):  a_rj * sqrt(1/d_j), one square root per column
+    if (tid < TB) dinv[tid] = sqrt(dinv[tid]);
+    __syncthreads();
     for (int e = tid; e < TB * TB; e += blockDim.x) {
         int r = e & (TB - 1), c = e >> 6;
-        if (r >= c) A[r + (int64_t)c * ld] = S[c * (TB + 1) + r] * sqrt(dinv[c]);
+        if (r >= c) A[r + (int64_t)c * ld] = S[c * (TB + 1) + r] * dinv[c];
     }
 }
 

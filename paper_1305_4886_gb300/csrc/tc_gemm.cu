@@ -445,213 +445,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
 }
 
-// ---------------------------------------------------------------------------
-// Row-scaled split of FP64 operands into three BF16 slices (see the top of
-// this file).  The operand element (r, k) is
-//   trans = 0: src[r + k ld]   (operand rows are rows of the column-major
-//                               source, K runs along its columns)
-//   trans = 1: src[k + r ld]   (operand rows are source columns)
-// lower_mask: entries above the source diagonal are treated as zero
-// (trans = 0: r + diag_off < k; trans = 1: k + diag_off < r), for triangular
-// sources whose upper part holds stale data.  One CTA packs 32 rows over a
-// 512-column chunk of K: pass 1 finds each row's bound 2^e_r over the chunk
-// (so the leading products are exact within every 512-deep chunk of a
-// contraction whose operands share the chunking), pass 2 writes the
-// slices with k contiguous (trans = 0 goes through a shared-memory
-// transpose so that both the FP64 reads and the BF16 writes are coalesced).
-// The split runs in FP32 after one FP64 -> (hi, lo) FP32 conversion.
-// ---------------------------------------------------------------------------
-struct SplitArgs {
-    const double *src;
-    int64_t ld, R, K, Kvalid;
-    int trans;
-    int64_t diag_off;
-    int lower_mask;
-    int S;      // 3: normalized FP16 slices + row exponents; 5: scaled BF16 integer slices
-    uint16_t *dst;
-    int *dst_ex;
-    int64_t ex_ld;
-    int64_t dst_rows, dst_kld, dst_row_off, dst_k_off;
-};
-
-// raw bits of operand element (r, k); masked and out-of-range entries are +0
-__device__ __forceinline__ unsigned long long split_get(const SplitArgs &a, int64_t r, int64_t k) {
-    if (r >= a.R || k >= a.Kvalid) return 0ull;
-    if (a.lower_mask) {
-        if (a.trans ? (k + a.diag_off < r) : (r + a.diag_off < k)) return 0ull;
-    }
-    const double v = a.trans ? a.src[k + r * a.ld] : a.src[r + k * a.ld];
-    return static_cast<unsigned long long>(__double_as_longlong(v));
-}
-
-// Normalized slices of one entry (mixed form), given the row's scale
-// sc = 2^{7-e}: with y = x sc held as a double-float (exact scaling),
-// s0 = round(y) (an integer in [-128, 128]), s1 = fp16(y - s0),
-// s2 = fp16(y - s0 - s1); y is then carried to about 2^-25 (2^{e-32} of x).
-__device__ __forceinline__ void split3_norm(unsigned long long u, float sc, uint16_t (&s)[3]) {
-    const dfl x = f64_to_df(u);
-    const float yh = x.h * sc, yl = x.l * sc;
-    const float q = rintf(yh);
-    float t, e;
-    two_sum(__fsub_rn(yh, q), yl, t, e);  // yh - q is exact
-    const __half h1 = __float2half_rn(t);
-    const float rest = __fadd_rn(__fsub_rn(t, __half2float(h1)), e);  // t - h1 exact
-    s[0] = __half_as_ushort(__float2half_rn(q));
-    s[1] = __half_as_ushort(h1);
-    s[2] = __half_as_ushort(__float2half_rn(rest));
-}
-
-// Integer slices on the row grid (FP64-grade mode): with y = x 2^{7-e} held
-// as a double-float, q_p = round(y_p), y_{p+1} = 256 (y_p - q_p); slice p is
-// q_p 2^{e-7-8p} (|q_p| <= 256, exact in BF16).  Five slices carry x to
-// 2^{e-40}.  All products of slice group d = p + q are then integers times
-// one power of two per output entry, so the leading groups accumulate
-// exactly in FP32 (see the top of this file for the depth limits).
-__device__ __forceinline__ void split_ozaki(unsigned long long u, float sc, float isc,
-                                            uint16_t (&s)[5]) {
-    const dfl x = f64_to_df(u);
-    float yh = x.h * sc, yl = x.l * sc, w = isc;
-#pragma unroll
-    for (int p = 0; p < 5; ++p) {
-        const float q = rintf(yh);
-        s[p] = __bfloat16_as_ushort(__float2bfloat16_rn(q * w));
-        float h, l;
-        const float d = __fsub_rn(yh, q);  // exact
-        const float t = __fadd_rn(d, yl);
-        const float bb = __fsub_rn(t, d);
-        l = __fadd_rn(__fsub_rn(d, __fsub_rn(t, bb)), __fsub_rn(yl, bb));
-        h = t;
-        yh = h * 256.0f;
-        yl = l * 256.0f;
-        w *= (1.0f / 256.0f);
-    }
-}
-
-constexpr int64_t SPLIT_KCH = TC_CHUNK_K;  // K chunk of one CTA (and of one row bound)
-constexpr int SPLIT_MAX_S = 5;
-
-__global__ void __launch_bounds__(256) split_rows_kernel(SplitArgs a) {
-    __shared__ unsigned long long pmax[8][32];
-    __shared__ float sc_s[32], isc_s[32];
-    __shared__ unsigned short tile[SPLIT_MAX_S][32][33];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t r0 = (int64_t)blockIdx.x * 32;
-    // this CTA's K chunk; each (row, chunk) gets its own bound 2^e
-    const int64_t kb = (int64_t)blockIdx.y * SPLIT_KCH;
-    const int64_t ke = min(a.K, kb + SPLIT_KCH);
-    const int64_t kev = min(ke, a.Kvalid);
-    constexpr unsigned long long ABS = 0x7FFFFFFFFFFFFFFFull;
-    // pass 1: row bounds, as the largest magnitude's bit pattern
-    if (a.trans == 0) {
-        unsigned long long m = 0ull;
-        for (int64_t k = kb + warp; k < kev; k += 8) {
-            const unsigned long long v = split_get(a, r0 + lane, k) & ABS;
-            m = v > m ? v : m;
-        }
-        pmax[warp][lane] = m;
-    } else {
-        for (int i = warp; i < 32; i += 8) {
-            unsigned long long m = 0ull;
-            for (int64_t k = kb + lane; k < kev; k += 32) {
-                const unsigned long long v = split_get(a, r0 + i, k) & ABS;
-                m = v > m ? v : m;
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
-                m = t > m ? t : m;
-            }
-            if (lane == 0) {
-                pmax[0][i] = m;
-                for (int w = 1; w < 8; ++w) pmax[w][i] = 0ull;
-            }
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        unsigned long long m = 0ull;
-        for (int w = 0; w < 8; ++w) m = pmax[w][threadIdx.x] > m ? pmax[w][threadIdx.x] : m;
-        // every entry of the row is below 2^e, e = unbiased exponent of the max + 1
-        int e = 0;
-        const int E = static_cast<int>(m >> 52);
-        if (E > 0) e = E - 1022;
-        e = max(-100, min(e, 120));
-        sc_s[threadIdx.x] = ldexpf(1.0f, 7 - e);
-        isc_s[threadIdx.x] = ldexpf(1.0f, e - 7);
-        if (a.dst_ex && r0 + threadIdx.x < a.R)
-            a.dst_ex[(a.dst_row_off + r0 + threadIdx.x) * a.ex_ld + (a.dst_k_off + kb) / SPLIT_KCH] = e;
-    }
-    __syncthreads();
-    const int64_t slice = a.dst_rows * a.dst_kld;
-    uint16_t *d0 = a.dst + (a.dst_row_off + r0) * a.dst_kld + a.dst_k_off;
-    if (a.trans == 0) {
-        for (int64_t kc = kb; kc < ke; kc += 32) {
-            // lane = row: coalesced FP64 reads down each column
-            for (int i = warp; i < 32; i += 8) {
-                uint16_t s[SPLIT_MAX_S] = {0, 0, 0, 0, 0};
-                const unsigned long long u = split_get(a, r0 + lane, kc + i);
-                if (a.S == 5) {
-                    split_ozaki(u, sc_s[lane], isc_s[lane], s);
-                } else {
-                    uint16_t t3[3];
-                    split3_norm(u, sc_s[lane], t3);
-                    s[0] = t3[0];
-                    s[1] = t3[1];
-                    s[2] = t3[2];
-                }
-#pragma unroll
-                for (int p = 0; p < SPLIT_MAX_S; ++p) tile[p][i][lane] = s[p];
-            }
-            __syncthreads();
-            // lane = k: coalesced BF16 writes along each row
-            for (int i = warp; i < 32; i += 8) {
-                const int64_t r = r0 + i, k = kc + lane;
-                if (r < a.R && k < ke) {
-                    for (int p = 0; p < a.S; ++p)
-                        d0[p * slice + (int64_t)i * a.dst_kld + k] = tile[p][lane][i];
-                }
-            }
-            __syncthreads();
-        }
-    } else {
-        for (int i = warp; i < 32; i += 8) {
-            const int64_t r = r0 + i;
-            if (r >= a.R) continue;
-            for (int64_t k = kb + lane; k < ke; k += 32) {
-                uint16_t s[SPLIT_MAX_S] = {0, 0, 0, 0, 0};
-                const unsigned long long u = split_get(a, r, k);
-                if (a.S == 5) {
-                    split_ozaki(u, sc_s[i], isc_s[i], s);
-                } else {
-                    uint16_t t3[3];
-                    split3_norm(u, sc_s[i], t3);
-                    s[0] = t3[0];
-                    s[1] = t3[1];
-                    s[2] = t3[2];
-                }
-                for (int p = 0; p < a.S; ++p) d0[p * slice + (int64_t)i * a.dst_kld + k] = s[p];
-            }
-        }
-    }
-}
-
-int split_rows(const double *src, int64_t ld, int64_t R, int64_t K, int64_t Kvalid, int trans,
-               int64_t diag_off, int lower_mask, int S, uint16_t *dst, int *dst_ex,
-               int64_t dst_rows, int64_t dst_kld, int64_t dst_row_off, int64_t dst_k_off,
-               cudaStream_t s) {
-    if (R <= 0 || K <= 0) return GP_OK;
-    if ((S != 3 && S != 5) || (S == 3) != (dst_ex != nullptr) || dst_row_off + R > dst_rows ||
-        dst_k_off + K > dst_kld || dst_k_off % SPLIT_KCH)
-        return GP_ERR_INVALID;
-    SplitArgs a{src, ld, R, K, Kvalid < K ? Kvalid : K, trans, diag_off, lower_mask, S,
-                dst, dst_ex, tc_ex_ld(dst_kld), dst_rows, dst_kld, dst_row_off, dst_k_off};
-    const int ev = prof_start(s);
-    dim3 g((unsigned)ceil_div(R, 32), (unsigned)ceil_div(K, SPLIT_KCH));
-    split_rows_kernel<<<g, 256, 0, s>>>(a);
-    GP_LAUNCH_CHECK();
-    prof_stop(ev, s, GP_PROF_PACK, 0.0, (double)R * K * (8.0 + 2.0 * S));
-    return GP_OK;
-}
 
 // C = alpha (hi + lo) + beta C over the written entries of a chunked contraction.
 __global__ void acc2_to_f64_kernel(const float2 *acc, int64_t M, int64_t N, double alpha,
