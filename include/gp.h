@@ -218,6 +218,15 @@ int gp_batched_task_stats(const void *d_ws, unsigned long long *h_out);
  * number.  The autotuner synchronises the stream (call it outside a graph
  * capture); the outputs of the last run are left in d_out / d_grad.     */
 int gp_batched_set_tile_policy(int64_t fp64_max_n);
+/* Host-only check of the batched launch's task order (no device work):
+ * rebuilds the merged task list that the launch would run for these sizes
+ * (precision GP_FP64 or GP_MIXED_F16, tile threshold fp64_max_n), and
+ * returns in *h_ntasks the list length, in *h_bad_order the number of task
+ * dependencies that are NOT earlier in the list (0 for a correct plan: the
+ * persistent launch cannot deadlock) and in *h_bad_slots the list slots not
+ * holding exactly one task (0).                                          */
+int gp_batched_plan_check(int nprob, const int64_t *h_n, int precision, int64_t fp64_max_n,
+                          int64_t *h_ntasks, int64_t *h_bad_order, int64_t *h_bad_slots);
 int64_t gp_batched_tile_policy(void);
 int gp_batched_autotune(int nprob, const int64_t *h_n, const double *const *h_dx,
                         const double *const *h_dy, const double *const *h_dmu,

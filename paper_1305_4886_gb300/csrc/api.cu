@@ -380,6 +380,14 @@ int gp_batched_set_tile_policy(int64_t fp64_max_n) {
 
 int64_t gp_batched_tile_policy(void) { return dag_fp64_max_n(); }
 
+int gp_batched_plan_check(int nprob, const int64_t *h_n, int precision, int64_t fp64_max_n,
+                          int64_t *h_ntasks, int64_t *h_bad_order, int64_t *h_bad_slots) {
+    if (!h_n || !(precision == GP_FP64 || precision == GP_MIXED_F16) || fp64_max_n < 0)
+        return GP_ERR_INVALID;
+    return dag_plan_check(nprob, h_n, precision == GP_MIXED_F16, fp64_max_n, h_ntasks, h_bad_order,
+                          h_bad_slots);
+}
+
 // The tile autotuner of the mixed batched launch: time the caller's batch
 // with every candidate threshold (problems with n <= threshold on FP64
 // 64 x 64 tiles, the others on tensor-core 128 x 128 tiles), one warm-up

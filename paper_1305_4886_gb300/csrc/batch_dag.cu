@@ -112,7 +112,6 @@ __global__ void dag_setup_kernel(const __grid_constant__ DagSetup s, DagProb *pr
     }
 }
 
-__device__ __forceinline__ int64_t round_start(int64_t N, int r, int R) { return (int64_t)r * N / R; }
 
 // One CTA per round: exclusive scan over problems of their task counts in
 // the round; poff[r * P + p], rtot[r].
@@ -168,7 +167,7 @@ __global__ void dag_plan_fill(const DagProb *probs, int P, int R, const int *pof
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t N = probs[p].ntasks;
     if (j >= N) return;
-    const int r = (int)(((int64_t)(j + 1) * R - 1) / N);
+    const int r = round_of(j, N, R);
     const int64_t pos = roff[r] + poff[(int64_t)r * P + p] + (j - round_start(N, r, R));
     list[pos] = make_int2(p, j);
 }
@@ -463,6 +462,140 @@ int dag_stats(const void *d_ws, unsigned long long *h_out) {
         h_out[2 * DAG_NSTAT + q] = hd.cnt[q];
     }
     h_out[3 * DAG_NSTAT] = hd.steps;
+    return GP_OK;
+}
+
+// --------------------------------------------------------------------------
+// Host check of the ordering invariant (no device work): rebuild the merged
+// global list of a batch as dag_plan_rounds / dag_plan_fill do, decode every
+// task, list the flags it waits on (the waits of the task functions) and the
+// tasks that raise them, and count the dependencies that are not earlier in
+// the list (a correct plan has none: the launch cannot deadlock) and the
+// list slots that are not exactly one task.
+// --------------------------------------------------------------------------
+int dag_plan_check(int nprob, const int64_t *h_n, int mixed, int64_t fp64_max_n, int64_t *h_ntasks,
+                   int64_t *h_bad_order, int64_t *h_bad_slots) {
+    if (nprob < 1 || nprob > 65535) return GP_ERR_INVALID;
+    for (int i = 0; i < nprob; ++i)
+        if (h_n[i] < 1 || ceil_div(h_n[i], mixed ? QB : DB) > 8192) return GP_ERR_INVALID;
+    const DagLayout L = dag_layout(nprob, h_n, mixed, 1, fp64_max_n);
+    const int R = L.R;
+    // merged positions, as the device plan computes them
+    std::vector<int64_t> rtot(R, 0), roff(R + 1, 0);
+    std::vector<int64_t> poff((size_t)R * nprob, 0);
+    for (int r = 0; r < R; ++r) {
+        int64_t acc = 0;
+        for (int p = 0; p < nprob; ++p) {
+            const int64_t N = L.ntasks[p];
+            poff[(size_t)r * nprob + p] = acc;
+            acc += round_start(N, r + 1, R) - round_start(N, r, R);
+        }
+        rtot[r] = acc;
+    }
+    for (int r = 0; r < R; ++r) roff[r + 1] = roff[r] + rtot[r];
+    std::vector<int64_t> base(nprob + 1, 0);
+    for (int p = 0; p < nprob; ++p) base[p + 1] = base[p] + L.ntasks[p];
+    std::vector<int64_t> pos(base[nprob], -1);
+    std::vector<int> hits(L.ntot, 0);
+    int64_t bad_slots = 0;
+    for (int p = 0; p < nprob; ++p)
+        for (int64_t j = 0; j < L.ntasks[p]; ++j) {
+            const int64_t N = L.ntasks[p];
+            const int r = round_of(j, N, R);
+            const int64_t q = roff[r] + poff[(size_t)r * nprob + p] + (j - round_start(N, r, R));
+            if (q < 0 || q >= L.ntot) {
+                ++bad_slots;
+                continue;
+            }
+            pos[base[p] + j] = q;
+            ++hits[q];
+        }
+    for (int64_t q = 0; q < L.ntot; ++q)
+        if (hits[q] != 1) ++bad_slots;
+    // per problem: the producer of every flag (local task index) and the waits
+    int64_t bad = 0;
+    for (int p = 0; p < nprob; ++p) {
+        const int T = L.T[p], tc = L.tc[p], N = L.ntasks[p];
+        const int nt = dag_ntiles(T);
+        std::vector<int> Lp(nt, -1), Xp(nt, -1);
+        std::vector<std::vector<int>> resp(DAG_EVALS);
+        std::vector<int> corrp(DAG_EVALS, -1), lgp;
+        int solvep = -1, finp = -1;
+        std::vector<int> type(N), ti(N), tk(N);
+        for (int q = 0; q < N; ++q) {
+            int i = 0, k = 0;
+            const int t = dag_decode(T, tc, q, i, k);
+            type[q] = t;
+            ti[q] = i;
+            tk[q] = k;
+            switch (t) {
+                case DT_CHOL:
+                    Lp[tile_index(T, i, k)] = q;
+                    if (i == k) Xp[tile_index(T, i, i)] = q;
+                    break;
+                case DT_TRTRI: Xp[tile_index(T, i, k)] = q; break;
+                case DT_SOLVE: solvep = q; break;
+                case DT_RES: resp[k].push_back(q); break;
+                case DT_CORR: corrp[k] = q; break;
+                case DT_FINLL: finp = q; break;
+                case DT_LG: lgp.push_back(q); break;
+                default: break;
+            }
+        }
+        auto before = [&](int prod, int q) {
+            if (prod < 0 || pos[base[p] + prod] >= pos[base[p] + q]) ++bad;
+        };
+        for (int q = 0; q < N; ++q) {
+            const int i = ti[q], k = tk[q];
+            switch (type[q]) {
+                case DT_CHOL:
+                    for (int m = 0; m < k; ++m) {
+                        before(Lp[tile_index(T, i, m)], q);
+                        before(Lp[tile_index(T, k, m)], q);
+                    }
+                    if (i > k) before(Lp[tile_index(T, k, k)], q);
+                    break;
+                case DT_SOLVE:
+                    for (int a = 0; a < T; ++a)
+                        for (int b = 0; b <= a; ++b) before(Lp[tile_index(T, a, b)], q);
+                    break;
+                case DT_TRTRI:
+                    for (int m = k + 1; m <= i; ++m) {
+                        before(Xp[tile_index(T, i, m)], q);
+                        before(Lp[tile_index(T, m, k)], q);
+                    }
+                    before(Xp[tile_index(T, k, k)], q);
+                    break;
+                case DT_LG:
+                    for (int m = i; m < T; ++m) {
+                        before(Xp[tile_index(T, m, i)], q);
+                        before(Xp[tile_index(T, m, k)], q);
+                    }
+                    before(tc ? finp : solvep, q);
+                    break;
+                case DT_RES:
+                    before(k == 0 ? solvep : corrp[k - 1], q);
+                    break;
+                case DT_CORR:
+                    if ((int)resp[k].size() != nt) ++bad;
+                    for (int d : resp[k]) before(d, q);
+                    break;
+                case DT_FINLL:
+                    if ((int)resp[DAG_EVALS - 1].size() != nt) ++bad;
+                    for (int d : resp[DAG_EVALS - 1]) before(d, q);
+                    break;
+                default:  // FINAL
+                    if ((int)lgp.size() != nt) ++bad;
+                    for (int d : lgp) before(d, q);
+                    break;
+            }
+        }
+        for (int t = 0; t < nt; ++t)
+            if (Lp[t] < 0 || Xp[t] < 0) ++bad;  // every tile has its producers
+    }
+    if (h_ntasks) *h_ntasks = L.ntot;
+    if (h_bad_order) *h_bad_order = bad;
+    if (h_bad_slots) *h_bad_slots = bad_slots;
     return GP_OK;
 }
 

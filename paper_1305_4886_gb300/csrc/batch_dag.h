@@ -88,7 +88,7 @@ __host__ __device__ inline int tile_index(int T, int i, int j) {
 
 enum { DT_RES = 5, DT_CORR = 6, DT_FINLL = 7 };
 
-__device__ inline void dag_decode_xt(int T, int q, int &i, int &k) {
+__host__ __device__ inline void dag_decode_xt(int T, int q, int &i, int &k) {
     int kk = T - 2;
     while (q >= T - 1 - kk) {
         q -= T - 1 - kk;
@@ -105,7 +105,7 @@ __device__ inline void dag_decode_xt(int T, int q, int &i, int &k) {
 // evaluation FINLL) through the TRTRI tasks in DAG_CHAIN segments, so that
 // each stage of the chain sits well after the one it waits for.  A RES task
 // returns its tile as i = row | (column << 16) and the evaluation in k.
-__device__ inline int dag_decode(int T, int mixed, int q, int &i, int &k) {
+__host__ __device__ inline int dag_decode(int T, int mixed, int q, int &i, int &k) {
     const int nc = dag_ntiles(T);
     if (q < nc) {
         int j = 0;
@@ -163,6 +163,13 @@ __device__ inline int dag_decode(int T, int mixed, int q, int &i, int &k) {
         return DT_LG;
     }
     return DT_FINAL;
+}
+
+// First task of round r of R in a list of N tasks (the proportional merge).
+__host__ __device__ inline int64_t round_start(int64_t N, int r, int R) { return (int64_t)r * N / R; }
+// Round of local task j of a list of N tasks.
+__host__ __device__ inline int round_of(int64_t j, int64_t N, int R) {
+    return (int)(((j + 1) * (int64_t)R - 1) / N);
 }
 
 // Tensor-core (mixed) form: 128 x 128 tiles, three FP16 slices per operand.

@@ -85,6 +85,8 @@ int dag_run(int nprob, const int64_t *h_n, const double *const *h_dx, const doub
             void *d_ws, size_t ws_bytes, double *d_out, double *d_grad, int64_t *d_info,
             cudaStream_t s);
 void dag_set_fp64_max_n(int64_t v);
+int dag_plan_check(int nprob, const int64_t *h_n, int mixed, int64_t fp64_max_n, int64_t *h_ntasks,
+                   int64_t *h_bad_order, int64_t *h_bad_slots);
 int64_t dag_fp64_max_n();
 int dag_stats(const void *d_ws, unsigned long long *h_out);
 void dag_set_profile(int on);

@@ -44,6 +44,7 @@ SYMBOLS = [
     "gp_batched_set_tile_policy",
     "gp_batched_tile_policy",
     "gp_batched_autotune",
+    "gp_batched_plan_check",
 ]
 
 
@@ -134,6 +135,10 @@ def lib():
                                               ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(ctypes.c_int)]
             L.gp_batched_autotune.restype = ci
+            L.gp_batched_plan_check.argtypes = [ci, p, ci, i64, ctypes.POINTER(ctypes.c_int64),
+                                                ctypes.POINTER(ctypes.c_int64),
+                                                ctypes.POINTER(ctypes.c_int64)]
+            L.gp_batched_plan_check.restype = ci
             for name in ["gp_cov_fill", "gp_chol", "gp_backsolve", "gp_mult_chol", "gp_loglik",
                          "gp_loglik_grad", "gp_syrk_lower", "gp_prof_enable", "gp_prof_read"]:
                 getattr(L, name).restype = ci
@@ -287,6 +292,17 @@ def gp_batched_autotune(batch, precision, ws, out, grad, info, stream=None):
     nmax = max(batch.n[i] for i in range(batch.nprob))
     cands = [t for t in AUTOTUNE_CANDIDATES if t == 0 or t < nmax][:ncand.value]
     return int(choice.value), {t: ms[q] for q, t in enumerate(cands)}
+
+
+def gp_batched_plan_check(ns, precision="mixed_f16", fp64_max_n=0):
+    """Host check of the batched launch's task order: (tasks, dependencies
+    not earlier in the list, list slots not holding exactly one task)."""
+    arr = (ctypes.c_int64 * len(ns))(*[int(v) for v in ns])
+    nt, bo, bs = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(lib().gp_batched_plan_check(len(ns), ctypes.cast(arr, ctypes.c_void_p), _prec(precision),
+                                       int(fp64_max_n), ctypes.byref(nt), ctypes.byref(bo),
+                                       ctypes.byref(bs)), "gp_batched_plan_check")
+    return nt.value, bo.value, bs.value
 
 
 def loglik_grad_batched(xs, ys, prms, precision="mixed_f16", mus=None, ws=None):
