@@ -279,20 +279,24 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(int64_t M, int64_t N, int
     }
 }
 
-// 32 x 32 output tiles, 64 threads (4 x 4 per thread): four times the CTAs of
-// the 64 x 64 kernel for the small, latency-bound updates of the diagonal
-// blocks.  mask.kchunk > 0 splits K into chunks over grid.z and adds each
-// partial product with FP64 atomics (C must already hold beta C).
+// 32 x 32 output tiles, 128 threads (2 x 4 per thread): four times the
+// CTAs of the 64 x 64 kernel for the small, latency-bound updates of the
+// diagonal blocks, and four warps per CTA so that one CTA keeps all four FP64
+// sub-pipes of its SM busy.  mask.kchunk > 0 splits K into chunks over
+// grid.z and adds each partial product with FP64 atomics (C must already
+// hold beta C).
 constexpr int SB = 32;
+constexpr int SB_THREADS = 128;
 
-__global__ void __launch_bounds__(64) gemm_f64_s32_kernel(int64_t M, int64_t N, int64_t K,
-                                                          double alpha,
-                                                          const double *__restrict__ A,
-                                                          int64_t lda, int opA,
-                                                          const double *__restrict__ B,
-                                                          int64_t ldb, int opB, double beta,
-                                                          double *C, int64_t ldc, F64Mask mask,
-                                                          const int64_t *info) {
+__global__ void __launch_bounds__(SB_THREADS) gemm_f64_s32_kernel(int64_t M, int64_t N, int64_t K,
+                                                                  double alpha,
+                                                                  const double *__restrict__ A,
+                                                                  int64_t lda, int opA,
+                                                                  const double *__restrict__ B,
+                                                                  int64_t ldb, int opB, double beta,
+                                                                  double *C, int64_t ldc,
+                                                                  F64Mask mask,
+                                                                  const int64_t *info) {
     __shared__ double As[GBK][SB + 1];
     __shared__ double Bs[GBK][SB + 1];
     if (info && failed(info)) return;
@@ -306,16 +310,16 @@ __global__ void __launch_bounds__(64) gemm_f64_s32_kernel(int64_t M, int64_t N, 
     if (mask.tri_k && c0 - mask.tri_off > kbeg) kbeg = ((c0 - mask.tri_off) / GBK) * GBK;
     if (kbeg >= kend) return;
     const int tid = threadIdx.x;
-    const int tx = tid & 7, ty = tid >> 3;
-    double acc[4][4];
+    const int tx = tid & 15, ty = tid >> 4;  // rows tx + 16a (a < 2), columns ty + 8b (b < 4)
+    double acc[2][4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
     for (int64_t k0 = kbeg; k0 < kend; k0 += GBK) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int idx = tid + 64 * q;  // 0..511
+        for (int q = 0; q < 4; ++q) {
+            const int idx = tid + SB_THREADS * q;  // 0..511
             int r, k, c, kb;
             double v = 0.0, w = 0.0;
             if (opA == 0) { r = idx & 31; k = idx >> 5; }
@@ -336,13 +340,13 @@ __global__ void __launch_bounds__(64) gemm_f64_s32_kernel(int64_t M, int64_t N, 
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < GBK; ++k) {
-            double av[4], bv[4];
+            double av[2], bv[4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) av[a] = As[k][tx + 8 * a];
+            for (int a = 0; a < 2; ++a) av[a] = As[k][tx + 16 * a];
 #pragma unroll
             for (int b = 0; b < 4; ++b) bv[b] = Bs[k][ty + 8 * b];
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+            for (int a = 0; a < 2; ++a)
 #pragma unroll
                 for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
         }
@@ -353,8 +357,8 @@ __global__ void __launch_bounds__(64) gemm_f64_s32_kernel(int64_t M, int64_t N, 
         const int64_t gc = c0 + ty + 8 * b;
         if (gc >= N) continue;
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            const int64_t gr = r0 + tx + 8 * a;
+        for (int a = 0; a < 2; ++a) {
+            const int64_t gr = r0 + tx + 16 * a;
             if (gr >= M) continue;
             if (mask.out_lower && gr + mask.diag_off < gc) continue;
             double *p = C + gr + gc * ldc;
@@ -387,7 +391,7 @@ int gemm_f64_ex(int64_t M, int64_t N, int64_t K, double alpha, const double *A, 
         }
         const int64_t kz = m.kchunk > 0 ? ceil_div(K, m.kchunk) : 1;
         dim3 g((unsigned)ceil_div(M, SB), (unsigned)ceil_div(N, SB), (unsigned)kz);
-        gemm_f64_s32_kernel<<<g, 64, 0, s>>>(M, N, K, alpha, A, lda, opA, B, ldb, opB, beta, C, ldc,
+        gemm_f64_s32_kernel<<<g, SB_THREADS, 0, s>>>(M, N, K, alpha, A, lda, opA, B, ldb, opB, beta, C, ldc,
                                              m, info);
         GP_LAUNCH_CHECK();
         return GP_OK;
