@@ -249,6 +249,9 @@ static __device__ bool dag_wait(const int *f, int target, DagHdr *h, int64_t *in
             }
             *reinterpret_cast<long long *>(okslot + 2) += clock64() - c0;
         }
+        // the acquire, made cumulative for the CTA's other threads, whose
+        // reads of the producer's tile follow the barrier below
+        __threadfence();
         *okslot = ok;
     }
     __syncthreads();
@@ -370,6 +373,11 @@ static __device__ void fill_tile(const DagProb &P, int i, int j, double (&acc)[4
         const int64_t gi = (int64_t)i * DB + tid, gj = (int64_t)j * DB + tid;
         sm.xr[tid] = gi < P.n ? P.x[gi] : make_double2(0.0, 0.0);
         sm.xc[tid] = gj < P.n ? P.x[gj] : make_double2(0.0, 0.0);
+        // a location that is not finite: d_info = -2 before any task can
+        // read a tile built from it (the first status wins)
+        if (!isfinite(sm.xr[tid].x) || !isfinite(sm.xr[tid].y) || !isfinite(sm.xc[tid].x) ||
+            !isfinite(sm.xc[tid].y))
+            set_info(P.info, -2);
     }
     __syncthreads();
 #pragma unroll
@@ -526,8 +534,10 @@ static __device__ bool task_solve(const DagProb &P, DagSmem &sm, DagHdr *h) {
     int *solved = P.flag + dag_solved_flag(T);
     double *r = P.vec, *v = P.vec + m, *al = P.vec + 2 * m;
     if (!failed(P.info)) {
-        for (int64_t e = tid; e < m; e += DAG_THREADS)
+        for (int64_t e = tid; e < m; e += DAG_THREADS) {
             r[e] = e < P.n ? P.y[e] - (P.mu ? P.mu[e] : 0.0) : 0.0;
+            if (!isfinite(r[e])) set_info(P.info, -2);
+        }
         const int row = tid & (DB - 1), q = tid >> 6;
         // forward: v_i = W_i (r_i - sum_{j<i} L_ij v_j)
         for (int i = 0; i < T; ++i) {

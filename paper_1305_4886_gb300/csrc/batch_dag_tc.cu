@@ -418,7 +418,10 @@ __device__ void tile_to_scr(TcCtx &c, F value) {
 __device__ void stage_points(TcCtx &c, const DagProb &P, int tile) {
     if (threadIdx.x < QB) {
         const int64_t g = (int64_t)tile * QB + threadIdx.x;
-        c.xs[threadIdx.x] = df_point(g < P.n ? P.x[g] : make_double2(0.0, 0.0));
+        const double2 p = g < P.n ? P.x[g] : make_double2(0.0, 0.0);
+        // a location that is not finite: d_info = -2 (first status wins)
+        if (!isfinite(p.x) || !isfinite(p.y)) set_info(P.info, -2);
+        c.xs[threadIdx.x] = df_point(p);
     }
 }
 
@@ -529,6 +532,8 @@ __device__ bool tc_chol(TcCtx &c, const DagProb &P, int i, int j) {
             if (!tc_contract(c, P, j, pair)) return false;
         }
         // A' = C_ij - running, to the FP64 scratch
+        __syncthreads();
+        stage_points(c, P, i);  // checks the row tile's locations
         __syncthreads();
         stage_points(c, P, j);
         __syncthreads();
@@ -752,6 +757,7 @@ __device__ bool tc_solve(TcCtx &c, const DagProb &P) {
         double rr = 0.0;
         for (int64_t e = tid; e < m; e += QTHREADS) {
             const double v = e < P.n ? P.y[e] - (P.mu ? P.mu[e] : 0.0) : 0.0;
+            if (!isfinite(v)) set_info(P.info, -2);
             r[e] = v;
             al[e] = v;
             rr = fma(v, v, rr);

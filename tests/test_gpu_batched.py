@@ -120,3 +120,37 @@ def test_batched_mixed_tile_policy_and_autotune(g, orc):
         assert np.all(r["info"].cpu().numpy() == 0)
     finally:
         g.gp_batched_set_tile_policy(old)
+
+
+@pytest.mark.parametrize("precision,tl,tg", [("fp64", 1e-10, 1e-9), ("mixed_f16", 1e-6, 1e-6)])
+def test_batched_means_and_failing_problems(g, orc, precision, tl, tg):
+    """Per-problem means; a problem whose covariance is singular (every
+    location equal, no nugget: the second pivot is exactly 0, d_info = 2) and
+    one with a NaN location (d_info = -2) report their own status and NaN
+    outputs, and the rest of the batch still matches the oracle."""
+    probs = small_batch()
+    sing, bad = 4, 6
+    probs[sing].x = np.repeat(probs[sing].x[:1], probs[sing].n, axis=0)
+    probs[sing].s2, probs[sing].tau2 = 1.0, 0.0
+    probs[bad].x = probs[bad].x.copy()
+    probs[bad].x[3, 0] = float("nan")
+    ys = [inputs.std_normal(p.n, 42000 + i) for i, p in enumerate(probs)]
+    mus = [np.full(p.n, 0.5) if i % 3 == 0 else None for i, p in enumerate(probs)]
+    r = g.loglik_grad_batched([dev(p.x) for p in probs], [dev(y) for y in ys],
+                              [g.params(p.kernel, p.s2, p.rho, p.tau2) for p in probs],
+                              precision=precision,
+                              mus=[dev(m) if m is not None else None for m in mus])
+    torch.cuda.synchronize()
+    info = r["info"].cpu().numpy()
+    out, grad = r["out"].cpu().numpy(), r["grad"].cpu().numpy()
+    assert info[sing] == 2 and info[bad] == -2
+    for i in (sing, bad):
+        assert np.all(np.isnan(out[i])) and np.all(np.isnan(grad[i]))
+    for i, (p, y) in enumerate(zip(probs, ys)):
+        if i in (sing, bad):
+            continue
+        assert info[i] == 0, (i, info[i])
+        ref = orc.loglik_grad(p.x, y, p.kernel, p.s2, p.rho, p.tau2, mu=mus[i])
+        assert rel_err(out[i, 0], ref["loglik"]) < tl, (i, p.n)
+        gerr = np.max(np.abs(grad[i] - ref["grad"])) / max(np.max(np.abs(ref["grad"])), 1e-300)
+        assert gerr < tg, (i, p.n, gerr)
