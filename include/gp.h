@@ -200,7 +200,8 @@ int gp_loglik_grad_batched(int nprob, const int64_t *h_n, const double *const *h
  * tasks [20..29] per class (0 off-diagonal Cholesky tile, 1 solve,
  * 2 inverse tile, 3 inverse-product + gradient tile, 4 gradient sum,
  * 5 refinement residual, 6 refinement correction, 7 log-likelihood,
- * 8 diagonal Cholesky tile), then [30] tensor-core contraction steps.
+ * 8 diagonal Cholesky tile, 9 refinement residual of a problem already
+ * converged), then [30] tensor-core contraction steps.
  * Synchronous (one device-to-host copy).                                  */
 void gp_batched_profile(int on);
 int gp_batched_task_stats(const void *d_ws, unsigned long long *h_out);

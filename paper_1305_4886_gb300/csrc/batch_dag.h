@@ -271,6 +271,12 @@ __device__ __forceinline__ void dag_stat_end(DagHdr *h, int cls, long long c0, c
     atomicAdd(&h->cnt[cls], 1ull);
 }
 
+// A problem's status (or any flag another CTA may set meanwhile) as ONE
+// value for the whole CTA: every thread must take the same branch around
+// the barriers that follow.  A barrier itself (all threads call it).
+__device__ __forceinline__ bool dag_uniform(bool v) { return __syncthreads_or(v ? 1 : 0) != 0; }
+__device__ __forceinline__ bool dag_failed(const DagProb &P) { return dag_uniform(failed(P.info)); }
+
 // All of the CTA's writes so far, then *f += 1 with release semantics.
 __device__ __forceinline__ void dag_signal(int *f) {
     __syncthreads();
@@ -486,7 +492,7 @@ static __device__ bool task_chol(const DagProb &P, int i, int j, DagSmem &sm, Da
     const int T = P.T;
     int *Lf = P.flag, *Xf = P.flag + dag_ntiles(T);
     const int tij = tile_index(T, i, j);
-    if (!failed(P.info)) {
+    if (!dag_failed(P)) {
         double acc[4][4];
         fill_tile(P, i, j, acc, sm);
         for (int k = 0; k < j; ++k) {
@@ -533,7 +539,7 @@ static __device__ bool task_solve(const DagProb &P, DagSmem &sm, DagHdr *h) {
     int *Lf = P.flag;
     int *solved = P.flag + dag_solved_flag(T);
     double *r = P.vec, *v = P.vec + m, *al = P.vec + 2 * m;
-    if (!failed(P.info)) {
+    if (!dag_failed(P)) {
         for (int64_t e = tid; e < m; e += DAG_THREADS) {
             r[e] = e < P.n ? P.y[e] - (P.mu ? P.mu[e] : 0.0) : 0.0;
             if (!isfinite(r[e])) set_info(P.info, -2);
@@ -604,7 +610,7 @@ static __device__ bool task_solve(const DagProb &P, DagSmem &sm, DagHdr *h) {
 static __device__ bool task_trtri(const DagProb &P, int i, int k, DagSmem &sm, DagHdr *h) {
     const int T = P.T;
     int *Lf = P.flag, *Xf = P.flag + dag_ntiles(T);
-    if (!failed(P.info)) {
+    if (!dag_failed(P)) {
         double acc[4][4];
         acc_zero(acc);
         for (int m = i; m > k; --m) {
@@ -633,7 +639,7 @@ static __device__ bool task_lg(const DagProb &P, int i, int j, DagSmem &sm, DagH
     int *lgc = P.flag + dag_lg_flag(T, 0);
     const int64_t m = (int64_t)T * DB;
     double g0 = 0.0, g1 = 0.0, g2 = 0.0;
-    if (!failed(P.info)) {
+    if (!dag_failed(P)) {
         double w[4][4];
         acc_zero(w);
         for (int mm = i; mm < T; ++mm) {
@@ -702,6 +708,7 @@ static __device__ bool task_final(const DagProb &P, DagSmem &sm, DagHdr *h) {
     int *lgc = P.flag + dag_lg_flag(T, 0);
     const int nt = dag_ntiles(T);
     if (!dag_wait(lgc, nt, h, P.info, sm.ok)) return false;
+    const bool bad = dag_failed(P);
     // Neumaier sums per thread, then in thread order
     double s[3] = {0.0, 0.0, 0.0}, c[3] = {0.0, 0.0, 0.0};
     for (int t = tid; t < nt; t += DAG_THREADS)
@@ -721,7 +728,7 @@ static __device__ bool task_final(const DagProb &P, DagSmem &sm, DagHdr *h) {
             C += (fabs(S) >= fabs(x)) ? (S - u) + x : (x - u) + S;
             S = u;
         }
-        P.grad[tid] = failed(P.info) ? nan("") : S + C;
+        P.grad[tid] = bad ? nan("") : S + C;
     }
     return true;
 }

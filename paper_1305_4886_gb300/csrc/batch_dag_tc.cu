@@ -520,7 +520,7 @@ __device__ bool tc_chol(TcCtx &c, const DagProb &P, int i, int j) {
     const int T = P.T;
     int *Lf = f_L(P), *Xf = f_X(P);
     const int tij = tile_index(T, i, j);
-    if (!failed(P.info)) {
+    if (!dag_failed(P)) {
         if (j > 0) {
             auto pair = [&](int k, const uint8_t *&ga, const uint8_t *&gb) -> bool {
                 if (!dag_wait(Lf + tile_index(T, i, k), 1, c.h, P.info, c.ok)) return false;
@@ -599,7 +599,7 @@ __device__ bool tc_chol(TcCtx &c, const DagProb &P, int i, int j) {
 __device__ bool tc_trtri(TcCtx &c, const DagProb &P, int i, int k) {
     const int T = P.T;
     int *Lf = f_L(P), *Xf = f_X(P);
-    if (!failed(P.info)) {
+    if (!dag_failed(P)) {
         auto pair = [&](int q, const uint8_t *&ga, const uint8_t *&gb) -> bool {
             const int m = i - q;  // m = i, i - 1, ..., k + 1
             if (!dag_wait(Xf + tile_index(T, i, m), 1, c.h, P.info, c.ok)) return false;
@@ -750,7 +750,7 @@ __device__ bool tc_solve(TcCtx &c, const DagProb &P) {
     const int T = P.T, tid = threadIdx.x;
     const int64_t m = (int64_t)T * QB;
     double *r = P.vec, *al = P.vec + m, *tt = P.vec + 3 * m;
-    if (!failed(P.info)) {
+    if (!dag_failed(P)) {
         for (int i = 0; i < T; ++i)
             for (int j = 0; j <= i; ++j)
                 if (!dag_wait(f_L(P) + tile_index(T, i, j), 1, c.h, P.info, c.ok)) return false;
@@ -782,7 +782,9 @@ __device__ bool tc_res(TcCtx &c, const DagProb &P, int e, int i, int j) {
     const double *al = P.vec + m;
     int *wait_f = e == 0 ? f_solved(P) : f_corr(P, e - 1);
     if (!dag_wait(wait_f, 1, c.h, P.info, c.ok)) return false;
-    if (!failed(P.info) && !*reinterpret_cast<volatile int *>(f_conv(P))) {
+    const bool skip = dag_uniform(failed(P.info) || *reinterpret_cast<volatile int *>(f_conv(P)));
+    if (threadIdx.x == 0) c.misc[1] = skip ? 1 : 0;
+    if (!skip) {
         float2 *stg = reinterpret_cast<float2 *>(c.opA);
         float2 *avr = reinterpret_cast<float2 *>(c.opA + 2 * QOPER - 4096);  // alpha of the rows
         float2 *pr = reinterpret_cast<float2 *>(c.red);                      // [2][128]
@@ -882,7 +884,7 @@ __device__ bool tc_corr(TcCtx &c, const DagProb &P, int e) {
     const int64_t m = (int64_t)T * QB;
     if (!dag_wait(f_res(P, e), dag_ntiles(T), c.h, P.info, c.ok)) return false;
     int *conv = f_conv(P);
-    if (!failed(P.info) && !*reinterpret_cast<volatile int *>(conv)) {
+    if (!dag_uniform(failed(P.info) || *reinterpret_cast<volatile int *>(conv))) {
         const double ratio = tc_combine(c, P);
         double *stat = P.part + T + 3 * dag_ntiles(T);
         if (ratio <= QREFINE_TOL) {
@@ -905,9 +907,9 @@ __device__ bool tc_finll(TcCtx &c, const DagProb &P) {
     const int T = P.T, tid = threadIdx.x;
     const int64_t m = (int64_t)T * QB;
     if (!dag_wait(f_res(P, DAG_EVALS - 1), dag_ntiles(T), c.h, P.info, c.ok)) return false;
-    if (!failed(P.info)) {
+    if (!dag_failed(P)) {
         double *stat = P.part + T + 3 * dag_ntiles(T);
-        const bool conv = *reinterpret_cast<volatile int *>(f_conv(P)) != 0;
+        const bool conv = dag_uniform(*reinterpret_cast<volatile int *>(f_conv(P)) != 0);
         const double ratio = conv ? __ldcg(stat) : tc_combine(c, P);
         const double *r = P.vec, *al = P.vec + m;
         double q = 0.0;
@@ -937,7 +939,7 @@ __device__ bool tc_lg(TcCtx &c, const DagProb &P, int i, int j) {
     int *Xf = f_X(P);
     double g0 = 0.0, g2 = 0.0;
     dfl h0{0.0f, 0.0f}, h1{0.0f, 0.0f};
-    if (!failed(P.info)) {
+    if (!dag_failed(P)) {
         auto pair = [&](int q, const uint8_t *&ga, const uint8_t *&gb) -> bool {
             const int mm = i + q;
             if (!dag_wait(Xf + tile_index(T, mm, i), 1, c.h, P.info, c.ok)) return false;
@@ -1021,6 +1023,7 @@ __device__ bool tc_final(TcCtx &c, const DagProb &P) {
     const int T = P.T, tid = threadIdx.x;
     const int nt = dag_ntiles(T);
     if (!dag_wait(f_lg(P), nt, c.h, P.info, c.ok)) return false;
+    const bool bad = dag_failed(P);
     double s[3] = {0.0, 0.0, 0.0}, cc[3] = {0.0, 0.0, 0.0};
     for (int t = tid; t < nt; t += QTHREADS)
         for (int q = 0; q < 3; ++q) {
@@ -1039,7 +1042,7 @@ __device__ bool tc_final(TcCtx &c, const DagProb &P) {
             C += (fabs(S) >= fabs(x)) ? (S - u) + x : (x - u) + S;
             S = u;
         }
-        P.grad[tid] = failed(P.info) ? nan("") : S + C;
+        P.grad[tid] = bad ? nan("") : S + C;
     }
     __syncthreads();
     return true;
@@ -1118,13 +1121,18 @@ __global__ void __launch_bounds__(QTHREADS, 1)
             case DT_CHOL: ok = tc_chol(c, P, i, k); break;
             case DT_SOLVE: ok = tc_solve(c, P); break;
             case DT_TRTRI: ok = tc_trtri(c, P, i, k); break;
-            case DT_RES: ok = tc_res(c, P, k, i & 0xffff, i >> 16); break;
+            case DT_RES:
+                c.misc[1] = 0;
+                ok = tc_res(c, P, k, i & 0xffff, i >> 16);
+                break;
             case DT_CORR: ok = tc_corr(c, P, k); break;
             case DT_FINLL: ok = tc_finll(c, P); break;
             case DT_LG: ok = tc_lg(c, P, i, k); break;
             default: ok = tc_final(c, P); break;
         }
-        dag_stat_end(h, (type == DT_CHOL && i == k) ? 8 : type, c0, c.ok);
+        // class 9: a residual task of a problem already converged (no work)
+        const int cls = (type == DT_CHOL && i == k) ? 8 : (type == DT_RES && c.misc[1]) ? 9 : type;
+        dag_stat_end(h, cls, c0, c.ok);
         if (!ok) break;
     }
     cp_async_wait_all();

@@ -321,7 +321,8 @@ def loglik_grad_batched(xs, ys, prms, precision="mixed_f16", mus=None, ws=None):
 
 
 BATCH_TASK_CLASSES = ["chol_offdiag", "solve", "inverse", "inverse_product_grad", "grad_sum",
-                      "refine_residual", "refine_correction", "loglik", "chol_diag"]
+                      "refine_residual", "refine_correction", "loglik", "chol_diag",
+                      "refine_residual_skipped"]
 
 
 def gp_batched_profile(on):
