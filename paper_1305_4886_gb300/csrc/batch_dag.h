@@ -406,7 +406,7 @@ static __device__ void fill_tile(const DagProb &P, int i, int j, double (&acc)[4
 // Wg, and the tile's sum of log L_rr over rows < n to *logpart.
 static __device__ void potrf_inv_tile(const DagProb &P, int j, double *G, double *Wg, double *logpart,
                                DagSmem &sm) {
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x;
     double *S = sm.sA;
     if (tid == 0) {
         sm.bad = 0;
@@ -430,10 +430,12 @@ static __device__ void potrf_inv_tile(const DagProb &P, int j, double *G, double
         }
         __syncthreads();
         if (sm.bad) break;
-        for (int c = jj + 1 + warp; c < DB; c += 8) {
-            const double l = sm.lj[c];
-            double *sc = S + c * DLD;
-            for (int r = c + lane; r < DB; r += 32) sc[r] = fma(-cj[r], l, sc[r]);
+        // the trailing triangle flattened over all threads (every lane busy)
+        const int ntri = (DB - 1 - jj) * (DB - jj) / 2;
+        for (int e = tid; e < ntri; e += DAG_THREADS) {
+            int r, c;
+            tri_desc_entry(e, DB, r, c);
+            S[c * DLD + r] = fma(-cj[r], sm.lj[c], S[c * DLD + r]);
         }
         __syncthreads();
     }
@@ -471,8 +473,10 @@ static __device__ void potrf_inv_tile(const DagProb &P, int j, double *G, double
     }
     __syncthreads();
     for (int l = DB - 1; l > 0; --l) {
-        for (int e = tid; e < l * DB; e += DAG_THREADS) {
-            const int c = e >> 6, r = e & (DB - 1);
+        // column l of Y is zero above row l: rows l.. only (exact zeros skipped)
+        const int nr = DB - l;
+        for (int e = tid; e < l * nr; e += DAG_THREADS) {
+            const int c = e / nr, r = l + (e - c * nr);
             sm.sB[c * DLD + r] = fma(-sm.sB[l * DLD + r], S[c * DLD + l], sm.sB[c * DLD + r]);
         }
         __syncthreads();

@@ -24,6 +24,19 @@ __device__ __forceinline__ bool failed(const int64_t *info) {
     return *reinterpret_cast<const volatile int64_t *>(info) != 0;
 }
 
+// Entry e of the lower triangle {(r, c): c <= r < n} of an n x n tile with the
+// columns in DESCENDING order (column n-1 first, rows ascending within a
+// column): the trailing triangle of elimination step j is then the prefix
+// e < (n-1-j)(n-j)/2.  For e below 2^20 (the float square root is exact
+// enough, and the two guards fix its last unit).
+__device__ __forceinline__ void tri_desc_entry(int e, int n, int &r, int &c) {
+    int t = static_cast<int>((sqrtf(8.0f * static_cast<float>(e) + 1.0f) - 1.0f) * 0.5f);
+    if ((t + 1) * (t + 2) / 2 <= e) ++t;
+    if (t * (t + 1) / 2 > e) --t;
+    c = n - 1 - t;
+    r = c + (e - t * (t + 1) / 2);
+}
+
 // Map a linear index over the lower-triangular tile grid to (ti, tj), ti >= tj.
 __device__ __forceinline__ void lower_tile_coords(int64_t t, int64_t &ti, int64_t &tj) {
     int64_t i = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);

@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(256) potrf_tile_kernel(double *A, int64_t ld, 
     __shared__ double dinv[TB];
     __shared__ int bad;
     if (failed(info)) return;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x;
     for (int e = tid; e < TB * TB; e += blockDim.x) {
         int r = e & (TB - 1), c = e >> 6;
         S[c * (TB + 1) + r] = (r >= c) ? A[r + (int64_t)c * ld] : 0.0;
@@ -59,12 +59,15 @@ __global__ void __launch_bounds__(256) potrf_tile_kernel(double *A, int64_t ld, 
         }
         __syncthreads();
         if (bad) break;  // uniform
-        // a_rc -= a_rj a_cj / d_j on the trailing lower triangle j < c <= r:
-        // a warp per column, lanes down the rows (one FMA per entry)
-        for (int c = j + 1 + warp; c < TB; c += 8) {
-            const double l = lj[c];
-            double *sc = S + c * (TB + 1);
-            for (int r = c + lane; r < TB; r += 32) sc[r] = fma(-cj[r], l, sc[r]);
+        // a_rc -= a_rj a_cj / d_j on the trailing lower triangle j < c <= r,
+        // flattened over all threads (every lane busy: on this FP64 pipe a
+        // warp instruction costs the same with few lanes active), one FMA per
+        // entry
+        const int ntri = (TB - 1 - j) * (TB - j) / 2;
+        for (int e = tid; e < ntri; e += blockDim.x) {
+            int r, c;
+            tri_desc_entry(e, TB, r, c);
+            S[c * (TB + 1) + r] = fma(-cj[r], lj[c], S[c * (TB + 1) + r]);
         }
         __syncthreads();
     }
@@ -161,9 +164,11 @@ __global__ void __launch_bounds__(256) trtri_tiles_kernel(const double *L, int64
     __syncthreads();
     // X L = I: column c of X (descending) = (B_c - sum_{l>c} X_l L_lc) / L_cc
     for (int c = TB - 1; c > 0; --c) {
-        for (int e = tid; e < c * TB; e += blockDim.x) {
-            int c2 = e / TB;
-            int r = e & (TB - 1);
+        // column c of B is zero above row c: rows c.. only (exact zeros skipped)
+        const int nr = TB - c;
+        for (int e = tid; e < c * nr; e += blockDim.x) {
+            const int c2 = e / nr;
+            const int r = c + (e - c2 * nr);
             Bs[c2 * (TB + 1) + r] -= Bs[c * (TB + 1) + r] * Ls[c2 * (TB + 1) + c];
         }
         __syncthreads();

@@ -57,8 +57,10 @@ __device__ void diag_inverse(double *Ld, double *Wd, double *rinv) {
     }
     __syncthreads();
     for (int l = PB - 1; l > 0; --l) {
-        for (int e = tid; e < l * PB; e += blockDim.x) {
-            const int c = e >> 6, r = e & (PB - 1);
+        // column l of Y is zero above row l: rows l.. only (exact zeros skipped)
+        const int nr = PB - l;
+        for (int e = tid; e < l * nr; e += blockDim.x) {
+            const int c = e / nr, r = l + (e - c * nr);
             Wd[c * (PB + 1) + r] = fma(-Wd[l * (PB + 1) + r], Ld[c * (PB + 1) + l], Wd[c * (PB + 1) + r]);
         }
         __syncthreads();
