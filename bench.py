@@ -71,6 +71,31 @@ def dist_env():
     return rank, world, local
 
 
+def lpt_partition(sizes, world, rank):
+    """Problems of rank `rank` when independent problems of the given sizes are
+    shared over `world` ranks: longest-processing-time first (cost ~ n^3), each
+    to the least-loaded rank; returns the problem indices in ascending order."""
+    order = sorted(range(len(sizes)), key=lambda i: (-sizes[i], i))
+    loads = [0.0] * world
+    mine = []
+    for i in order:
+        k = min(range(world), key=lambda r: (loads[r], r))
+        loads[k] += float(sizes[i]) ** 3
+        if k == rank:
+            mine.append(i)
+    return sorted(mine)
+
+
+def max_over_ranks(value, dist, device):
+    """The largest of every rank's value (the slowest rank's time); the value
+    itself without a process group."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def workload_config(n, precision):
     return {
         "workload": f"GP loglik+grad, Matern 3/2, n={n}, 2-D clustered locations "
@@ -320,10 +345,7 @@ def run_ours(args, rank, world, local):
     gp.gp_prof_enable(False)
     if int(info.item()) != 0:
         raise RuntimeError(f"timed steps failed, info={int(info.item())}")
-    t_max = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    elapsed_ms = float(t_max.item())
+    elapsed_ms = max_over_ranks(elapsed_ms, dist if dist else None, "cuda")
     value = world * args.steps / (elapsed_ms / 1e3)
     res = out.cpu().numpy()
     g_res = grad.cpu().numpy()
@@ -352,10 +374,8 @@ def run_ours(args, rank, world, local):
         f1.record(stream)
         torch.cuda.synchronize()
         e2e_ms = f0.elapsed_time(f1)
-        tm = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-        if dist:
-            dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * args.steps / (float(tm.item()) / 1e3), "unit": UNIT,
+        e2e_ms = max_over_ranks(e2e_ms, dist if dist else None, "cuda")
+        e2e = {"value": world * args.steps / (e2e_ms / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(x_h.numel() * 8 + y_h.numel() * 8),
                "d2h_bytes_per_step": int((out_h.numel() + grad_h.numel()) * 8)}
 
@@ -483,15 +503,7 @@ def run_batched(args, rank, world, local):
         dist.init_process_group("nccl")
     probs = inputs.config5(nprob=args.nprob)
     # longest-processing-time partition of the problems over ranks
-    order = sorted(range(len(probs)), key=lambda i: -probs[i].n)
-    loads = [0.0] * world
-    mine = []
-    for i in order:
-        k = min(range(world), key=lambda r: loads[r])
-        loads[k] += float(probs[i].n) ** 3
-        if k == rank:
-            mine.append(i)
-    mine.sort()
+    mine = lpt_partition([p.n for p in probs], world, rank)
     sel = [probs[i] for i in mine]
     xs = [torch.as_tensor(p.x, device="cuda") for p in sel]
     zs = [torch.as_tensor(p.z, device="cuda") for p in sel]
@@ -534,11 +546,7 @@ def run_batched(args, rank, world, local):
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    tm = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-    ms = float(tm.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     bad = int((info != 0).sum().item())
     rres = out[:, 3].double().cpu().numpy()
     flops = sum(float(p.n) ** 3 for p in probs)
