@@ -446,6 +446,394 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 }
 
 
+// ---------------------------------------------------------------------------
+// Three-slice (mixed form) kernel: one TMEM accumulator per product group
+// d = p + q (hi: d = 0, d1, d2), two MMA issuers, epilogue through registers.
+//
+// A stage carries every slice of both operands for one 64-deep K block (two
+// 3-D boxes of 3 x 128 x 64 FP16, 96 KB), so each fetched byte feeds all the
+// products that use it (4 KB of operands per 128 x 128 x 16 instruction
+// instead of 8 KB).  Issuer A (warp 1) forms (0,0) into hi and (0,1), (1,0)
+// into d1; issuer B (warp 2) forms (0,2), (1,1), (2,0) into d2: three
+// instructions per stage and k-step each, issued concurrently (one issuing
+// thread sustains about one instruction per 150 cycles, two together about
+// one per 88).  TMEM: hi [0, 128), d1 [128, 256), d2 [256, 384); columns
+// [384, 512) hold the epilogue's staged high parts.
+//
+// Epilogue (warps 3-10, 32 rows x 64 columns each): as soon as a unit's
+// accumulators are complete it reads hi and d1, adds them error-free into a
+// double-float pair (h, l) per entry, writes h to the staging columns, keeps
+// l in registers and frees hi and d1 for issuer A; then it adds d2 into l
+// and frees d2 for issuer B.  The read-modify-write of
+// the outputs then runs while the next unit's instructions execute; its old
+// values are prefetched into L2 while the unit's own instructions execute.
+// ---------------------------------------------------------------------------
+constexpr int T3_STAGES = 2;
+constexpr int T3_SLICE = TC_BM * TC_BK * 2;  // 16 KB: one slice of one operand
+constexpr int T3_OPER = 3 * T3_SLICE;        // 48 KB: every slice of one operand
+constexpr int T3_STAGE = 2 * T3_OPER;        // 96 KB
+constexpr int T3_SMEM = T3_STAGES * T3_STAGE + 1024 /*barriers*/ + 1024 /*align*/;
+#ifndef T3_EPI_WARPS
+#define T3_EPI_WARPS 8
+#endif
+constexpr int T3_EPI = T3_EPI_WARPS;           // epilogue warps (4: one per TMEM lane quarter)
+constexpr int T3_THREADS = 32 * (3 + T3_EPI);  // producer, two issuers, epilogue
+constexpr int T3_COLS = TC_BN * 4 / T3_EPI;    // columns per epilogue warp
+constexpr int T3_NEB = T3_COLS / 32;           // B-row exponents per lane
+constexpr int T3_EG = 4;                       // columns per output step
+constexpr int T3_INFL = 4;                     // output steps with old values in flight
+
+// Previous output values of T3_EG consecutive columns of this thread's row:
+// p points at column cl of the row (8-byte entries, stride ld8 bytes), lim is
+// the row's first column (local) that is not written; masked entries read 0.
+__device__ __forceinline__ void t3_fetch(const char *p, int64_t ld8, int cl, int lim,
+                                         unsigned long long (&o)[T3_EG]) {
+#pragma unroll
+    for (int j = 0; j < T3_EG; ++j)
+        o[j] = cl + j < lim ? *reinterpret_cast<const unsigned long long *>(p + j * ld8) : 0ull;
+}
+
+// One output step: columns cl + j of this thread's row from the pairs
+// (h[j], l[j]) (the unit's unscaled sums), old values in old[].  The sums
+// carry the factor alpha 2^{e_a + e_b - 14}: fa = alpha 2^{e_a} is this
+// row's, e_b of column cl + j sits in lane lane0 + j of ebr.  Row exponents
+// lie in [-100, 120] (the packing clamps them), so fa and 2^{e_b - 14} are
+// normal and their product is exact wherever the scaled result is
+// representable (a power of two down to 2^-149).
+__device__ __forceinline__ void t3_store(const TcGemmArgs &args, const float *h_, const float *l_,
+                                         char *p, int64_t ld8, int cl, int lim, float fa, int ea,
+                                         int ebr, int lane0, const unsigned long long (&old)[T3_EG]) {
+#pragma unroll
+    for (int j = 0; j < T3_EG; ++j) {
+        const int eb = __shfl_sync(0xffffffffu, ebr, lane0 + j);
+        if (args.out_mode == 2) {
+            const float f = __fmul_rn(fa, __int_as_float((eb + 113) << 23));
+            const float ox = __uint_as_float(static_cast<uint32_t>(old[j]));
+            const float oy = __uint_as_float(static_cast<uint32_t>(old[j] >> 32));
+            const float h = __fmul_rn(h_[j], f), l = __fmul_rn(l_[j], f);
+            float s1, e1, hi, lo;
+            two_sum(ox, h, s1, e1);
+            e1 = __fadd_rn(e1, __fadd_rn(oy, l));
+            two_sum(s1, e1, hi, lo);
+            if (cl + j < lim) *reinterpret_cast<float2 *>(p + j * ld8) = make_float2(hi, lo);
+        } else {
+            double v = static_cast<double>(h_[j]) + static_cast<double>(l_[j]);
+            v *= __longlong_as_double(static_cast<long long>(ea + eb - 14 + 1023) << 52);  // exact
+            if (args.beta != 0.0)
+                v = fma(args.beta, __longlong_as_double(static_cast<long long>(old[j])),
+                        args.alpha * v);
+            else if (args.alpha != 1.0)
+                v = args.alpha * v;
+            if (cl + j < lim) *reinterpret_cast<double *>(p + j * ld8) = v;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(T3_THREADS, 1)
+    tc_gemm3_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                    TcGemmArgs args) {
+    extern __shared__ uint8_t smem_raw[];
+    if (args.info && failed(args.info)) return;
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                ~static_cast<uintptr_t>(1023));
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + T3_STAGES * T3_STAGE);
+    uint64_t *empty = full + T3_STAGES;  // both issuers' commits
+    uint64_t *fullA = empty + T3_STAGES;  // hi, d1 of a unit complete
+    uint64_t *fullB = fullA + 1;          // d2 complete
+    uint64_t *freeA = fullB + 1;          // hi, d1 read by every epilogue warp
+    uint64_t *freeB = freeA + 1;          // d2 read by every epilogue warp
+    uint64_t *drain = freeB + 1;          // [2] each issuer's last instructions done
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 2);
+    __shared__ volatile int abort_flag;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < T3_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 2);
+        }
+        mbar_init(fullA, 1);
+        mbar_init(fullB, 1);
+        mbar_init(freeA, T3_EPI);
+        mbar_init(freeB, T3_EPI);
+        mbar_init(&drain[0], 1);
+        mbar_init(&drain[1], 1);
+        abort_flag = 0;
+        fence_barrier_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, TC_TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int ntiles = args.tiles_m * args.tiles_n;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer: one stage per K block ----------------
+        uint32_t it = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const TileInfo ti = tile_at(args, t);
+            if (ti.skip) continue;
+            const int ra = ti.tm * TC_BM + args.a_row_off, rb = ti.tn * TC_BN + args.b_row_off;
+            const int nch = tile_chunks(args, ti.kb_lo, ti.kb_hi);
+            for (int c = 0; c < nch && ok; ++c) {
+                int clo, chi;
+                chunk_range(args, ti.kb_lo, ti.kb_hi, c, clo, chi);
+                for (int kb = clo; kb < chi; ++kb, ++it) {
+                    const uint32_t s = it % T3_STAGES, use = it / T3_STAGES;
+                    if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    if (abort_flag) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *st = smem + s * T3_STAGE;
+                    mbar_arrive_expect_tx(&full[s], T3_STAGE);
+                    const int kx = kb * TC_BK;
+                    tma_load_3d(st, &tmA, &full[s], args.a_k_off + kx, ra, 0);
+                    tma_load_3d(st + T3_OPER, &tmB, &full[s], args.b_k_off + kx, rb, 0);
+                }
+            }
+        }
+        if (!ok) abort_flag = 1;
+        for (uint32_t j = (it > T3_STAGES ? it - T3_STAGES : 0); j < it; ++j)
+            mbar_wait(&full[j % T3_STAGES], (j / T3_STAGES) & 1);
+    } else if ((warp == 1 || warp == 2) && lane == 0) {
+        // ---------------- MMA issuers ----------------
+        const bool isB = warp == 2;
+        const uint32_t idesc = args.idesc;
+        uint32_t it = 0, local = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const TileInfo ti = tile_at(args, t);
+            if (ti.skip) continue;
+            const int nch = tile_chunks(args, ti.kb_lo, ti.kb_hi);
+            for (int c = 0; c < nch && ok; ++c) {
+                int clo, chi;
+                chunk_range(args, ti.kb_lo, ti.kb_hi, c, clo, chi);
+                if (local > 0 && !mbar_wait(isB ? freeB : freeA, (local - 1) & 1)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t acc0 = isB ? tmem + 2 * TC_BN : tmem;
+                const uint32_t acc1 = isB ? acc0 : tmem + TC_BN;
+                // the pair that opens acc0: A (0,0) into hi, B (0,2) into d2
+                const int q0 = isB ? 2 : 0;
+                for (int kb = clo; kb < chi; ++kb, ++it) {
+                    const uint32_t s = it % T3_STAGES, use = it / T3_STAGES;
+                    if (!mbar_wait(&full[s], use & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a_addr = smem_u32(smem + s * T3_STAGE);
+                    const uint32_t b_addr = a_addr + T3_OPER;
+                    const uint32_t first = kb == clo ? 0u : 1u;
+#pragma unroll
+                    for (int k = 0; k < TC_BK / 16; ++k)
+                        mma_f16_ss(acc0, sdesc_sw128(a_addr + k * 32),
+                                   sdesc_sw128(b_addr + q0 * T3_SLICE + k * 32), idesc,
+                                   k == 0 ? first : 1u);
+                    if (!isB) {
+                        // d1: (0,1) opens it, then (1,0)
+#pragma unroll
+                        for (int k = 0; k < TC_BK / 16; ++k)
+                            mma_f16_ss(acc1, sdesc_sw128(a_addr + k * 32),
+                                       sdesc_sw128(b_addr + T3_SLICE + k * 32), idesc,
+                                       k == 0 ? first : 1u);
+#pragma unroll
+                        for (int k = 0; k < TC_BK / 16; ++k)
+                            mma_f16_ss(acc1, sdesc_sw128(a_addr + 1 * T3_SLICE + k * 32),
+                                       sdesc_sw128(b_addr + 0 * T3_SLICE + k * 32), idesc, 1u);
+                    } else {
+                        // d2: (0,2) opened it above, then (1,1), (2,0)
+#pragma unroll
+                        for (int k = 0; k < TC_BK / 16; ++k)
+                            mma_f16_ss(acc0, sdesc_sw128(a_addr + 1 * T3_SLICE + k * 32),
+                                       sdesc_sw128(b_addr + 1 * T3_SLICE + k * 32), idesc, 1u);
+#pragma unroll
+                        for (int k = 0; k < TC_BK / 16; ++k)
+                            mma_f16_ss(acc0, sdesc_sw128(a_addr + 2 * T3_SLICE + k * 32),
+                                       sdesc_sw128(b_addr + 0 * T3_SLICE + k * 32), idesc, 1u);
+                    }
+                    mma_commit(&empty[s]);
+                }
+                if (!ok) break;
+                mma_commit(isB ? fullB : fullA);
+                ++local;
+            }
+        }
+        if (!ok) abort_flag = 1;
+        mma_commit(&drain[isB ? 1 : 0]);
+        mbar_wait(&drain[isB ? 1 : 0], 0);
+    } else if (warp >= 3) {
+        // ---------------- epilogue ----------------
+        const int q = warp & 3;                        // TMEM lane quarter of this warp
+        const int cbeg = ((warp - 3) >> 2) * T3_COLS;  // its columns in the tile
+        uint32_t local = 0;
+        const float alpha_f = static_cast<float>(args.alpha);
+        const bool need_old = args.out_mode == 2 || args.beta != 0.0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            const TileInfo ti = tile_at(args, t);
+            if (ti.skip) continue;
+            const int nch = tile_chunks(args, ti.kb_lo, ti.kb_hi);
+            bool stop = false;
+            const int64_t row = (int64_t)ti.tm * TC_BM + q * 32 + lane;
+            const bool row_ok = row < args.M;
+            const int64_t col0 = (int64_t)ti.tn * TC_BN + cbeg;
+            for (int c = 0; c < nch; ++c) {
+                int clo, chi;
+                chunk_range(args, ti.kb_lo, ti.kb_hi, c, clo, chi);
+                const bool has_acc = clo < chi;
+                // this thread's row: its entries at p_row + cl * ld8 (local
+                // column cl), written while cl < lim
+                int lim = 0;
+                if (row_ok) {
+                    int64_t e = args.N;
+                    if (args.lower && row + args.diag_off + 1 < e) e = row + args.diag_off + 1;
+                    e -= col0;
+                    lim = e <= 0 ? 0 : (e >= T3_COLS ? T3_COLS : (int)e);
+                }
+                const int64_t ld8 = args.ldc * 8;
+                char *p_row = static_cast<char *>(args.C) + (row_ok ? (row + col0 * args.ldc) * 8 : 0);
+                // old values of this row into L2 while the unit's instructions
+                // run (one line request per column and lane pair)
+                if (need_old)
+                    for (int j = 0; j < lim; ++j)
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(p_row + j * ld8));
+                // row exponents of this unit's 512-deep chunk: this thread's A
+                // row, and the B rows of columns col0 + 32 m + lane
+                // (unscaled sums: ea = 0, eb = 14)
+                int ea = 0, eb[T3_NEB];
+#pragma unroll
+                for (int m = 0; m < T3_NEB; ++m) eb[m] = 14;
+                if (args.ex_b && has_acc) {
+                    const int64_t cha = (args.a_k_off + (int64_t)clo * TC_BK) / TC_CHUNK_K;
+                    const int64_t chb = (args.b_k_off + (int64_t)clo * TC_BK) / TC_CHUNK_K;
+                    if (row_ok) ea = args.ex_a[(args.a_row_off + row) * args.ex_ld_a + cha];
+#pragma unroll
+                    for (int m = 0; m < T3_NEB; ++m) {
+                        const int64_t cm = col0 + 32 * m + lane;
+                        if (cm < args.N) eb[m] = args.ex_b[(args.b_row_off + cm) * args.ex_ld_b + chb];
+                    }
+                }
+                const int flim = need_old ? lim : 0;  // columns whose old values are read
+                const float fa = __fmul_rn(alpha_f, __int_as_float((ea + 127) << 23));
+                // a ring of T3_INFL output steps of old values; the first ones
+                // are in flight during the wait
+                unsigned long long old[T3_INFL][T3_EG];
+#pragma unroll
+                for (int g = 0; g < T3_INFL - 1; ++g)
+                    t3_fetch(p_row + g * T3_EG * ld8, ld8, g * T3_EG, flim, old[g]);
+                bool ok = mbar_wait(fullB, local & 1) && mbar_wait(fullA, local & 1);
+                ok = __all_sync(0xffffffffu, ok) && !abort_flag;
+                if (!ok) {
+                    if (lane == 0) abort_flag = 1;
+                    stop = true;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t tl = tmem + (static_cast<uint32_t>(q * 32) << 16) + cbeg;
+                const uint32_t th = tl + 3 * TC_BN;  // staged high parts
+                float L[T3_COLS];
+                if (has_acc) {
+#pragma unroll
+                    for (int g = 0; g < T3_COLS; g += 16) {
+                        uint32_t a0[16], a1[16];
+                        tmem_ld_32x32b_x16(tl + g, a0);
+                        tmem_ld_32x32b_x16(tl + TC_BN + g, a1);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            float h;
+                            two_sum(__uint_as_float(a0[j]), __uint_as_float(a1[j]), h, L[g + j]);
+                            a0[j] = __float_as_uint(h);
+                        }
+                        // the store reads a0 asynchronously: wait before the
+                        // registers are reused
+                        tmem_st_32x32b_x16(th + g, a0);
+                        tmem_st_wait();
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < T3_COLS; ++j) L[j] = 0.0f;
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(freeA);
+                if (has_acc) {
+#pragma unroll
+                    for (int g = 0; g < T3_COLS; g += 16) {
+                        uint32_t a2[16];
+                        tmem_ld_32x32b_x16(tl + 2 * TC_BN + g, a2);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) L[g + j] = __fadd_rn(L[g + j], __uint_as_float(a2[j]));
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(freeB);
+                // outputs, 16 columns per block: h from the staging columns,
+                // l from L[0..15] (L rotates by 16 per block, so that the loop
+                // stays rolled: unrolled over 128 columns the code outgrows the
+                // instruction cache); step g's old values were requested
+                // T3_INFL - 1 steps earlier
+                static_assert(16 % T3_EG == 0 && (16 / T3_EG) % T3_INFL == 0, "ring");
+                constexpr int NSTEP = T3_COLS / T3_EG;
+#pragma unroll 1
+                for (int blk = 0; blk < T3_COLS / 16; ++blk) {
+                    float H[16];
+                    if (has_acc) {
+                        uint32_t hv[16];
+                        tmem_ld_32x32b_x16(th + blk * 16, hv);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) H[j] = __uint_as_float(hv[j]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) H[j] = 0.0f;
+                    }
+                    int ebr = eb[0];
+#pragma unroll
+                    for (int m = 1; m < T3_NEB; ++m)
+                        if ((blk >> 1) == m) ebr = eb[m];
+#pragma unroll
+                    for (int st = 0; st < 16 / T3_EG; ++st) {
+                        const int g = blk * (16 / T3_EG) + st;
+                        const int gf = g + T3_INFL - 1;
+                        if (gf < NSTEP)
+                            t3_fetch(p_row + gf * T3_EG * ld8, ld8, gf * T3_EG, flim,
+                                     old[(st + T3_INFL - 1) % T3_INFL]);
+                        const int cl = g * T3_EG;
+                        t3_store(args, H + st * T3_EG, L + st * T3_EG, p_row + cl * ld8, ld8, cl,
+                                 lim, fa, ea, ebr, cl & 31, old[st % T3_INFL]);
+                    }
+#pragma unroll
+                    for (int j = 0; j < T3_COLS - 16; ++j) L[j] = L[j + 16];
+                }
+                ++local;
+            }
+            if (stop) break;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (abort_flag && threadIdx.x == 0 && args.info) set_info(args.info, -1);
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, TC_TMEM_COLS);
+    }
+}
+
+
 // C = alpha (hi + lo) + beta C over the written entries of a chunked contraction.
 __global__ void acc2_to_f64_kernel(const float2 *acc, int64_t M, int64_t N, double alpha,
                                    double beta, double *C, int64_t ldc, int lower,
@@ -476,13 +864,15 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-static int make_slice_map(CUtensorMap *map, const TcOperand &op, int box_rows) {
+// 3-D map over a slice store [S][rows][Kld]; one box is box_rows x 64 of
+// box_slices consecutive slices (1, or every slice for the three-slice kernel).
+static int make_slice_map(CUtensorMap *map, const TcOperand &op, int box_rows, int box_slices) {
     auto fn = encode_fn();
     if (!fn) return GP_ERR_CUDA;
     if ((reinterpret_cast<uintptr_t>(op.slices) & 15) || (op.Kld % TC_BK)) return GP_ERR_INVALID;
     cuuint64_t dims[3] = {(cuuint64_t)op.Kld, (cuuint64_t)op.rows, (cuuint64_t)op.S};
     cuuint64_t strides[2] = {(cuuint64_t)op.Kld * 2, (cuuint64_t)(op.rows * op.Kld * 2)};
-    cuuint32_t box[3] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, 1};
+    cuuint32_t box[3] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, (cuuint32_t)box_slices};
     cuuint32_t estr[3] = {1, 1, 1};
     const CUtensorMapDataType dt =
         op.S == 3 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
@@ -522,13 +912,17 @@ int tc_gemm(const TcOperand &A, const TcOperand &B, int64_t M, int64_t N, int64_
         if (cudaFuncSetAttribute(tc_gemm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  TC_SMEM) != cudaSuccess ||
             cudaFuncSetAttribute(tc_gemm_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 TC_SMEM) != cudaSuccess)
+                                 TC_SMEM) != cudaSuccess ||
+            cudaFuncSetAttribute(tc_gemm3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 T3_SMEM) != cudaSuccess)
             return GP_ERR_CUDA;
         attr_set[dev] = true;
     }
+    // three slices: the per-group kernel, whose stages carry every slice
+    const bool three = A.S == 3;
     CUtensorMap ma, mb;
-    GP_TRY(make_slice_map(&ma, A, TC_BM));
-    GP_TRY(make_slice_map(&mb, B, TC_BN));
+    GP_TRY(make_slice_map(&ma, A, TC_BM, three ? 3 : 1));
+    GP_TRY(make_slice_map(&mb, B, TC_BN, three ? 3 : 1));
     TcGemmArgs a{};
     a.C = out.C;
     a.ldc = out.ldc;
@@ -603,7 +997,9 @@ int tc_gemm(const TcOperand &A, const TcOperand &B, int64_t M, int64_t N, int64_
     const int sms = num_sms();
     const int grid = (int)(ntiles < sms ? ntiles : (sms > 0 ? sms : 148));
     const int ev = prof_start(s);
-    if (a.nacc == 4)
+    if (three)
+        tc_gemm3_kernel<<<grid, T3_THREADS, T3_SMEM, s>>>(ma, mb, a);
+    else if (a.nacc == 4)
         tc_gemm_kernel<4><<<grid, TC_THREADS, TC_SMEM, s>>>(ma, mb, a);
     else
         tc_gemm_kernel<2><<<grid, TC_THREADS, TC_SMEM, s>>>(ma, mb, a);
