@@ -1,48 +1,45 @@
 // tc_gemm.cu -- the dense contractions of the blocked Cholesky (Sec. 2.1:
 // "most of the total work is in the matrix multiplications") and of the
 // gradient's inverse, on the sm_103a tensor cores, with FP64 operands
-// carried as BF16 slices.
+// carried as 16-bit slices.
 //
 // Operand splitting (row-scaled).  For operand row r let 2^e_r bound its
-// entries over a 512-deep chunk of K.  Each FP64 entry x becomes BF16 slices
-// whose leading one is s0 = round(x 2^{7-e_r}) 2^{e_r-7}, an integer in
-// [-128, 128] times a per-row power of two (exact in BF16).
-//   Mixed form (three slices): s1 = bf16(x - s0), s2 = bf16(x - s0 - s1), so
-//   x = s0 + s1 + s2 to about 2^-26 of the row's largest entry; the slice
+// entries over a 512-deep chunk of K.
+//   Mixed form (three FP16 slices, "normalized"): with y = x 2^{7-e_r},
+//   s0 = round(y), an integer in [-128, 128]; s1 = fp16(y - s0);
+//   s2 = fp16(y - s0 - s1), so y is carried to about 2^-25.  The slice
 //   products s_p t_q with p + q < 3 are kept (the dropped ones are below
-//   2^-25 of the row maxima).
-//   FP64-grade form (five slices): every slice is an integer q_p in
-//   [-128, 128] times 2^{e_r-7-8p}, carrying x to 2^-40 of the row bound;
-//   the 15 products with p + q < 5 are kept.
-// All products of one group d = p + q are integers times one common power of
-// two for a given output (r, c).  A group's sum is exact in an FP32
-// accumulator, however the tensor core rounds, while it stays below 2^24
-// units: for K <= 1024 in group 0, K <= 512 in group 1, and K <= 341 (in
-// practice 512) in group 2.  Exact groups get their own TMEM accumulators:
-// the mixed form has "hi" (group 0) and "lo" (groups 1, 2, rounding 2^-8
-// smaller); the FP64-grade form has groups 0, 1, 2 and a fourth accumulator
-// for groups 3 and 4 (rounding 2^-24 smaller).  The epilogue adds them in
-// FP64 or in double-float.
+//   2^-28 of the row maxima); the epilogue scales each chunk's sums by
+//   2^{e_a + e_b - 14}.
+//   FP64-grade form (five BF16 slices, "scaled"): every slice is an integer
+//   q_p in [-128, 128] times 2^{e_r-7-8p}, carrying x to 2^-40 of the row
+//   bound; the 15 products with p + q < 5 are kept.
+// The products of one group d = p + q share their scale for a given output
+// (r, c); group 0 (integer products) is exact in an FP32 accumulator for
+// K <= 1024, and in the integer form groups 1 and 2 are too for K <= 512.
+// Groups get their own TMEM accumulators: the mixed form one per group (hi,
+// d1, d2), the FP64-grade form groups 0, 1, 2 and a fourth for groups 3 and
+// 4.  The epilogue adds them in FP64 or in double-float.
 //
-// Kernel.  Persistent: one CTA per SM walks a static tile schedule of
-// 128 x 128 output tiles (grouped 16 tile-rows at a time so the operand
-// tiles in flight stay in L2).  10 warps:
-//   warp 0     TMA producer (one thread): a 6-stage ring of 32 KB stages
-//              (A and B 128 x 64 BF16 boxes, 128-byte swizzle).
-//   warp 1     TMEM owner (512 columns: 2 tile buffers x {hi, lo}, or one
-//              buffer x 4 groups) and MMA issuer (one thread):
-//              tcgen05.mma.cta_group::1.kind::f16, 128 x 128 x 16 per
-//              instruction; tcgen05.commit frees stages and hands finished
-//              accumulators to the epilogue.
-//   warps 2-9  epilogue, two warps per TMEM lane quarter (32 rows x 64
-//              columns each): tcgen05.ld of the accumulators, output in FP64
-//              (C = beta C + alpha acc) or as a double-float FP32 pair (C +=
-//              alpha acc, error-free sums), one row per thread so that every
-//              warp access covers 32 consecutive rows of one column.  The
-//              previous output values are read one 8-column step ahead (the
-//              first step before the accumulators are ready), so two steps of
-//              loads are in flight per thread.  Two TMEM buffers let the
-//              epilogue of one tile overlap the MMAs of the next.
+// Two kernels, both persistent (one CTA per SM walks a static tile schedule
+// of 128 x 128 output tiles, grouped 16 tile-rows at a time so the operand
+// tiles in flight stay in L2):
+//   tc_gemm_kernel<NACC> (five slices): 10 warps.
+//     warp 0     TMA producer (one thread): a 6-stage ring of 32 KB stages
+//                (one slice pair: A and B 128 x 64 boxes, 128-byte swizzle).
+//     warp 1     TMEM owner (512 columns: 2 tile buffers x 2 accumulators, or
+//                one buffer x 4) and MMA issuer (one thread):
+//                tcgen05.mma.cta_group::1.kind::f16, 128 x 128 x 16 per
+//                instruction; tcgen05.commit frees stages and hands finished
+//                accumulators to the epilogue.
+//     warps 2-9  epilogue, two warps per TMEM lane quarter (32 rows x 64
+//                columns each): tcgen05.ld of the accumulators, output in
+//                FP64 (C = beta C + alpha acc) or as a double-float FP32 pair
+//                (C += alpha acc, error-free sums), one row per thread so that
+//                every warp access covers 32 consecutive rows of one column.
+//                The previous output values are read one 8-column step ahead.
+//   tc_gemm3_kernel (three slices): stages that carry every slice, two MMA
+//   issuers and an epilogue staged through registers (described with it).
 // Every mbarrier wait is bounded (1 s); a wait that gives up sets
 // *info = -1, the roles wind down (the producer waits, bounded, for its
 // copies in flight) and TMEM is freed.
@@ -573,6 +570,9 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
 
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer: one stage per K block ----------------
+        // operand slices are re-read by other tiles: kept in L2 in preference
+        // to the outputs, which each unit reads and writes once
+        const uint64_t pol_in = l2_policy_evict_last();
         uint32_t it = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
@@ -596,8 +596,8 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                     uint8_t *st = smem + s * T3_STAGE;
                     mbar_arrive_expect_tx(&full[s], T3_STAGE);
                     const int kx = kb * TC_BK;
-                    tma_load_3d(st, &tmA, &full[s], args.a_k_off + kx, ra, 0);
-                    tma_load_3d(st + T3_OPER, &tmB, &full[s], args.b_k_off + kx, rb, 0);
+                    tma_load_3d_hint(st, &tmA, &full[s], args.a_k_off + kx, ra, 0, pol_in);
+                    tma_load_3d_hint(st + T3_OPER, &tmB, &full[s], args.b_k_off + kx, rb, 0, pol_in);
                 }
             }
         }
