@@ -94,7 +94,7 @@ int chol_mixed(double *A, int64_t ld, int64_t np, int S, void *ws, double *winv,
             prof_stop(ev, s, GP_PROF_FOLD, 0.0, 16.0 * (double)rows * nb);
         }
         int ev = prof_start(s);
-        GP_TRY(chol_fp64_tiled(Akk, ld, nb, k0, info, s));
+        GP_TRY(chol_fp64_tiled(Akk, ld, nb, k0, info, s, S == 3));
         prof_stop(ev, s, GP_PROF_DIAG, (double)nb * nb * nb / 3.0, 0.0);
         const int64_t m = np - k0 - nb;
         if (m <= 0 && !winv) break;

@@ -3,7 +3,8 @@
 // update the trailing blocks by multiply-and-subtract; repeat per block
 // column).
 //
-//   potrf_tile   Cholesky of one 64 x 64 diagonal tile in shared memory.
+//   potrf_tile   Cholesky of one 64 x 64 diagonal tile in shared memory,
+//                blocked by 8 columns.
 //   trsm_tiles   panel solve  B <- B L_kk^{-T}  for the tiles below it.
 //   trtri_tiles  inverse of each 64 x 64 diagonal tile of a lower block.
 //   gemm_f64     C = alpha op(A) op(B) + beta C, 64 x 64 register-tiled.
@@ -12,62 +13,84 @@
 // kernels are bounded by the FP64 pipe, not by memory: a 4 x 4 register tile
 // per thread keeps shared-memory traffic far below the DFMA issue rate.
 #include "internal.h"
+#include "kern_df.cuh"
 
 namespace gp {
 
 // ---------------------------------------------------------------------------
-// Cholesky of the 64 x 64 tile at A (column-major, ld), right-looking in
-// shared memory on the unscaled columns: step j subtracts a_rj a_cj / d_j
-// from the trailing lower triangle (d_j the current pivot), and the columns
-// are scaled by 1/sqrt(d_j) once at the end (L_rj = a_rj / sqrt(d_j)).  Each
-// step costs one reciprocal, two barriers and one FMA per trailing lower
-// entry (a warp per column: the FP64 pipe of one SM, about two FMAs per
-// clock, is what bounds this kernel).  col_base is the global column of the
-// tile's first column (for the d_info convention).  A pivot <= 0 or NaN
-// stops the factorisation.
+// Cholesky of the 64 x 64 tile at A (column-major, ld) in shared memory, on
+// the unscaled columns: a_rc -= a_rj a_cj / d_j (d_j the current pivot),
+// the columns scaled by 1/sqrt(d_j) once at the end (L_rj = a_rj /
+// sqrt(d_j)).  Blocked by PB columns: one warp factors a panel of PB columns
+// (all rows below them; only warp synchronisation between its columns),
+// then every thread applies the panel's PB updates to its entries of the
+// trailing lower triangle (PB FMAs per index computation).  Two block
+// barriers per panel instead of two per column: on this part the per-column
+// barriers and dependency latencies, not the FP64 pipe, bounded the
+// column-at-a-time form (66 us per tile against about 20 us of FP64 work).
+// col_base is the global column of the tile's first column (for the d_info
+// convention).  A pivot <= 0 or NaN stops the factorisation.
 // ---------------------------------------------------------------------------
+constexpr int PB = 8;
+
 __global__ void __launch_bounds__(256) potrf_tile_kernel(double *A, int64_t ld, int64_t col_base,
                                                          int64_t *info) {
     __shared__ double S[TB * (TB + 1)];
-    __shared__ double lj[TB];    // a_cj / d_j of the current step
+    __shared__ double lj[PB][TB];  // a_cj / d_j: panel column j, trailing column c
     __shared__ double dinv[TB];
     __shared__ int bad;
     if (failed(info)) return;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int e = tid; e < TB * TB; e += blockDim.x) {
         int r = e & (TB - 1), c = e >> 6;
         S[c * (TB + 1) + r] = (r >= c) ? A[r + (int64_t)c * ld] : 0.0;
     }
     if (tid == 0) bad = 0;
     __syncthreads();
-    for (int j = 0; j < TB; ++j) {
-        const double *cj = S + j * (TB + 1);
-        if (tid < TB) {
-            // every thread of the first two warps forms 1/d_j (one division's
-            // latency on the serial chain) and its own multiplier
-            const double d = cj[j];
-            if (!(d > 0.0)) {
-                if (tid == 0) {
-                    bad = 1;
-                    set_info(info, col_base + j + 1);
+    for (int p = 0; p < TB; p += PB) {
+        if (warp == 0) {
+            // panel columns p .. p + PB - 1 (rows c .. 63 of each column c)
+            for (int j = p; j < p + PB; ++j) {
+                const double *cj = S + j * (TB + 1);
+                const double d = cj[j];
+                if (!(d > 0.0)) {  // every lane read the same pivot
+                    if (lane == 0) {
+                        bad = 1;
+                        set_info(info, col_base + j + 1);
+                    }
+                    break;
                 }
-            } else {
                 const double inv = 1.0 / d;
-                if (tid == 0) dinv[j] = inv;
-                if (tid > j) lj[tid] = cj[tid] * inv;
+                if (lane == 0) dinv[j] = inv;
+                for (int c = j + 1; c < p + PB; ++c) {
+                    const double l = cj[c] * inv;
+                    double *cc = S + c * (TB + 1);
+                    for (int r = c + lane; r < TB; r += 32) cc[r] = fma(-cj[r], l, cc[r]);
+                }
+                __syncwarp();
             }
         }
         __syncthreads();
         if (bad) break;  // uniform
-        // a_rc -= a_rj a_cj / d_j on the trailing lower triangle j < c <= r,
-        // flattened over all threads (every lane busy: on this FP64 pipe a
-        // warp instruction costs the same with few lanes active), one FMA per
-        // entry
-        const int ntri = (TB - 1 - j) * (TB - j) / 2;
+        const int q = p + PB;  // first trailing column
+        if (q >= TB) break;
+        const int nt = TB - q;
+        for (int e = tid; e < PB * nt; e += blockDim.x) {
+            const int jj = e / nt, c = q + e % nt;
+            lj[jj][c] = S[(p + jj) * (TB + 1) + c] * dinv[p + jj];
+        }
+        __syncthreads();
+        // trailing lower triangle q <= c <= r < 64
+        const int ntri = nt * (nt + 1) / 2;
         for (int e = tid; e < ntri; e += blockDim.x) {
             int r, c;
-            tri_desc_entry(e, TB, r, c);
-            S[c * (TB + 1) + r] = fma(-cj[r], lj[c], S[c * (TB + 1) + r]);
+            tri_desc_entry(e, nt, r, c);
+            r += q;
+            c += q;
+            double acc = S[c * (TB + 1) + r];
+#pragma unroll
+            for (int jj = 0; jj < PB; ++jj) acc = fma(-S[(p + jj) * (TB + 1) + r], lj[jj][c], acc);
+            S[c * (TB + 1) + r] = acc;
         }
         __syncthreads();
     }
@@ -82,12 +105,136 @@ __global__ void __launch_bounds__(256) potrf_tile_kernel(double *A, int64_t ld, 
 }
 
 // ---------------------------------------------------------------------------
-// B <- B L^{-T} for the rows below the diagonal tile L (the panel
-// forward-solve of Sec. 2.1).  Each CTA solves 32 rows (rows r0 = 32 blockIdx
-// of B0) against the whole 64 x 64 triangle; the pivots' reciprocals are
-// formed once.
+// The same blocked factorisation in double-float arithmetic (pairs of FP32
+// numbers, about 48 significant bits) on the FP32 pipe, for the diagonal
+// blocks of the tensor-core forms, whose inputs (the FP64 matrix plus the
+// double-float pending updates) carry no more.  On this part a dependent
+// FP64 FMA takes about 47 cycles and an FP64 division about 540, against
+// about 4 for an FP32 operation, and the column chain of the factorisation
+// (pivot reciprocal, multipliers, update, next pivot) is latency bound.  The
+// tile is converted from FP64 by integer operations and written back in FP64.
 // ---------------------------------------------------------------------------
-constexpr int TR_ROWS = 32;
+// One PB-column panel of potrf_tile_df_kernel, on one warp, in registers:
+// the lane owns rows lane and lane + 32 of the panel's columns; pivots and
+// multipliers travel by shuffles (entries above a column's diagonal are
+// updated too, and never read).  The panel's own rows lie in row slot SLOT.
+template <int SLOT>
+__device__ __forceinline__ void df_panel(dfl *S, dfl *dinv, int *bad, int p, int lane,
+                                         int64_t col_base, int64_t *info) {
+    float vh[2][PB], vl[2][PB];  // the pairs' high and low parts, kept apart (registers)
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int jj = 0; jj < PB; ++jj) {
+            const dfl x = S[(p + jj) * (TB + 1) + lane + 32 * i];
+            vh[i][jj] = x.h;
+            vl[i][jj] = x.l;
+        }
+    bool ok = true;
+#pragma unroll
+    for (int jj = 0; jj < PB; ++jj) {
+        const int j = p + jj;
+        const dfl d{__shfl_sync(0xffffffffu, vh[SLOT][jj], j & 31),
+                    __shfl_sync(0xffffffffu, vl[SLOT][jj], j & 31)};
+        if (ok && !(d.h > 0.0f)) {  // uniform; the first failing pivot is reported
+            if (lane == 0) {
+                *bad = 1;
+                set_info(info, col_base + j + 1);
+            }
+            ok = false;
+        }
+        const dfl inv = df_rcp(d);
+        if (lane == 0) dinv[j] = inv;
+        // a constant trip count (the guard folds once both loops are
+        // unrolled), so that every register index is static
+#pragma unroll
+        for (int cc = 1; cc < PB; ++cc) {
+            if (cc <= jj) continue;
+            const int c = p + cc;
+            const dfl l = df_mul(dfl{__shfl_sync(0xffffffffu, vh[SLOT][jj], c & 31),
+                                     __shfl_sync(0xffffffffu, vl[SLOT][jj], c & 31)},
+                                 inv);
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const dfl r = df_fms(dfl{vh[i][cc], vl[i][cc]}, dfl{vh[i][jj], vl[i][jj]}, l);
+                vh[i][cc] = r.h;
+                vl[i][cc] = r.l;
+            }
+        }
+    }
+    if (ok) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int jj = 0; jj < PB; ++jj)
+                S[(p + jj) * (TB + 1) + lane + 32 * i] = dfl{vh[i][jj], vl[i][jj]};
+    }
+}
+
+__global__ void __launch_bounds__(256) potrf_tile_df_kernel(double *A, int64_t ld,
+                                                            int64_t col_base, int64_t *info) {
+    __shared__ dfl S[TB * (TB + 1)];
+    __shared__ dfl lj[PB][TB];  // a_cj / d_j: panel column j, trailing column c
+    __shared__ dfl dinv[TB];
+    __shared__ int bad;
+    if (failed(info)) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int e = tid; e < TB * TB; e += blockDim.x) {
+        int r = e & (TB - 1), c = e >> 6;
+        S[c * (TB + 1) + r] =
+            (r >= c) ? f64_to_df(static_cast<unsigned long long>(
+                           __double_as_longlong(A[r + (int64_t)c * ld])))
+                     : dfl{0.0f, 0.0f};
+    }
+    if (tid == 0) bad = 0;
+    __syncthreads();
+    for (int p = 0; p < TB; p += PB) {
+        if (warp == 0) {
+            if (p < 32)
+                df_panel<0>(S, dinv, &bad, p, lane, col_base, info);
+            else
+                df_panel<1>(S, dinv, &bad, p, lane, col_base, info);
+        }
+        __syncthreads();
+        if (bad) break;  // uniform
+        const int q = p + PB;
+        if (q >= TB) break;
+        const int nt = TB - q;
+        for (int e = tid; e < PB * nt; e += blockDim.x) {
+            const int jj = e / nt, c = q + e % nt;
+            lj[jj][c] = df_mul(S[(p + jj) * (TB + 1) + c], dinv[p + jj]);
+        }
+        __syncthreads();
+        const int ntri = nt * (nt + 1) / 2;
+        for (int e = tid; e < ntri; e += blockDim.x) {
+            int r, c;
+            tri_desc_entry(e, nt, r, c);
+            r += q;
+            c += q;
+            dfl acc = S[c * (TB + 1) + r];
+#pragma unroll
+            for (int jj = 0; jj < PB; ++jj) acc = df_fms(acc, S[(p + jj) * (TB + 1) + r], lj[jj][c]);
+            S[c * (TB + 1) + r] = acc;
+        }
+        __syncthreads();
+    }
+    if (bad) return;
+    if (tid < TB) dinv[tid] = df_sqrt(dinv[tid]);
+    __syncthreads();
+    for (int e = tid; e < TB * TB; e += blockDim.x) {
+        int r = e & (TB - 1), c = e >> 6;
+        if (r >= c) A[r + (int64_t)c * ld] = df_to_double(df_mul(S[c * (TB + 1) + r], dinv[c]));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// B <- B L^{-T} for the rows below the diagonal tile L (the panel
+// forward-solve of Sec. 2.1).  Each CTA solves 16 rows (rows r0 = 16 blockIdx
+// of B0) against the whole 64 x 64 triangle (more CTAs for the latency-bound
+// small panels of the diagonal blocks); the pivots' reciprocals are formed
+// once.
+// ---------------------------------------------------------------------------
+constexpr int TR_ROWS = 16;
 
 __global__ void __launch_bounds__(256) trsm_tiles_kernel(const double *L, double *B0, int64_t ld,
                                                          int64_t rows, const int64_t *info) {
@@ -104,7 +251,7 @@ __global__ void __launch_bounds__(256) trsm_tiles_kernel(const double *L, double
         Ls[c * (TB + 1) + r] = (r >= c) ? L[r + (int64_t)c * ld] : 0.0;
     }
     for (int e = tid; e < TB * TR_ROWS; e += blockDim.x) {
-        int r = e & (TR_ROWS - 1), c = e >> 5;
+        int r = e & (TR_ROWS - 1), c = e / TR_ROWS;
         Bs[c * (TR_ROWS + 1) + r] = (r < nr) ? B[r + (int64_t)c * ld] : 0.0;
     }
     __syncthreads();
@@ -128,7 +275,7 @@ __global__ void __launch_bounds__(256) trsm_tiles_kernel(const double *L, double
         __syncthreads();
     }
     for (int e = tid; e < TB * TR_ROWS; e += blockDim.x) {
-        int r = e & (TR_ROWS - 1), c = e >> 5;
+        int r = e & (TR_ROWS - 1), c = e / TR_ROWS;
         if (r < nr) B[r + (int64_t)c * ld] = Bs[c * (TR_ROWS + 1) + r] * rinv[c];
     }
 }
@@ -425,15 +572,19 @@ int gemm_f64(int64_t M, int64_t N, int64_t K, double alpha, const double *A, int
 // ---------------------------------------------------------------------------
 // Right-looking tiled Cholesky in FP64 of the m x m block at A (m a multiple
 // of 64): per tile column k, POTRF of the diagonal tile, TRSM of the tiles
-// below, SYRK/GEMM of the trailing lower triangle (Sec. 2.1).
+// below, SYRK/GEMM of the trailing lower triangle (Sec. 2.1).  df_tiles:
+// the diagonal tiles are factored in double-float (potrf_tile_df_kernel).
 // ---------------------------------------------------------------------------
 int chol_fp64_tiled(double *A, int64_t ld, int64_t m, int64_t col_base, int64_t *info,
-                    cudaStream_t s) {
+                    cudaStream_t s, bool df_tiles) {
     const int64_t T = m / TB;
     for (int64_t k = 0; k < T; ++k) {
         const int64_t k0 = k * TB;
         double *Akk = A + k0 + k0 * ld;
-        potrf_tile_kernel<<<1, 256, 0, s>>>(Akk, ld, col_base + k0, info);
+        if (df_tiles)
+            potrf_tile_df_kernel<<<1, 256, 0, s>>>(Akk, ld, col_base + k0, info);
+        else
+            potrf_tile_kernel<<<1, 256, 0, s>>>(Akk, ld, col_base + k0, info);
         GP_LAUNCH_CHECK();
         const int64_t rest = m - k0 - TB;
         if (rest <= 0) continue;
@@ -441,7 +592,10 @@ int chol_fp64_tiled(double *A, int64_t ld, int64_t m, int64_t col_base, int64_t 
         trsm_tiles_kernel<<<(unsigned)ceil_div(rest, TR_ROWS), 256, 0, s>>>(Akk, P, ld, rest, info);
         GP_LAUNCH_CHECK();
         double *C = P + TB * ld;  // trailing block
-        GP_TRY(gemm_f64(rest, rest, TB, -1.0, P, ld, 0, P, ld, 1, 1.0, C, ld, 1, info, s));
+        // small (latency-bound) updates: K = 64 split in four over the grid
+        // (FP64 atomics into C), four times the CTAs
+        F64Mask split{0, 0, 0, 0, rest <= 512 ? 16 : 0};
+        GP_TRY(gemm_f64_ex(rest, rest, TB, -1.0, P, ld, 0, P, ld, 1, 1.0, C, ld, 1, split, info, s));
     }
     return GP_OK;
 }

@@ -30,7 +30,7 @@ int gemm_f64(int64_t M, int64_t N, int64_t K, double alpha, const double *A, int
              const double *B, int64_t ldb, int opB, double beta, double *C, int64_t ldc, int lower,
              const int64_t *info, cudaStream_t s);
 int chol_fp64_tiled(double *A, int64_t ld, int64_t m, int64_t col_base, int64_t *info,
-                    cudaStream_t s);
+                    cudaStream_t s, bool df_tiles = false);
 int trtri_fp64_blocked(const double *L, int64_t ld_l, int64_t m, double *X, int64_t ld_x,
                        double *tmp, const int64_t *info, cudaStream_t s);
 

@@ -95,6 +95,20 @@ __device__ __forceinline__ dfl df_sqr(dfl a) {
     return df_quick_sum(p.h, p.l);
 }
 
+// 1 / a for a != 0: an FP32 reciprocal refined by one Newton step,
+// y + y (1 - a y), with the residual 1 - a y formed in double-float (the
+// FP32 seed's relative error 2^-23 squares to below the pair's precision).
+__device__ __forceinline__ dfl df_rcp(dfl a) {
+    const float y = __frcp_rn(a.h);
+    dfl p = df_two_prod(a.h, y);  // a.h y exactly
+    p.l = __fmaf_rn(a.l, y, p.l);
+    const dfl e = df_add_f({-p.h, -p.l}, 1.0f);  // 1 - a y
+    return df_add_f(df_mul_f(e, y), y);
+}
+
+// a - b c
+__device__ __forceinline__ dfl df_fms(dfl a, dfl b, dfl c) { return df_add(a, df_neg(df_mul(b, c))); }
+
 // sqrt of a >= 0: an FP32 root refined once against the double-float
 // residual (a - s^2 is exact through the FMA to FP32 precision).
 __device__ __forceinline__ dfl df_sqrt(dfl a) {
