@@ -206,11 +206,11 @@ __global__ void __launch_bounds__(256) split_rows_kernel(SplitArgs a) {
 // The three-slice split with vector memory access (the mixed form's hot
 // case): the same row bounds and slices as split_rows_kernel, one CTA per 32
 // rows x one 512-deep K chunk.  trans = 1 (operand rows contiguous in K):
-// double2 loads along K and 8-byte slice stores.  trans = 0 (operand rows are
-// rows of the column-major source): double2 loads down the columns, the
-// slices transposed through shared memory in 64-column steps and stored
-// 16 bytes per thread.  Requires K % 64 == 0, a 16-byte aligned source and
-// an even ld.
+// split3_vec_kernel, double2 loads along K and 8-byte slice stores.
+// trans = 0 (operand rows are rows of the column-major source):
+// split3_panel_kernel, double2 loads down the columns, the slices transposed
+// through shared memory in 64-column steps and stored 16 bytes per thread.
+// Both require K % 64 == 0, a 16-byte aligned source and an even ld.
 __device__ __forceinline__ unsigned long long split_bits(const SplitArgs &a, int64_t r, int64_t k,
                                                          double v) {
     if (r >= a.R || k >= a.Kvalid) return 0ull;
@@ -236,10 +236,10 @@ __device__ __forceinline__ void split_pair(const SplitArgs &a, int64_t r, int64_
 
 constexpr int SPV_LD = 72;  // shared row stride of the transpose tile (16-byte rows)
 
+// trans = 1 only (trans = 0 is split3_panel_kernel)
 __global__ void __launch_bounds__(256) split3_vec_kernel(SplitArgs a) {
-    __shared__ unsigned long long pm[8][32];
+    __shared__ unsigned long long pm[32];
     __shared__ float sc_s[32];
-    __shared__ __align__(16) uint16_t tile[3][32][SPV_LD];
     constexpr unsigned long long ABS = 0x7FFFFFFFFFFFFFFFull;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t r0 = (int64_t)blockIdx.x * 32;
@@ -247,44 +247,24 @@ __global__ void __launch_bounds__(256) split3_vec_kernel(SplitArgs a) {
     const int64_t ke = min(a.K, kb + SPLIT_KCH);
     const int64_t slice = a.dst_rows * a.dst_kld;
     uint16_t *d0 = a.dst + (a.dst_row_off + r0) * a.dst_kld + a.dst_k_off;
-    if (a.trans) {
-        // warp: rows r0 + warp + 8i; lane: K quads kb + 4 lane + 128 j
-        unsigned long long m[4] = {0ull, 0ull, 0ull, 0ull};
-        for (int i = 0; i < 4; ++i) {
-            const int64_t r = r0 + warp + 8 * i;
-            for (int64_t k = kb + 4 * lane; k < ke; k += 128) {
-                unsigned long long u[4];
-                split_pair(a, r, k, true, u[0], u[1]);
-                split_pair(a, r, k + 2, true, u[2], u[3]);
+    // warp: rows r0 + warp + 8i; lane: K quads kb + 4 lane + 128 j
+    unsigned long long m[4] = {0ull, 0ull, 0ull, 0ull};
+    for (int i = 0; i < 4; ++i) {
+        const int64_t r = r0 + warp + 8 * i;
+        for (int64_t k = kb + 4 * lane; k < ke; k += 128) {
+            unsigned long long u[4];
+            split_pair(a, r, k, true, u[0], u[1]);
+            split_pair(a, r, k + 2, true, u[2], u[3]);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) m[i] = max(m[i], u[q] & ABS);
-            }
+            for (int q = 0; q < 4; ++q) m[i] = max(m[i], u[q] & ABS);
+        }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) m[i] = max(m[i], __shfl_xor_sync(0xffffffffu, m[i], o));
-            if (lane == 0) pm[0][warp + 8 * i] = m[i];
-        }
-    } else {
-        // lane: rows 2 (lane % 16) and + 1, column parity lane / 16; warp: columns 2 warp + 16 i
-        const int rp = 2 * (lane & 15), co = lane >> 4;
-        unsigned long long m0 = 0ull, m1 = 0ull;
-        for (int64_t k = kb + 2 * warp + co; k < ke; k += 16) {
-            unsigned long long u0, u1;
-            split_pair(a, r0 + rp, k, false, u0, u1);
-            m0 = max(m0, u0 & ABS);
-            m1 = max(m1, u1 & ABS);
-        }
-        m0 = max(m0, __shfl_xor_sync(0xffffffffu, m0, 16));
-        m1 = max(m1, __shfl_xor_sync(0xffffffffu, m1, 16));
-        if (lane < 16) {
-            pm[warp][rp] = m0;
-            pm[warp][rp + 1] = m1;
-        }
+        for (int o = 16; o > 0; o >>= 1) m[i] = max(m[i], __shfl_xor_sync(0xffffffffu, m[i], o));
+        if (lane == 0) pm[warp + 8 * i] = m[i];
     }
     __syncthreads();
     if (threadIdx.x < 32) {
-        unsigned long long m = 0ull;
-        const int nw = a.trans ? 1 : 8;
-        for (int w = 0; w < nw; ++w) m = max(m, pm[w][threadIdx.x]);
+        const unsigned long long m = pm[threadIdx.x];
         int e = 0;
         const int E = static_cast<int>(m >> 52);
         if (E > 0) e = E - 1022;
@@ -294,60 +274,115 @@ __global__ void __launch_bounds__(256) split3_vec_kernel(SplitArgs a) {
             a.dst_ex[(a.dst_row_off + r0 + threadIdx.x) * a.ex_ld + (a.dst_k_off + kb) / SPLIT_KCH] = e;
     }
     __syncthreads();
-    if (a.trans) {
-        for (int i = 0; i < 4; ++i) {
-            const int rl = warp + 8 * i;
-            const int64_t r = r0 + rl;
-            if (r >= a.R) continue;
-            const float sc = sc_s[rl];
-            for (int64_t k = kb + 4 * lane; k < ke; k += 128) {
-                unsigned long long u[4];
-                split_pair(a, r, k, true, u[0], u[1]);
-                split_pair(a, r, k + 2, true, u[2], u[3]);
-                uint16_t t[4][3];
+    for (int i = 0; i < 4; ++i) {
+        const int rl = warp + 8 * i;
+        const int64_t r = r0 + rl;
+        if (r >= a.R) continue;
+        const float sc = sc_s[rl];
+        for (int64_t k = kb + 4 * lane; k < ke; k += 128) {
+            unsigned long long u[4];
+            split_pair(a, r, k, true, u[0], u[1]);
+            split_pair(a, r, k + 2, true, u[2], u[3]);
+            uint16_t t[4][3];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    uint16_t s3[3];
-                    split3_norm(u[q], sc, s3);
-                    t[q][0] = s3[0];
-                    t[q][1] = s3[1];
-                    t[q][2] = s3[2];
-                }
+            for (int q = 0; q < 4; ++q) {
+                uint16_t s3[3];
+                split3_norm(u[q], sc, s3);
+                t[q][0] = s3[0];
+                t[q][1] = s3[1];
+                t[q][2] = s3[2];
+            }
 #pragma unroll
-                for (int p = 0; p < 3; ++p) {
-                    uint2 v;
-                    v.x = t[0][p] | ((uint32_t)t[1][p] << 16);
-                    v.y = t[2][p] | ((uint32_t)t[3][p] << 16);
-                    *reinterpret_cast<uint2 *>(d0 + p * slice + (int64_t)rl * a.dst_kld + (k - kb) + kb) = v;
-                }
+            for (int p = 0; p < 3; ++p) {
+                uint2 v;
+                v.x = t[0][p] | ((uint32_t)t[1][p] << 16);
+                v.y = t[2][p] | ((uint32_t)t[3][p] << 16);
+                *reinterpret_cast<uint2 *>(d0 + p * slice + (int64_t)rl * a.dst_kld + (k - kb) + kb) = v;
             }
         }
-    } else {
-        const int rp = 2 * (lane & 15), co = lane >> 4;
-        const float sc0 = sc_s[rp], sc1 = sc_s[rp + 1];
-        for (int64_t c0 = kb; c0 < ke; c0 += 64) {
-            for (int kk = 2 * warp + co; kk < 64; kk += 16) {
-                unsigned long long u0, u1;
-                split_pair(a, r0 + rp, c0 + kk, false, u0, u1);
-                uint16_t s3[3];
-                split3_norm(u0, sc0, s3);
-                tile[0][rp][kk] = s3[0];
-                tile[1][rp][kk] = s3[1];
-                tile[2][rp][kk] = s3[2];
-                split3_norm(u1, sc1, s3);
-                tile[0][rp + 1][kk] = s3[0];
-                tile[1][rp + 1][kk] = s3[1];
-                tile[2][rp + 1][kk] = s3[2];
-            }
-            __syncthreads();
-            const int row = threadIdx.x >> 3, ch = threadIdx.x & 7;
-            if (r0 + row < a.R) {
+    }
+}
+
+// The trans = 0 case in one pass over the source: 512
+// threads keep their 16 entry pairs in registers between the row-bound
+// reduction and the split, where the two-pass form read the panel twice
+// (the second time often from DRAM again) and waited on each 64-column
+// step's loads in turn.  Same bounds, slices and layout.
+constexpr int SPP_THREADS = 512;
+
+__global__ void __launch_bounds__(SPP_THREADS) split3_panel_kernel(SplitArgs a) {
+    __shared__ unsigned long long pm[SPP_THREADS / 32][32];
+    __shared__ float sc_s[32];
+    __shared__ __align__(16) uint16_t tile[2][3][32][SPV_LD];
+    constexpr unsigned long long ABS = 0x7FFFFFFFFFFFFFFFull;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t r0 = (int64_t)blockIdx.x * 32;
+    const int64_t kb = (int64_t)blockIdx.y * SPLIT_KCH;
+    const int64_t ke = min(a.K, kb + SPLIT_KCH);
+    const int64_t slice = a.dst_rows * a.dst_kld;
+    uint16_t *d0 = a.dst + (a.dst_row_off + r0) * a.dst_kld + a.dst_k_off;
+    // lane: rows rp and rp + 1; columns kb + kc + 32 i (i < 16), kc = 2 warp + co
+    const int rp = 2 * (lane & 15), kc = 2 * warp + (lane >> 4);
+    unsigned long long u[16][2];
+    unsigned long long m0 = 0ull, m1 = 0ull;
 #pragma unroll
-                for (int p = 0; p < 3; ++p)
-                    *reinterpret_cast<uint4 *>(d0 + p * slice + (int64_t)row * a.dst_kld + c0 + 8 * ch) =
-                        *reinterpret_cast<const uint4 *>(&tile[p][row][8 * ch]);
-            }
-            __syncthreads();
+    for (int i = 0; i < 16; ++i) {
+        const int64_t k = kb + kc + 32 * i;
+        if (k < ke) {
+            split_pair(a, r0 + rp, k, false, u[i][0], u[i][1]);
+        } else {
+            u[i][0] = u[i][1] = 0ull;
+        }
+        m0 = max(m0, u[i][0] & ABS);
+        m1 = max(m1, u[i][1] & ABS);
+    }
+    m0 = max(m0, __shfl_xor_sync(0xffffffffu, m0, 16));
+    m1 = max(m1, __shfl_xor_sync(0xffffffffu, m1, 16));
+    if (lane < 16) {
+        pm[warp][rp] = m0;
+        pm[warp][rp + 1] = m1;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        unsigned long long m = 0ull;
+        for (int w = 0; w < SPP_THREADS / 32; ++w) m = max(m, pm[w][threadIdx.x]);
+        int e = 0;
+        const int E = static_cast<int>(m >> 52);
+        if (E > 0) e = E - 1022;
+        e = max(-100, min(e, 120));
+        sc_s[threadIdx.x] = ldexpf(1.0f, 7 - e);
+        if (r0 + threadIdx.x < a.R)
+            a.dst_ex[(a.dst_row_off + r0 + threadIdx.x) * a.ex_ld + (a.dst_k_off + kb) / SPLIT_KCH] = e;
+    }
+    __syncthreads();
+    const float sc0 = sc_s[rp], sc1 = sc_s[rp + 1];
+    // 64-column steps: this thread's columns kc and kc + 32 of step c are its
+    // pairs 2c and 2c + 1; the transpose tile is double-buffered (one barrier
+    // per step: a buffer is rewritten only after the barrier that follows its
+    // stores)
+#pragma unroll
+    for (int c = 0; c < SPLIT_KCH / 64; ++c) {
+        if (kb + 64 * c >= ke) break;  // uniform
+        uint16_t(*t)[32][SPV_LD] = tile[c & 1];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int kk = kc + 32 * h;
+            uint16_t s3[3];
+            split3_norm(u[2 * c + h][0], sc0, s3);
+            t[0][rp][kk] = s3[0];
+            t[1][rp][kk] = s3[1];
+            t[2][rp][kk] = s3[2];
+            split3_norm(u[2 * c + h][1], sc1, s3);
+            t[0][rp + 1][kk] = s3[0];
+            t[1][rp + 1][kk] = s3[1];
+            t[2][rp + 1][kk] = s3[2];
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < 3 * 32 * 8; idx += SPP_THREADS) {
+            const int p = idx >> 8, row = (idx >> 3) & 31, ch = idx & 7;
+            if (r0 + row < a.R)
+                *reinterpret_cast<uint4 *>(d0 + p * slice + (int64_t)row * a.dst_kld + kb + 64 * c + 8 * ch) =
+                    *reinterpret_cast<const uint4 *>(&t[p][row][8 * ch]);
         }
     }
 }
@@ -367,7 +402,9 @@ int split_rows(const double *src, int64_t ld, int64_t R, int64_t K, int64_t Kval
     const bool vec = S == 3 && K % 64 == 0 && ld % 2 == 0 &&
                      reinterpret_cast<uintptr_t>(src) % 16 == 0 &&
                      reinterpret_cast<uintptr_t>(dst) % 16 == 0 && dst_kld % 64 == 0;
-    if (vec)
+    if (vec && !trans)
+        split3_panel_kernel<<<g, SPP_THREADS, 0, s>>>(a);
+    else if (vec)
         split3_vec_kernel<<<g, 256, 0, s>>>(a);
     else
         split_rows_kernel<<<g, 256, 0, s>>>(a);
