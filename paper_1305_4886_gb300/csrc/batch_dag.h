@@ -204,7 +204,7 @@ struct DagSmem {
     int badcol;
     int task;
     int pad_;
-    int ok[4];  // verdict of the last wait, spin cycles (as one 64-bit value at ok + 2)
+    int ok[4];  // outcome of the last wait, spin cycles (as one 64-bit value at ok + 2)
 };
 
 // --------------------------------------------------------------------------
@@ -222,8 +222,8 @@ __device__ __forceinline__ int ld_relaxed_gpu(const int *p) {
     return v;
 }
 
-// Wait (thread 0, bounded) until *f >= target; every thread gets the verdict.
-// okslot[0]: the verdict; okslot[2..3]: cycles spent spinning (accumulated
+// Wait (thread 0, bounded) until *f >= target; every thread gets the outcome.
+// okslot[0]: the outcome; okslot[2..3]: cycles spent spinning (accumulated
 // for the optional counters).
 static __device__ bool dag_wait(const int *f, int target, DagHdr *h, int64_t *info, int *okslot) {
     __syncthreads();
