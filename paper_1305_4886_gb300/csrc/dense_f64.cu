@@ -616,14 +616,16 @@ int trtri_fp64_blocked(const double *L, int64_t ld_l, int64_t m, double *X, int6
     for (int64_t i = 1; i < T; ++i) {
         const int64_t i0 = i * TB;
         // tmp (64 x i0) = L[i0:i0+64, 0:i0] * X[0:i0, 0:i0]; X lower, so column
-        // block j needs K >= j only; K split in 64-chunks accumulated atomically
+        // block j needs K >= j only.  Both products are small and latency
+        // bound: K is split in 16-chunks over the grid, accumulated atomically
         if (cudaMemsetAsync(tmp, 0, sizeof(double) * TB * i0, s) != cudaSuccess) return GP_ERR_CUDA;
-        F64Mask split{0, 0, 1, 0, TB};
+        F64Mask split{0, 0, 1, 0, 16};
         GP_TRY(gemm_f64_ex(TB, i0, i0, 1.0, L + i0, ld_l, 0, X, ld_x, 0, 1.0, tmp, TB, 0, split,
                            info, s));
-        // X[i0:i0+64, 0:i0] = -X_ii * tmp
-        GP_TRY(gemm_f64(TB, i0, TB, -1.0, X + i0 + i0 * ld_x, ld_x, 0, tmp, TB, 0, 0.0, X + i0,
-                        ld_x, 0, info, s));
+        // X[i0:i0+64, 0:i0] = -X_ii * tmp, into the zeros set above
+        F64Mask k16{0, 0, 0, 0, 16};
+        GP_TRY(gemm_f64_ex(TB, i0, TB, -1.0, X + i0 + i0 * ld_x, ld_x, 0, tmp, TB, 0, 1.0, X + i0,
+                           ld_x, 0, k16, info, s));
     }
     return GP_OK;
 }
