@@ -68,7 +68,9 @@ typedef enum { GP_KERNEL_EXP = 0, GP_KERNEL_MATERN32 = 1, GP_KERNEL_MATERN52 = 2
 
 /* Arithmetic of the factorisation.
  *   GP_FP64        every step in FP64 on the CUDA cores.
- *   GP_MIXED_F16  the mixed form: FP64 diagonal blocks, pivots,
+ *   GP_MIXED_F16  the mixed form: FP64 diagonal blocks (their 64 x 64
+ *                  diagonal tiles factored in double-float, about 48 bits,
+ *                  the precision of the pending updates), pivots,
  *                  log-determinant and residuals; the off-diagonal panel
  *                  solve, the trailing SYRK updates and the gradient's
  *                  inverse run on the tcgen05 tensor cores over three
@@ -282,8 +284,9 @@ int64_t gp_launch_count(void);
 #define GP_PROF_FILL 1     /* covariance fill; bytes = lower-triangle FP64 */
 #define GP_PROF_RESIDUAL 2 /* matrix-free refinement residual */
 #define GP_PROF_GRAD 3     /* gradient contraction; bytes = lower-triangle FP64 */
-#define GP_PROF_DIAG 4     /* FP64 tiled Cholesky of a diagonal block (or of the
-                              whole matrix in GP_FP64); flops = nb^3/3 */
+#define GP_PROF_DIAG 4     /* tiled Cholesky of a diagonal block (or of the
+                              whole matrix in GP_FP64), FP64 with double-float
+                              diagonal tiles in GP_MIXED_F16; flops = nb^3/3 */
 #define GP_PROF_DIAGINV 5  /* FP64 inverse of a diagonal block; flops = nb^3/3 */
 #define GP_PROF_SOLVE 6    /* triangular solves; bytes = 8 per lower entry read */
 #define GP_PROF_PACK 7     /* FP64 -> 16-bit slice packing */
