@@ -15,13 +15,21 @@ With N > 1 (torchrun, one rank per GPU) every rank evaluates its own
 replica: the single large problem does not shard (replicas only), so the
 whole-job value is N x K evaluations over the slowest rank's time.
 
+After the timed region (unless --no-extras) the same JSON line also carries,
+measured in the same run: the Cholesky factorisation alone in the mixed and
+FP64-grade forms (n^3/3 over its CUDA-event time), the FP64-grade form's
+loglik+grad on the same inputs (its time and the mixed form's error against
+it), and the batched workload (512 problems, one CUDA-graph replay per step)
+in the mixed and FP64 forms.
+
 --impl reference times the FP64 CPU oracle (the plain implementation the
 parity tests use) on the host cores, on a bounded sample of the same
 workload, and prints the same JSON line with "impl": "reference".
+--cpu-plan n1,n2,.. times the oracle at those sizes with all cores and one
+thread, and LAPACK's Cholesky, and prints one JSON line per measurement.
 """
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -54,13 +62,23 @@ def parse():
                     help="batched workload: number of problems (exploration only; 512 is the workload)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-error", action="store_true",
-                    help="skip the untimed comparison with the FP64-grade form")
+                    help="(kept for older command lines; the comparison is part of the extras)")
     ap.add_argument("--accuracy", default=None,
                     help="comma-separated n: print mixed / FP64-grade errors against the "
                          "FP64 path on the config-3 recipe at each n, then exit")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-budget", type=float, default=15.0,
-                    help="seconds of oracle work for the CPU baseline sample")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline run without the Cholesky-only timing, the FP64-grade "
+                         "form and the batched workload")
+    ap.add_argument("--e2e-steps", type=int, default=5,
+                    help="evaluations in the end-to-end (host buffers) measurement")
+    ap.add_argument("--emu-steps", type=int, default=2,
+                    help="timed evaluations of the FP64-grade form")
+    ap.add_argument("--batched-steps", type=int, default=10,
+                    help="timed graph replays of the batched workload")
+    ap.add_argument("--cpu-plan", default=None,
+                    help="comma-separated n: time the oracle (all cores and one thread) "
+                         "and LAPACK's Cholesky at each n, then exit")
     return ap.parse_args()
 
 
@@ -189,83 +207,78 @@ def source_digest(path):
     return hashlib.sha256(code.encode()).hexdigest()[:16]
 
 
-def contraction_traffic(flops_per_launch, prec):
-    """DRAM bytes per average contraction launch, scaled from the committed ncu
-    summary (bytes per slice-product flop over every contraction launch of a
-    smaller loglik+grad); None when the kernel source has changed since."""
-    path = os.path.join(ROOT, "profiles", "tc_gemm3_kernel_traffic.md")
-    src = os.path.join(ROOT, "paper_1305_4886_gb300", "csrc", "tc_gemm.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "tc_gemm3_kernel_traffic.json")
+TRAFFIC_SRC = os.path.join(ROOT, "paper_1305_4886_gb300", "csrc", "tc_gemm.cu")
+
+
+def contraction_traffic(flops_per_launch, prec, path=TRAFFIC_FILE, src=TRAFFIC_SRC):
+    """DRAM bytes per average contraction launch: the committed ncu figure
+    (dram bytes read + written per slice-product flop over every contraction
+    launch of one loglik+grad step) times this run's slice-product flops per
+    launch; None when the kernel's code has changed since the capture or no
+    figure exists for this precision."""
     try:
-        text = open(path).read()
+        with open(path) as f:
+            rec = json.load(f)
         digest = source_digest(src)
-    except OSError:
+    except (OSError, ValueError):
         return None
-    vals = {}
-    for line in text.splitlines():
-        if line.startswith("- ") and ":" in line:
-            k, v = line[2:].split(":", 1)
-            vals[k.strip()] = v.strip().strip("`")
-    if vals.get("tc_gemm.cu code sha256 prefix") != digest:
+    if rec.get("tc_gemm_code_sha256_prefix") != digest:
         return None
-    key = f"bytes per slice-product flop ({prec})"
-    if key not in vals or not flops_per_launch:
+    ratio = rec.get("bytes_per_slice_flop", {}).get(prec)
+    if not ratio or not flops_per_launch:
         return None
-    return {"bytes_per_launch": float(vals[key]) * flops_per_launch,
-            "source": f"{os.path.relpath(path, ROOT)}: {key} x flops per launch"}
+    return {"bytes_per_launch": float(ratio) * flops_per_launch,
+            "source": f"{os.path.relpath(path, ROOT)} (n={rec.get('n')}): dram bytes per "
+                      "slice-product flop x this run's flops per launch"}
 
 
-def oracle_sample(n_target, budget_s, p_full=None):
-    """Times the oracle's loglik+grad on a size whose cost fits the budget and
-    extrapolates to n_target by the n^3 cost.  Returns (evals/s at n_target,
-    description, threads, seconds)."""
+# The oracle sample that both arms time: one loglik+grad on the headline
+# recipe at this size, extrapolated to the headline n by the n^3 cost.
+CPU_SAMPLE_N = 4096
+
+
+def oracle_time(n, threads=None):
+    """Seconds of one oracle loglik+grad on the config-3 recipe at size n."""
     import oracle
     from paper_1305_4886_gb300 import inputs
     oracle.build()
+    if threads:
+        oracle.set_threads(threads)
+    p = inputs.config3(n)
+    t0 = time.perf_counter()
+    oracle.loglik_grad(p.x, p.z, p.kernel, p.s2, p.rho, p.tau2)
+    return time.perf_counter() - t0
+
+
+def oracle_sample(n_target, n_s=CPU_SAMPLE_N):
+    """The oracle's loglik+grad at n_s (after a small warm-up call),
+    extrapolated to n_target by n^3.  Returns (evals/s at n_target,
+    description, threads)."""
+    import oracle
+    oracle.build()
     threads = oracle.num_threads()
-
-    def run(n):
-        p = inputs.config3(n)
-        t0 = time.perf_counter()
-        oracle.loglik_grad(p.x, p.z, p.kernel, p.s2, p.rho, p.tau2)
-        return time.perf_counter() - t0
-
-    run(256)  # first call: thread start-up and page faults
-    n0 = 768
-    t0 = run(n0)
-    n_s = int(n0 * (budget_s / max(t0, 1e-3)) ** (1.0 / 3.0))
-    n_s = max(n0, min(n_s, 8192, n_target))
-    t_s = run(n_s)
-    if t_s < 0.4 * budget_s and n_s < min(8192, n_target):  # estimate was low: one more step
-        n_s = max(n_s, min(int(n_s * (budget_s / max(t_s, 1e-3)) ** (1.0 / 3.0)), 8192, n_target))
-        t_s = run(n_s)
+    oracle_time(256)  # thread start-up and page faults
+    t_s = oracle_time(n_s)
     t_full = t_s * (n_target / n_s) ** 3
-    desc = (f"oracle loglik+grad on the same recipe at n={n_s} ({t_s:.1f} s, {threads} threads), "
+    desc = (f"oracle loglik+grad on the same recipe at n={n_s} ({t_s:.2f} s, {threads} threads), "
             f"extrapolated to n={n_target} by n^3")
-    return 1.0 / t_full, desc, threads, t_s, n_s
+    return 1.0 / t_full, desc, threads
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
     import oracle
-    from paper_1305_4886_gb300 import inputs
     oracle.build()
     threads = oracle.num_threads()
-    # one step = one oracle loglik+grad on a bounded sample of the workload
-    budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
-    p0 = inputs.config3(384)
-    t0 = time.perf_counter()
-    oracle.loglik_grad(p0.x, p0.z, p0.kernel, p0.s2, p0.rho, p0.tau2)
-    t0 = time.perf_counter() - t0
-    n_s = max(384, min(4096, int(384 * (budget / max(t0, 1e-3)) ** (1.0 / 3.0))))
-    p = inputs.config3(n_s)
+    # one step = one oracle loglik+grad on the same bounded sample of the
+    # workload that our arm's cpu_baseline times, extrapolated by n^3
+    n_s = min(CPU_SAMPLE_N, args.n)
+    oracle_time(256)
     for _ in range(args.warmup):
-        oracle.loglik_grad(p.x, p.z, p.kernel, p.s2, p.rho, p.tau2)
-    ts = []
-    for _ in range(args.steps):
-        t = time.perf_counter()
-        oracle.loglik_grad(p.x, p.z, p.kernel, p.s2, p.rho, p.tau2)
-        ts.append(time.perf_counter() - t)
+        oracle_time(n_s)
+    ts = [oracle_time(n_s) for _ in range(args.steps)]
     t_step = sum(ts) / len(ts)
     t_full = t_step * (args.n / n_s) ** 3
     value = 1.0 / t_full
@@ -276,16 +289,170 @@ def run_reference(args, rank, world):
         "data": "synthetic", "config": workload_config(args.n, "fp64 (CPU oracle)"),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"each step: oracle loglik+grad at n={n_s} "
-                                   f"({t_step:.2f} s), extrapolated to n={args.n} by n^3"},
+                                   f"({t_step:.2f} s mean over {args.steps}), extrapolated "
+                                   f"to n={args.n} by n^3"},
+        "measured_ms_per_sample": t_step * 1e3,
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
+def run_cpu_plan(args):
+    """The CPU baseline table: the oracle's loglik+grad at several n, with all
+    host cores and with one thread, and LAPACK's Cholesky (scipy cho_factor)
+    on the oracle's covariance, one JSON line per measurement."""
+    import numpy as np
+    import oracle
+    import scipy.linalg
+    from paper_1305_4886_gb300 import inputs
+    oracle.build()
+    cores = oracle.num_threads()
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name"):
+                model = ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    host = {"nproc": os.cpu_count(), "model": model}
+    oracle_time(256)
+    sizes = [int(v) for v in args.cpu_plan.split(",")]
+    for n in sizes:
+        for thr in (cores, 1):
+            if thr == 1 and n > 4096:
+                continue  # one thread at n > 4096 takes longer than a bench call allows
+            t = oracle_time(n, threads=thr)
+            print(json.dumps({"kind": "oracle loglik+grad", "n": n, "threads": thr, "s": t,
+                              "extrapolated_to_67275_s": t * (67275 / n) ** 3, "host": host}),
+                  flush=True)
+        oracle.set_threads(cores)
+        p = inputs.config3(n)
+        C = oracle.cov_fill(p.x, p.kernel, p.s2, p.rho, p.tau2)
+        t0 = time.perf_counter()
+        scipy.linalg.cho_factor(C, lower=True, overwrite_a=True, check_finite=False)
+        t = time.perf_counter() - t0
+        print(json.dumps({"kind": "library CPU: scipy.linalg.cho_factor (LAPACK)", "n": n,
+                          "threads": "library default", "s": t,
+                          "gflops": n ** 3 / 3 / t / 1e9, "host": host}), flush=True)
+        del C
+    return 0
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def _mk_graph(fn):
+    """Capture fn() (launches on the current stream) into a CUDA graph on a side
+    stream and return the graph."""
+    import torch
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=side):
+            fn()
+    torch.cuda.current_stream().wait_stream(side)
+    return graph
+
+
+def batched_measure(probs, prec, steps, warmup, autotune=True, task_stats=True):
+    """Config-5 style batch: one gp_loglik_grad_batched call per step, captured
+    once into a CUDA graph and replayed; returns a dict of measurements."""
+    import numpy as np
+    import torch
+
+    from paper_1305_4886_gb300 import gp
+
+    xs = [torch.as_tensor(p.x, device="cuda") for p in probs]
+    zs = [torch.as_tensor(p.z, device="cuda") for p in probs]
+    prms = [gp.params(p.kernel, p.s2, p.rho, p.tau2) for p in probs]
+    r = gp.loglik_grad_batched(xs, zs, prms, precision=prec)
+    torch.cuda.synchronize()
+    batch, ws = r["batch"], r["ws"]
+    out, grad, info = r["out"], r["grad"], r["info"]
+    tile_policy = None
+    if prec == "mixed_f16" and autotune:
+        # the tile autotuner: FP64 64 x 64 tiles below a size threshold,
+        # tensor-core 128 x 128 tiles above it, chosen by timing this batch
+        choice, cand_ms = gp.gp_batched_autotune(batch, prec, ws, out, grad, info)
+        torch.cuda.synchronize()
+        tile_policy = {"fp64_tiles_up_to_n": choice,
+                       "candidates_ms": {str(k): round(v, 3) for k, v in cand_ms.items()}}
+    for _ in range(max(0, warmup - 1)):
+        gp.gp_loglik_grad_batched(batch, prec, ws, out, grad, info)
+    torch.cuda.synchronize()
+    graph = _mk_graph(lambda: gp.gp_loglik_grad_batched(batch, prec, ws, out, grad, info))
+    graph.replay()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        graph.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    bad = int((info != 0).sum().item())
+    rres = out[:, 3].double().cpu().numpy()
+    flops = sum(float(p.n) ** 3 for p in probs)
+    res = {"precision": prec, "steps": steps, "warmup": warmup, "ms_per_batch": ms / steps,
+           "evals_per_s": len(probs) * steps / (ms / 1e3), "failed_problems": bad,
+           "loglik_grad_alg_tflops": flops * steps / (ms / 1e3) / 1e12,
+           "graph": "one CUDA graph per step", "tiles": tile_policy or "FP64 64 x 64",
+           "out": out.cpu().numpy(), "grad": grad.cpu().numpy()}
+    if prec == "mixed_f16":
+        res["refine_resid"] = {"max": float(np.max(rres)), "median": float(np.median(rres))}
+    if task_stats and prec in ("fp64", "mixed_f16"):
+        # one more (untimed) batch with the task graph's cycle counters on:
+        # where the persistent launch spends its CTA time, per task class
+        gp.gp_batched_profile(True)
+        gp.gp_loglik_grad_batched(batch, prec, ws, out, grad, info)
+        torch.cuda.synchronize()
+        gp.gp_batched_profile(False)
+        st = gp.gp_batched_task_stats(ws)
+        mhz = 2070.0
+        ts = {k: {"cta_ms": v["cycles"] / (mhz * 1e3), "wait_ms": v["wait_cycles"] / (mhz * 1e3),
+                  "tasks": v["tasks"]}
+              for k, v in st.items() if k != "steps" and v["tasks"]}
+        if st["steps"]:
+            # one step: a 128 x 128 x 128 tile product, six 16-bit slice products
+            ts["tensor_steps"] = st["steps"]
+            ts["slice_tflops_per_step_time"] = st["steps"] * 6 * 2 * 128.0 ** 3 / (ms / steps / 1e3) / 1e12
+        res["task_stats"] = ts
+    del ws, r, graph
+    torch.cuda.empty_cache()
+    return res
+
+
+def time_cholesky(x, prm, n, prec, ws, info, reps):
+    """CUDA-event time of gp_chol alone (the fill is redone, untimed, before
+    each repetition) on the matrix region of a loglik workspace, whose tail
+    serves as the factorisation's workspace.  Returns the median ms."""
+    import torch
+
+    from paper_1305_4886_gb300 import gp
+    np_ = gp.gp_padded_order(n)
+    A = ws[: np_ * np_ * 8].view(torch.float64)
+    tail = ws[np_ * np_ * 8:]
+    stream = torch.cuda.current_stream()
+    times = []
+    for _ in range(reps):
+        gp.gp_cov_fill(x, prm, A, np_, precision=prec)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gp.gp_chol(A, n, np_, prec, tail, info)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if int(info.item()) != 0:
+            raise RuntimeError(f"gp_chol failed, info={int(info.item())}")
+        times.append(e0.elapsed_time(e1))
+    return statistics.median(times)
+
+
 def run_ours(args, rank, world, local):
     import numpy as np
     import torch
@@ -308,19 +475,28 @@ def run_ours(args, rank, world, local):
     np_ = gp.gp_padded_order(n)
     x = torch.as_tensor(p.x, device="cuda")
     z = torch.as_tensor(p.z, device="cuda")
-    ws = gp.workspace(n, prec, want_grad=True)
     out = torch.empty(4, dtype=torch.float64, device="cuda")
     grad = torch.empty(3, dtype=torch.float64, device="cuda")
     alpha = torch.empty(n, dtype=torch.float64, device="cuda")
     info = torch.zeros(1, dtype=torch.int64, device="cuda")
+    extras = rank == 0 and not args.no_extras and prec == "mixed_f16"
 
-    # y = L z with this library's factor of C(theta) (untimed set-up)
-    gp.gp_loglik(x, z, None, n, prm, prec, ws, out, None, info)
+    # y = L z with the FP64-grade factor of C(theta) (untimed set-up; at this
+    # size the CUDA-core FP64 factor takes minutes, and the FP64-grade one
+    # agrees with it to about 1e-12)
+    y_form = "emu_fp64" if prec != "fp64" else "fp64"
+    ws_ref = gp.workspace(n, y_form, want_grad=True)
+    gp.gp_loglik(x, z, None, n, prm, y_form, ws_ref, out, None, info)
     y = torch.empty(n, dtype=torch.float64, device="cuda")
-    gp.gp_mult_chol(ws[: np_ * np_ * 8].view(torch.float64), n, np_, z, y)
+    gp.gp_mult_chol(ws_ref[: np_ * np_ * 8].view(torch.float64), n, np_, z, y)
     torch.cuda.synchronize()
     if int(info.item()) != 0:
         raise RuntimeError(f"set-up factorisation failed, info={int(info.item())}")
+    if not extras:
+        del ws_ref
+        ws_ref = None
+        torch.cuda.empty_cache()
+    ws = gp.workspace(n, prec, want_grad=True)
 
     def step():
         gp.gp_loglik_grad(x, y, None, n, prm, prec, ws, out, alpha, grad, info)
@@ -352,6 +528,7 @@ def run_ours(args, rank, world, local):
     if dist:
         dist.barrier()
     elapsed_ms = e0.elapsed_time(e1)
+    # every profiled launch of the timed region is recorded, or this raises
     prof = {c: gp.gp_prof_read(c) for c in gp.PROF_CLASSES}
     gp.gp_prof_enable(False)
     if int(info.item()) != 0:
@@ -360,10 +537,12 @@ def run_ours(args, rank, world, local):
     value = world * args.steps / (elapsed_ms / 1e3)
     res = out.cpu().numpy()
     g_res = grad.cpu().numpy()
+    a_res = alpha.cpu().numpy()
 
     # ---- end to end through the public API: host buffers in, scalars out ----
     e2e = None
     if not args.no_e2e:
+        ksteps = max(1, min(args.steps, args.e2e_steps))
         x_h = torch.as_tensor(p.x).pin_memory()
         y_h = y.cpu().pin_memory()
         out_h = torch.empty(4, dtype=torch.float64).pin_memory()
@@ -376,7 +555,7 @@ def run_ours(args, rank, world, local):
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
         f0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(ksteps):
             x_d.copy_(x_h, non_blocking=True)
             y_d.copy_(y_h, non_blocking=True)
             gp.gp_loglik_grad(x_d, y_d, None, n, prm, prec, ws, out, alpha, grad, info)
@@ -386,52 +565,50 @@ def run_ours(args, rank, world, local):
         torch.cuda.synchronize()
         e2e_ms = f0.elapsed_time(f1)
         e2e_ms = max_over_ranks(e2e_ms, dist if dist else None, "cuda")
-        e2e = {"value": world * args.steps / (e2e_ms / 1e3), "unit": UNIT,
+        e2e = {"value": world * ksteps / (e2e_ms / 1e3), "unit": UNIT, "steps": ksteps,
                "h2d_bytes_per_step": int(x_h.numel() * 8 + y_h.numel() * 8),
                "d2h_bytes_per_step": int((out_h.numel() + grad_h.numel()) * 8)}
 
-    # ---- stated error (untimed): the same evaluation in the FP64-grade form ----
-    err = None
-    if not args.no_error and prec == "mixed_f16":
-        ws_ref = gp.workspace(n, "emu_fp64", want_grad=True)
-        r = gp.loglik_grad(x, y, p.kernel, p.s2, p.rho, p.tau2, precision="emu_fp64", ws=ws_ref)
-        ro, rg, ra = r["out"].cpu().numpy(), r["grad"].cpu().numpy(), r["alpha"].cpu().numpy()
-        del ws_ref, r
-        torch.cuda.empty_cache()
-        a_res = alpha.cpu().numpy()
-        err = {"against": "emu_fp64 (five BF16 integer slices, FP64-grade; pinned to the "
-                          "oracle at n <= 1300 to 1e-10 / 1e-8)",
-               "loglik_rel": float(abs(res[0] - ro[0]) / abs(ro[0])),
-               "grad_rel_inf": float(np.max(np.abs(g_res - rg)) / np.max(np.abs(rg))),
-               "alpha_rel": float(np.linalg.norm(a_res - ra) / np.linalg.norm(ra))}
-
     peaks, peak_src = measured_peaks()
     ms_c, cnt_c, fl_c, _ = prof["contract"]
-    achieved = fl_c / (ms_c / 1e3) / 1e12 if ms_c > 0 else None
     peak_tf = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
     pairs = {"mixed_f16": 6, "emu_fp64": 15}.get(prec, 0)
+    slice_tf = fl_c / (ms_c / 1e3) / 1e12 if ms_c > 0 else None
+    # algorithmic (FP64-equivalent) flops of the contractions: the useful
+    # output entries and K ranges, 2 flops per multiply-add, not the split
+    # products that carry them
+    alg_c = fl_c / pairs if pairs else fl_c
+    alg_tf = alg_c / (ms_c / 1e3) / 1e12 if ms_c > 0 else None
     traffic = contraction_traffic(fl_c / max(cnt_c, 1), prec)
     kname = {"mixed_f16": "tc_gemm3_kernel (tcgen05 contraction, three FP16 slices, one "
                           "accumulator per product group, two MMA issuers",
              "emu_fp64": "tc_gemm_kernel<4> (tcgen05 contraction, five BF16 slices"}.get(
-                 prec, "contraction")
+                 prec, "gemm_f64_kernel (FP64 CUDA cores")
     roofline = {
         "kernel": kname + "; Cholesky update, panel solve, TRTRI/LAUUM)",
-        "bound": "tensor", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
-        "frac": (achieved / peak_tf) if achieved else None,
+        "bound": "tensor", "achieved": alg_tf, "peak": peak_tf, "unit": "TFLOP/s",
+        "frac": (alg_tf / peak_tf) if alg_tf else None,
         "traffic": traffic["bytes_per_launch"] if traffic else None,
         "traffic_source": traffic["source"] if traffic else None,
         "peak_source": f"bf16 sustained, {peak_src}", "launches": cnt_c,
         "share_of_step": ms_c / elapsed_ms if elapsed_ms > 0 else None,
-        "flops_counted": f"slice-product flops ({pairs} 16-bit products per FP64 product) "
-                         "over the useful output entries and K ranges, per launch (average)",
+        "flops_counted": "algorithmic: 2 flops per multiply-add of the FP64 products the "
+                         "contractions stand for (useful output entries and K ranges), per launch "
+                         "(average)",
+        "alg_flops_per_step": alg_c / args.steps,
+        "slice_products": {"per_fp64_product": pairs, "achieved": slice_tf,
+                           "frac": (slice_tf / peak_tf) if slice_tf else None,
+                           "note": "the tensor pipe's own work: every 16-bit slice product "
+                                   "counted"},
     }
     ms_f, cnt_f, _, by_f = prof["fill"]
     fill = {"achieved_gbs": (by_f / (ms_f / 1e3) / 1e9) if ms_f > 0 else None,
             "peak_gbs": peaks.get("hbm_gbs"), "ms_per_launch": ms_f / max(cnt_f, 1),
-            "bound": "fp64 alu (exp)"}
+            "bound": "fp32 alu (double-float kernel evaluation)" if prec != "fp64"
+                     else "fp64 alu (exp)"}
     fill["frac_of_hbm"] = (fill["achieved_gbs"] / fill["peak_gbs"]) if fill["achieved_gbs"] else None
     chol_alg = n ** 3 / 3.0
+    per_step = {c: prof[c][0] / args.steps for c in prof}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -444,33 +621,96 @@ def run_ours(args, rank, world, local):
         "roofline": roofline, "fill": fill,
         "result": {"loglik": float(res[0]), "logdet": float(res[1]), "quad": float(res[2]),
                    "refine_resid": float(res[3]), "grad": [float(v) for v in g_res]},
-        "error": err,
         "loglik_grad_alg_tflops": n ** 3 / (elapsed_ms / args.steps / 1e3) / 1e12,
-        "per_step_ms": {c: prof[c][0] / args.steps for c in prof},
+        "per_step_ms": per_step,
+        "per_step_ms_profiled_sum": sum(per_step.values()),
         "per_step_launches": {c: prof[c][1] / args.steps for c in prof},
-        "contract_flops_per_step": fl_c / args.steps,
         "cholesky_alg_flop": chol_alg,
+        "y": f"L z with the {y_form} factor",
         "parallelism": "replicas" if world > 1 else "single GPU",
     }
 
+    if extras:
+        # ---- the Cholesky alone (the metric's first clause), mixed form ----
+        t_chol = time_cholesky(x, prm, n, prec, ws, info, reps=3)
+        chol = {prec: {"ms": t_chol, "tflops": chol_alg / (t_chol / 1e3) / 1e12}}
+        del ws
+        torch.cuda.empty_cache()
+        # ---- the FP64-grade form (five BF16 integer slices), same workload ----
+        r_ws = ws_ref
+        for _ in range(1):
+            gp.gp_loglik_grad(x, y, None, n, prm, "emu_fp64", r_ws, out, alpha, grad, info)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.emu_steps):
+            gp.gp_loglik_grad(x, y, None, n, prm, "emu_fp64", r_ws, out, alpha, grad, info)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        if int(info.item()) != 0:
+            raise RuntimeError(f"FP64-grade evaluation failed, info={int(info.item())}")
+        emu_ms = f0.elapsed_time(f1) / args.emu_steps
+        ro, rg, ra = out.cpu().numpy(), grad.cpu().numpy(), alpha.cpu().numpy()
+        t_chol_e = time_cholesky(x, prm, n, "emu_fp64", r_ws, info, reps=2)
+        chol["emu_fp64"] = {"ms": t_chol_e, "tflops": chol_alg / (t_chol_e / 1e3) / 1e12}
+        del r_ws, ws_ref
+        torch.cuda.empty_cache()
+        line["cholesky"] = chol
+        line["cholesky_tflops"] = chol[prec]["tflops"]
+        line["emu_fp64"] = {
+            "evals_per_s": 1e3 / emu_ms, "ms_per_eval": emu_ms, "steps": args.emu_steps,
+            "warmup": 1, "speedup_of_mixed": emu_ms / (elapsed_ms / args.steps),
+            "result": {"loglik": float(ro[0]), "grad": [float(v) for v in rg]}}
+        line["error"] = {
+            "against": "emu_fp64 (five BF16 integer slices, FP64-grade), same run and inputs",
+            "loglik_rel": float(abs(res[0] - ro[0]) / abs(ro[0])),
+            "grad_rel_inf": float(np.max(np.abs(g_res - rg)) / np.max(np.abs(rg))),
+            "alpha_rel": float(np.linalg.norm(a_res - ra) / np.linalg.norm(ra))}
+        # ---- the batched workload (512 problems, one graph replay per step) ----
+        probs = inputs.config5(nprob=args.nprob)
+        bm = batched_measure(probs, "mixed_f16", args.batched_steps, 3)
+        bf = batched_measure(probs, "fp64", 2, 1, task_stats=False)
+        ob, gb = bm.pop("out"), bm.pop("grad")
+        of, gf = bf.pop("out"), bf.pop("grad")
+        bm["error_vs_fp64"] = {
+            "loglik_rel_max": float(np.max(np.abs(ob[:, 0] - of[:, 0]) / np.abs(of[:, 0]))),
+            "grad_rel_inf_max": float(np.max(np.max(np.abs(gb - gf), axis=1) /
+                                              np.max(np.abs(gf), axis=1)))}
+        line["batched"] = {"workload": "512 independent GPs, n log-uniform [256, 4096], 2-D "
+                                       "uniform locations, exp / Matern 3/2 alternating, "
+                                       "y ~ N(0, I)", "seed": 48865,
+                           "mixed_f16": bm, "fp64": bf}
+
     if rank == 0 and not args.no_cpu_baseline:
-        v, desc, thr, _, _ = oracle_sample(n, args.cpu_budget)
+        v, desc, thr = oracle_sample(n)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
                                 "sample": desc}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
+        dist.barrier()
         dist.destroy_process_group()
     return 0
 
 
 def run_accuracy(args):
-    """Errors of the mixed and FP64-grade forms against the FP64 path (config-3
-    recipe, y = L z with the FP64 factor), one JSON line per n and form."""
+    """Errors of the mixed and FP64-grade forms against the CUDA-core FP64
+    path (config-3 recipe, y = L z with the FP64 factor), one JSON line per n
+    and form, with each form's evaluation time."""
     import numpy as np
     import torch
 
     from paper_1305_4886_gb300 import gp, inputs
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1)
 
     for n in [int(v) for v in args.accuracy.split(",")]:
         p = inputs.config3(n)
@@ -481,17 +721,21 @@ def run_accuracy(args):
         gp.loglik(x, z, p.kernel, p.s2, p.rho, p.tau2, precision="fp64", ws=ws)
         y = torch.empty_like(z)
         gp.gp_mult_chol(gp.factor_view(ws, n).reshape(-1), n, np_, z, y)
-        ref = gp.loglik_grad(x, y, p.kernel, p.s2, p.rho, p.tau2, precision="fp64", ws=ws)
+        ref, ms64 = timed(lambda: gp.loglik_grad(x, y, p.kernel, p.s2, p.rho, p.tau2,
+                                                 precision="fp64", ws=ws))
         ro, rg, ra = (ref["out"].cpu().numpy(), ref["grad"].cpu().numpy(),
                       ref["alpha"].cpu().numpy())
+        print(json.dumps({"n": n, "precision": "fp64", "ms": ms64, "loglik": float(ro[0]),
+                          "grad": [float(v) for v in rg]}), flush=True)
         del ws, ref
         torch.cuda.empty_cache()
         for prec in ["mixed_f16", "emu_fp64"]:
-            r = gp.loglik_grad(x, y, p.kernel, p.s2, p.rho, p.tau2, precision=prec)
+            r, ms = timed(lambda: gp.loglik_grad(x, y, p.kernel, p.s2, p.rho, p.tau2,
+                                                 precision=prec))
             o, g, a = r["out"].cpu().numpy(), r["grad"].cpu().numpy(), r["alpha"].cpu().numpy()
             del r
             torch.cuda.empty_cache()
-            print(json.dumps({"n": n, "precision": prec, "against": "fp64",
+            print(json.dumps({"n": n, "precision": prec, "against": "fp64", "ms": ms,
                               "loglik_rel": float(abs(o[0] - ro[0]) / abs(ro[0])),
                               "logdet_rel": float(abs(o[1] - ro[1]) / abs(ro[1])),
                               "grad_rel_inf": float(np.max(np.abs(g - rg)) / np.max(np.abs(rg))),
@@ -505,10 +749,9 @@ def run_batched(args, rank, world, local):
     [256, 4096], exponential / Matern 3/2 alternating, one gp_loglik_grad_batched
     call per step, captured once into a CUDA graph and replayed.  With N ranks
     the problems are partitioned by cost (no collective on the data path)."""
-    import numpy as np
     import torch
 
-    from paper_1305_4886_gb300 import gp, inputs
+    from paper_1305_4886_gb300 import inputs
 
     torch.cuda.set_device(local)
     dist = None
@@ -519,69 +762,17 @@ def run_batched(args, rank, world, local):
     # longest-processing-time partition of the problems over ranks
     mine = lpt_partition([p.n for p in probs], world, rank)
     sel = [probs[i] for i in mine]
-    xs = [torch.as_tensor(p.x, device="cuda") for p in sel]
-    zs = [torch.as_tensor(p.z, device="cuda") for p in sel]
-    prms = [gp.params(p.kernel, p.s2, p.rho, p.tau2) for p in sel]
-    prec = args.precision
-    r = gp.loglik_grad_batched(xs, zs, prms, precision=prec)
-    torch.cuda.synchronize()
-    batch, ws = r["batch"], r["ws"]
-    out, grad, info = r["out"], r["grad"], r["info"]
-    tile_policy = None
-    if prec == "mixed_f16":
-        # the tile autotuner: FP64 64 x 64 tiles below a size threshold,
-        # tensor-core 128 x 128 tiles above it, chosen by timing this batch
-        choice, cand_ms = gp.gp_batched_autotune(batch, prec, ws, out, grad, info)
-        torch.cuda.synchronize()
-        tile_policy = {"fp64_tiles_up_to_n": choice,
-                       "candidates_ms": {str(k): round(v, 3) for k, v in cand_ms.items()}}
-    for _ in range(max(0, args.warmup - 1)):
-        gp.gp_loglik_grad_batched(batch, prec, ws, out, grad, info)
-    torch.cuda.synchronize()
-    side = torch.cuda.Stream()
-    side.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(side):
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph, stream=side):
-            gp.gp_loglik_grad_batched(batch, prec, ws, out, grad, info)
-    torch.cuda.current_stream().wait_stream(side)
-    graph.replay()
-    torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    stream = torch.cuda.current_stream()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
     clocks.start()
-    e0.record(stream)
-    for _ in range(args.steps):
-        graph.replay()
-    e1.record(stream)
-    torch.cuda.synchronize()
+    res = batched_measure(sel, args.precision, args.steps, args.warmup)
     clk = clocks.stop()
-    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
-    bad = int((info != 0).sum().item())
-    rres = out[:, 3].double().cpu().numpy()
-    flops = sum(float(p.n) ** 3 for p in probs)
-    task_stats = None
-    if prec in ("fp64", "mixed_f16"):
-        # one more (untimed) batch with the task graph's cycle counters on:
-        # where the persistent launch spends its CTA time, per task class
-        gp.gp_batched_profile(True)
-        gp.gp_loglik_grad_batched(batch, prec, ws, out, grad, info)
-        torch.cuda.synchronize()
-        gp.gp_batched_profile(False)
-        st = gp.gp_batched_task_stats(ws)
-        mhz = clk.get("sm_mhz") or 2070.0
-        task_stats = {k: {"cta_ms": v["cycles"] / (mhz * 1e3), "wait_ms": v["wait_cycles"] / (mhz * 1e3),
-                          "tasks": v["tasks"]}
-                      for k, v in st.items() if k != "steps" and v["tasks"]}
-        if st["steps"]:
-            # one step: a 128 x 128 x 128 tile product, six 16-bit slice products
-            task_stats["tensor_steps"] = st["steps"]
-            task_stats["slice_tflops_per_step_time"] = st["steps"] * 6 * 2 * 128.0 ** 3 / (ms / args.steps / 1e3) / 1e12
+    res.pop("out")
+    res.pop("grad")
+    ms = max_over_ranks(res["ms_per_batch"] * args.steps, dist, "cuda")
     value = len(probs) * args.steps / (ms / 1e3)
+    prec = args.precision
     line = {"metric": f"batched GP loglik+grad evaluations/s ({len(probs)} problems, n in [256, 4096])",
             "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -591,13 +782,9 @@ def run_batched(args, rank, world, local):
             "data": "synthetic",
             "config": {"workload": "512 independent GPs, n log-uniform [256, 4096], 2-D uniform "
                                    "locations, exp / Matern 3/2 alternating, y ~ N(0, I)",
-                       "precision": prec, "seed": 48865, "graph": "one CUDA graph per step",
-                       "tiles": tile_policy or "FP64 64 x 64"},
-            "clocks": clk, "failed_problems": bad,
-            "refine_resid": {"max": float(np.max(rres)), "median": float(np.median(rres))},
-            "loglik_grad_alg_tflops": flops * args.steps / (ms / 1e3) / 1e12}
-    if task_stats:
-        line["task_stats"] = task_stats
+                       "precision": prec, "seed": 48865, "graph": res["graph"],
+                       "tiles": res["tiles"]},
+            "clocks": clk, "detail": res}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -610,6 +797,8 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.cpu_plan:
+        return run_cpu_plan(args) if rank == 0 else 0
     if args.accuracy:
         return run_accuracy(args) if rank == 0 else 0
     if args.workload == "batched":

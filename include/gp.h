@@ -208,6 +208,27 @@ int gp_loglik_grad_batched(int nprob, const int64_t *h_n, const double *const *h
 void gp_batched_profile(int on);
 int gp_batched_task_stats(const void *d_ws, unsigned long long *h_out);
 
+/* Limit of each dependency wait inside the persistent batched launch (one
+ * thread of a CTA spinning on another task's flag), in seconds, for later
+ * gp_loglik_grad_batched calls in this process; default 20, accepted range
+ * 1e-3 to 600 (else GP_ERR_INVALID).  A wait that runs past it sets that
+ * problem's d_info to -1 and makes every CTA leave the launch; problems
+ * whose evaluation had finished keep their results, every other problem
+ * gets d_info = -1 (if it had no status) and NaN results.  The device stays
+ * usable: the next call starts afresh.                                    */
+int gp_batched_set_wait_limit(double seconds);
+
+/* Testing aid for the bounded waits (no counterpart in the paper): in later
+ * gp_loglik_grad_batched calls of this process, every wait for the Cholesky
+ * tile (tile_row, tile_col) of problem `problem` (tile coordinates in that
+ * problem's tiles: 64 x 64 in GP_FP64) behaves as if the tile were never
+ * produced, so that the first such wait runs into the wait limit.  No GPU
+ * fault is involved: the wait ends at its limit like any other.  problem
+ * = -1 turns it off.  tile_col > tile_row or a negative index returns
+ * GP_ERR_INVALID here; a tile row beyond the problem's tiles makes the
+ * batched call return GP_ERR_INVALID before any device work.              */
+int gp_batched_test_unset_tile(int problem, int64_t tile_row, int64_t tile_col);
+
 /* Tile policy of the GP_MIXED_F16 batched launch (per device): problems with
  * n <= fp64_max_n run on FP64 64 x 64 tiles (CUDA cores), the others on
  * 128 x 128 tensor-core tiles, in the same launch.  Default 0 (every problem
@@ -302,9 +323,15 @@ int gp_prof_enable(int on);
 
 /* Sums for one class over the launches recorded since gp_prof_enable(1):
  * total event time (ms), launch count, algorithmic flops and bytes.  Waits
- * for the recorded events.  Returns GP_ERR_WORKSPACE if launches were
- * dropped because the event pool (16384 launches) was full.               */
+ * for the recorded events.  The event pool grows on demand up to 2^20
+ * launches; returns GP_ERR_WORKSPACE if any launch since gp_prof_enable(1)
+ * went unrecorded (pool cap reached or an event call failed), in which case
+ * the sums cover only the recorded launches and must not be used.        */
 int gp_prof_read(int cls, double *ms_total, int64_t *launches, double *flops, double *bytes);
+
+/* Launches left unrecorded since gp_prof_enable(1) (0 when the sums of
+ * gp_prof_read cover every profiled launch).                              */
+int64_t gp_prof_dropped(void);
 
 #ifdef __cplusplus
 }

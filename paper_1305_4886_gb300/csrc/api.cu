@@ -372,6 +372,15 @@ int gp_loglik_grad_batched(int nprob, const int64_t *h_n, const double *const *h
 
 void gp_batched_profile(int on) { dag_set_profile(on); }
 
+int gp_batched_set_wait_limit(double seconds) {
+    if (!(seconds >= 1e-3 && seconds <= 600.0)) return GP_ERR_INVALID;
+    return dag_set_wait_ns((uint64_t)(seconds * 1e9));
+}
+
+int gp_batched_test_unset_tile(int problem, int64_t tile_row, int64_t tile_col) {
+    return dag_set_unset_tile(problem, tile_row, tile_col);
+}
+
 int gp_batched_set_tile_policy(int64_t fp64_max_n) {
     if (fp64_max_n < 0) return GP_ERR_INVALID;
     dag_set_fp64_max_n(fp64_max_n);

@@ -38,6 +38,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <stdlib.h>
 #include <string.h>
 #include <vector>
@@ -75,11 +76,13 @@ __global__ void __launch_bounds__(DAG_THREADS, 2)
     }
 }
 
-// After an abort, every problem still without a status gets -1 and NaN.
+// After an abort, every problem whose final task did not finish gets -1 (if
+// it has no status yet) and NaN results; finished problems keep theirs.
 __global__ void dag_finish_kernel(const DagHdr *h, const DagProb *probs, int P) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P || !h->abort) return;
     const DagProb &d = probs[p];
+    if (d.flag[dag_done_flag(d.T, d.mixed)] != 0) return;
     if (*d.info == 0) *d.info = -1;
     for (int q = 0; q < 4; ++q) d.out[q] = nan("");
     for (int q = 0; q < 3; ++q) d.grad[q] = nan("");
@@ -92,6 +95,8 @@ __global__ void dag_finish_kernel(const DagHdr *h, const DagProb *probs, int P) 
 constexpr int DAG_SETUP_CHUNK = 128;
 struct DagSetup {
     int first, count, prof, pad_;
+    unsigned long long wait_ns;
+    const int *unset;
     double tab[EXP_TAB];
     float2 dftab[DF_TAB];
     DagProb p[DAG_SETUP_CHUNK];
@@ -106,7 +111,12 @@ __global__ void dag_setup_kernel(const __grid_constant__ DagSetup s, DagProb *pr
         *s.p[t].info = 0;
     }
     if (s.first == 0) {
-        if (t == 0) reinterpret_cast<DagHdr *>(hdr_raw)->prof = s.prof;
+        if (t == 0) {
+            DagHdr *h = reinterpret_cast<DagHdr *>(hdr_raw);
+            h->prof = s.prof;
+            h->wait_ns = s.wait_ns;
+            h->unset = s.unset;
+        }
         if (t < EXP_TAB) tab[t] = s.tab[t];
         for (int q = t; q < DF_TAB; q += blockDim.x) dftab[q] = s.dftab[q];
     }
@@ -339,6 +349,28 @@ int64_t dag_fp64_max_n() {
     return g_fp64_max_n[dev].load();
 }
 
+// The wait limit of the batched launches and the testing aid that leaves one
+// Cholesky tile flag of one problem unraised (process-wide settings).
+static std::mutex g_wait_mu;
+static uint64_t g_wait_ns = DAG_WAIT_NS;
+static int g_unset_prob = -1;
+static int64_t g_unset_i = 0, g_unset_j = 0;
+
+int dag_set_wait_ns(uint64_t ns) {
+    std::lock_guard<std::mutex> lk(g_wait_mu);
+    g_wait_ns = ns;
+    return GP_OK;
+}
+
+int dag_set_unset_tile(int prob, int64_t i, int64_t j) {
+    if (prob >= 0 && (j < 0 || i < j)) return GP_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(g_wait_mu);
+    g_unset_prob = prob < 0 ? -1 : prob;
+    g_unset_i = i;
+    g_unset_j = j;
+    return GP_OK;
+}
+
 size_t dag_workspace_bytes(int nprob, const int64_t *h_n, int mixed) {
     return dag_layout(nprob, h_n, mixed, mixed ? std::max(dag_tc_ctas(), 1) : 0, 0, true).total;
 }
@@ -358,12 +390,14 @@ int dag_run(int nprob, const int64_t *h_n, const double *const *h_dx, const doub
     char *base = static_cast<char *>(d_ws);
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return GP_ERR_CUDA;
-    static bool attr_set[64] = {};
-    if (!mixed && !attr_set[dev]) {
+    // set once per device; a race between host threads only repeats the
+    // (idempotent) attribute call
+    static std::atomic<bool> attr_set[64];
+    if (!mixed && !attr_set[dev].load(std::memory_order_acquire)) {
         if (cudaFuncSetAttribute(dag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sizeof(DagSmem)) != cudaSuccess)
             return GP_ERR_CUDA;
-        attr_set[dev] = true;
+        attr_set[dev].store(true, std::memory_order_release);
     }
     if (cudaMemsetAsync(base + L.flags, 0, L.flags_bytes, s) != cudaSuccess) return GP_ERR_CUDA;
     DagHdr *hdr = reinterpret_cast<DagHdr *>(base + L.flags);
@@ -371,6 +405,18 @@ int dag_run(int nprob, const int64_t *h_n, const double *const *h_dx, const doub
     DagProb *probs = reinterpret_cast<DagProb *>(base + L.probs);
     double *tab = reinterpret_cast<double *>(base + L.tab);
     float2 *dftab = reinterpret_cast<float2 *>(base + L.dftab);
+    uint64_t wait_ns;
+    const int *unset = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_wait_mu);
+        wait_ns = g_wait_ns;
+        if (g_unset_prob >= 0 && g_unset_prob < nprob) {
+            int sidx = 0;
+            while (L.order[sidx] != g_unset_prob) ++sidx;
+            if (g_unset_i >= L.T[sidx]) return GP_ERR_INVALID;
+            unset = flag0 + L.flag[sidx] + tile_index(L.T[sidx], (int)g_unset_i, (int)g_unset_j);
+        }
+    }
     // descriptors, in chunks of kernel parameters
     std::vector<DagSetup> chunks((nprob + DAG_SETUP_CHUNK - 1) / DAG_SETUP_CHUNK);
     for (int s0 = 0, c = 0; s0 < nprob; s0 += DAG_SETUP_CHUNK, ++c) {
@@ -379,6 +425,8 @@ int dag_run(int nprob, const int64_t *h_n, const double *const *h_dx, const doub
         su.first = s0;
         su.count = std::min(DAG_SETUP_CHUNK, nprob - s0);
         su.prof = dag_profiling() ? 1 : 0;
+        su.wait_ns = wait_ns;
+        su.unset = unset;
         for (int q = 0; q < EXP_TAB; ++q) su.tab[q] = kps[0].tab[q];
         for (int q = 0; q < DF_TAB; ++q) su.dftab[q] = kps[0].kd.tab[q];
         for (int q = 0; q < su.count; ++q) {

@@ -14,8 +14,8 @@ constexpr int DB = 64;                  // tile order
 constexpr int DLD = DB + 1;             // shared-memory leading dimension
 constexpr int DAG_THREADS = 256;
 constexpr int DAG_ROUNDS = 1024;        // rounds of the proportional merge
-constexpr uint64_t DAG_WAIT_NS = 20ull * 1000 * 1000 * 1000;  // 20 s per wait
-constexpr uint32_t DAG_WAIT_POLLS = 1u << 30;
+constexpr uint64_t DAG_WAIT_NS = 20ull * 1000 * 1000 * 1000;  // default limit of one wait: 20 s
+constexpr uint32_t DAG_WAIT_POLLS = 1u << 30;  // a second guard on every wait (> 2 min of polls)
 
 enum DagTaskType { DT_CHOL = 0, DT_SOLVE = 1, DT_TRTRI = 2, DT_LG = 3, DT_FINAL = 4 };
 
@@ -53,7 +53,10 @@ struct DagHdr {
     int next;   // ticket of the next task in the global list
     int abort;  // a wait timed out: every CTA stops
     int prof;   // count cycles per task class (diagnostics)
-    int pad_[13];
+    int pad0_;
+    unsigned long long wait_ns;  // limit of one dependency wait (host-set per call)
+    const int *unset;            // testing aid: waits on this flag never see it raised
+    int pad_[8];
     unsigned long long cyc[DAG_NSTAT];   // SM cycles inside tasks of the class
     unsigned long long wait[DAG_NSTAT];  // of which spent waiting for inputs
     unsigned long long cnt[DAG_NSTAT];   // tasks
@@ -73,10 +76,12 @@ __host__ __device__ inline int dag_ntasks(int T, int mixed) {
 
 // Flags per problem.  FP64: L (ntiles), X (ntiles), solve, LG count.
 // Mixed: L, X, solve, residual counts (DAG_EVALS), corrections
-// (DAG_EVALS - 1), log-likelihood, LG count, converged.
+// (DAG_EVALS - 1), log-likelihood, LG count, converged.  Both: a last flag
+// raised when the problem's final task has written its results.
 __host__ __device__ inline int dag_nflags(int T, int mixed) {
-    return 2 * dag_ntiles(T) + (mixed ? 3 + 2 * DAG_EVALS + 1 : 2);
+    return 2 * dag_ntiles(T) + (mixed ? 3 + 2 * DAG_EVALS + 1 : 2) + 1;
 }
+__host__ __device__ inline int dag_done_flag(int T, int mixed) { return dag_nflags(T, mixed) - 1; }
 __host__ __device__ inline int dag_solved_flag(int T) { return 2 * dag_ntiles(T); }
 __host__ __device__ inline int dag_lg_flag(int T, int mixed) {
     return mixed ? 2 * dag_ntiles(T) + 2 * DAG_EVALS + 1 : 2 * dag_ntiles(T) + 1;
@@ -229,9 +234,12 @@ static __device__ bool dag_wait(const int *f, int target, DagHdr *h, int64_t *in
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
+        // the testing aid: a flag that counts as never raised
+        if (f == h->unset) target = 0x7fffffff;
         if (ld_acquire_gpu(f) < target) {
             const long long c0 = clock64();
             const uint64_t t0 = globaltimer_ns();
+            const uint64_t limit = h->wait_ns;
             for (uint32_t it = 0;; ++it) {
                 if (ld_acquire_gpu(f) >= target) break;
                 if (ld_relaxed_gpu(&h->abort)) {
@@ -240,7 +248,7 @@ static __device__ bool dag_wait(const int *f, int target, DagHdr *h, int64_t *in
                 }
                 __nanosleep(128);
                 if (it >= DAG_WAIT_POLLS ||
-                    ((it & 255) == 0 && globaltimer_ns() - t0 > DAG_WAIT_NS)) {
+                    ((it & 255) == 0 && globaltimer_ns() - t0 > limit)) {
                     set_info(info, -1);
                     atomicExch(&h->abort, 1);
                     ok = 0;
@@ -734,6 +742,7 @@ static __device__ bool task_final(const DagProb &P, DagSmem &sm, DagHdr *h) {
         }
         P.grad[tid] = bad ? nan("") : S + C;
     }
+    dag_signal(P.flag + dag_done_flag(T, 0));
     return true;
 }
 

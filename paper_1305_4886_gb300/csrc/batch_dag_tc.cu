@@ -33,6 +33,8 @@
 
 #include <cuda_fp16.h>
 
+#include <atomic>
+
 namespace gp {
 
 constexpr int QTHREADS = 256;
@@ -1044,6 +1046,7 @@ __device__ bool tc_final(TcCtx &c, const DagProb &P) {
         }
         P.grad[tid] = bad ? nan("") : S + C;
     }
+    dag_signal(P.flag + dag_done_flag(T, 1));
     __syncthreads();
     return true;
 }
@@ -1146,14 +1149,16 @@ __global__ void __launch_bounds__(QTHREADS, 1)
 
 int dag_tc_launch(int grid, DagHdr *hdr, const DagProb *probs, const int2 *list, int ntot,
                   const double *tab, const float2 *dftab, double *scratch, cudaStream_t s) {
-    static bool attr_set[64] = {};
+    // set once per device; a race between host threads only repeats the
+    // (idempotent) attribute call
+    static std::atomic<bool> attr_set[64];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return GP_ERR_CUDA;
-    if (!attr_set[dev]) {
+    if (!attr_set[dev].load(std::memory_order_acquire)) {
         if (cudaFuncSetAttribute(dag_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  QS_DYN) != cudaSuccess)
             return GP_ERR_CUDA;
-        attr_set[dev] = true;
+        attr_set[dev].store(true, std::memory_order_release);
     }
     dag_tc_kernel<<<grid, QTHREADS, QS_DYN, s>>>(hdr, probs, list, ntot, tab, dftab, scratch);
     GP_LAUNCH_CHECK();

@@ -435,8 +435,8 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(int64_t M, int64_t N, int
 // CTAs of the 64 x 64 kernel for the small, latency-bound updates of the
 // diagonal blocks, and four warps per CTA so that one CTA keeps all four FP64
 // sub-pipes of its SM busy.  mask.kchunk > 0 splits K into chunks over
-// grid.z and adds each partial product with FP64 atomics (C must already
-// hold beta C).
+// grid.z and adds each partial product with FP64 atomics: C += alpha A B
+// (beta must be 1; kchunk a multiple of GBK).
 constexpr int SB = 32;
 constexpr int SB_THREADS = 128;
 
@@ -538,9 +538,10 @@ int gemm_f64_ex(int64_t M, int64_t N, int64_t K, double alpha, const double *A, 
             m.out_lower = 1;
             m.diag_off = 0;
         }
-        if (m.kchunk > 0 && beta != 1.0) {
-            if (beta != 0.0) return GP_ERR_INVALID;  // split K accumulates into C
-        }
+        // split K adds every chunk's partial product into C: only C += alpha op(A) op(B)
+        // is expressible, and chunks must start on the kernel's 16-deep K steps (the
+        // triangular start is rounded down to one)
+        if (m.kchunk > 0 && (beta != 1.0 || m.kchunk % GBK != 0)) return GP_ERR_INVALID;
         const int64_t kz = m.kchunk > 0 ? ceil_div(K, m.kchunk) : 1;
         dim3 g((unsigned)ceil_div(M, SB), (unsigned)ceil_div(N, SB), (unsigned)kz);
         gemm_f64_s32_kernel<<<g, SB_THREADS, 0, s>>>(M, N, K, alpha, A, lda, opA, B, ldb, opB, beta, C, ldc,

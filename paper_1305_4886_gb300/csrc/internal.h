@@ -90,5 +90,7 @@ int dag_plan_check(int nprob, const int64_t *h_n, int mixed, int64_t fp64_max_n,
 int64_t dag_fp64_max_n();
 int dag_stats(const void *d_ws, unsigned long long *h_out);
 void dag_set_profile(int on);
+int dag_set_wait_ns(uint64_t ns);
+int dag_set_unset_tile(int prob, int64_t i, int64_t j);
 
 }  // namespace gp

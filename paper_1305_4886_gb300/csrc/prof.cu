@@ -2,9 +2,11 @@
 // for roofline reporting).  Off by default; when enabled, selected launches
 // are bracketed by an event pair recorded on the launch's own stream, and
 // the algorithmic flops / bytes of the launch are tallied per kernel class.
-// Reading the counters synchronises on the recorded events.
+// The event pool grows on demand in blocks of 4096 pairs, up to
+// PROF_MAX_LAUNCHES; launches beyond that are counted as dropped.  Reading
+// the counters synchronises on the recorded events.
+#include <deque>
 #include <mutex>
-#include <vector>
 
 #include "internal.h"
 
@@ -17,22 +19,42 @@ struct Rec {
     double flops = 0.0, bytes = 0.0;
 };
 std::mutex g_mu;
-std::vector<Rec> g_pool;
+std::deque<Rec> g_pool;  // a deque keeps references stable while it grows
 size_t g_used = 0;
 bool g_on = false;
 int64_t g_dropped = 0;
-constexpr size_t POOL = 16384;
+constexpr size_t GROW = 4096;
+constexpr size_t PROF_MAX_LAUNCHES = size_t(1) << 20;
+
+// Adds GROW event pairs; false if the cap is reached or CUDA refuses.
+bool grow_locked() {
+    if (g_pool.size() + GROW > PROF_MAX_LAUNCHES) return false;
+    for (size_t i = 0; i < GROW; ++i) {
+        Rec r;
+        if (cudaEventCreate(&r.a) != cudaSuccess) return false;
+        if (cudaEventCreate(&r.b) != cudaSuccess) {
+            cudaEventDestroy(r.a);
+            return false;
+        }
+        g_pool.push_back(r);
+    }
+    return true;
+}
 }  // namespace
 
 int prof_start(cudaStream_t s) {
     if (!g_on) return -1;
     std::lock_guard<std::mutex> lk(g_mu);
-    if (g_used >= g_pool.size()) {
+    if (g_used >= g_pool.size() && !grow_locked()) {
         ++g_dropped;
         return -1;
     }
     Rec &r = g_pool[g_used];
-    if (cudaEventRecord(r.a, s) != cudaSuccess) return -1;
+    r.cls = -1;  // counted once prof_stop has recorded its end
+    if (cudaEventRecord(r.a, s) != cudaSuccess) {
+        ++g_dropped;
+        return -1;
+    }
     return static_cast<int>(g_used++);
 }
 
@@ -43,7 +65,10 @@ void prof_stop(int idx, cudaStream_t s, int cls, double flops, double bytes) {
     r.cls = cls;
     r.flops = flops;
     r.bytes = bytes;
-    cudaEventRecord(r.b, s);
+    if (cudaEventRecord(r.b, s) != cudaSuccess) {
+        r.cls = -1;  // unusable: left out of the sums
+        ++g_dropped;
+    }
 }
 
 }  // namespace gp
@@ -54,15 +79,7 @@ extern "C" {
 
 int gp_prof_enable(int on) {
     std::lock_guard<std::mutex> lk(g_mu);
-    if (on && g_pool.empty()) {
-        g_pool.resize(POOL);
-        for (auto &r : g_pool) {
-            if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) {
-                g_pool.clear();
-                return GP_ERR_CUDA;
-            }
-        }
-    }
+    if (on && g_pool.empty() && !grow_locked()) return GP_ERR_CUDA;
     g_used = 0;
     g_dropped = 0;
     g_on = on != 0;
@@ -89,6 +106,11 @@ int gp_prof_read(int cls, double *ms_total, int64_t *launches, double *flops, do
     if (flops) *flops = fl;
     if (bytes) *bytes = by;
     return g_dropped ? GP_ERR_WORKSPACE : GP_OK;
+}
+
+int64_t gp_prof_dropped(void) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    return g_dropped;
 }
 
 }  // extern "C"

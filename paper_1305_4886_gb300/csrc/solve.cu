@@ -189,9 +189,11 @@ int lower_matvec(const double *L, int64_t ld, int64_t n, const double *z, double
 }
 
 // ---------------------------------------------------------------------------
-// logdet = 2 sum log L_ii and q = u^T v over i < n, Neumaier-compensated per
-// thread and combined in thread order (deterministic).  out = {loglik,
-// logdet, q, resid}; NaN when *info != 0.
+// logdet = 2 sum log L_ii and q = u^T v over i < n (Sec. 2.2.2).  Each thread
+// keeps Neumaier-compensated sums; the 1024 partial sums are combined by a
+// butterfly of warp shuffles (sum and compensation both), then one warp
+// combines the 32 warp sums the same way: a fixed order, so the result is
+// deterministic.  out = {loglik, logdet, q, resid}; NaN when *info != 0.
 // ---------------------------------------------------------------------------
 struct NSum {
     double s = 0.0, c = 0.0;
@@ -201,28 +203,52 @@ struct NSum {
         else c += (x - t) + s;
         s = t;
     }
+    // adds another compensated sum (its sum with compensation, its compensation plainly)
+    __device__ void merge(double s2, double c2) {
+        add(s2);
+        c += c2;
+    }
     __device__ double get() const { return s + c; }
 };
+
+__device__ __forceinline__ void warp_merge(NSum &x) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const double s2 = __shfl_xor_sync(0xffffffffu, x.s, off);
+        const double c2 = __shfl_xor_sync(0xffffffffu, x.c, off);
+        x.merge(s2, c2);
+    }
+}
 
 __global__ void __launch_bounds__(1024) loglik_reduce_kernel(const double *L, int64_t ld, int64_t n,
                                                              const double *u, const double *v,
                                                              const double *resid, double *out,
                                                              const int64_t *info) {
-    __shared__ double ps[2][1024];
+    __shared__ double ws[4][32];
     NSum a, b;
     for (int64_t i = threadIdx.x; i < n; i += 1024) {
         a.add(log(L[i + i * ld]));
         b.add(u[i] * v[i]);
     }
-    ps[0][threadIdx.x] = a.get();
-    ps[1][threadIdx.x] = b.get();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    warp_merge(a);
+    warp_merge(b);
+    if (lane == 0) {
+        ws[0][warp] = a.s;
+        ws[1][warp] = a.c;
+        ws[2][warp] = b.s;
+        ws[3][warp] = b.c;
+    }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        NSum A, B;
-        for (int t = 0; t < 1024; ++t) {
-            A.add(ps[0][t]);
-            B.add(ps[1][t]);
-        }
+    if (warp != 0) return;
+    NSum A, B;
+    A.s = ws[0][lane];
+    A.c = ws[1][lane];
+    B.s = ws[2][lane];
+    B.c = ws[3][lane];
+    warp_merge(A);
+    warp_merge(B);
+    if (lane == 0) {
         double logdet = 2.0 * A.get(), q = B.get();
         if (*info != 0) {
             out[0] = out[1] = out[2] = out[3] = nan("");

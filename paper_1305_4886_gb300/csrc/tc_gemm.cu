@@ -48,6 +48,8 @@
 #include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
+#include <atomic>
+
 #include "internal.h"
 #include "kern_df.cuh"
 #include "tc_gemm.h"
@@ -905,10 +907,12 @@ int tc_gemm(const TcOperand &A, const TcOperand &B, int64_t M, int64_t N, int64_
     if (normalized && (!A.ex || !B.ex)) return GP_ERR_INVALID;
     if (A.k_off % TC_CHUNK_K || B.k_off % TC_CHUNK_K) return GP_ERR_INVALID;
     // the shared-memory opt-in is per device (setting it twice is harmless)
-    static bool attr_set[64] = {};
+    // set once per device; a race between host threads only repeats the
+    // (idempotent) attribute call
+    static std::atomic<bool> attr_set[64];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return GP_ERR_CUDA;
-    if (!attr_set[dev]) {
+    if (!attr_set[dev].load(std::memory_order_acquire)) {
         if (cudaFuncSetAttribute(tc_gemm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  TC_SMEM) != cudaSuccess ||
             cudaFuncSetAttribute(tc_gemm_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -916,7 +920,7 @@ int tc_gemm(const TcOperand &A, const TcOperand &B, int64_t M, int64_t N, int64_
             cudaFuncSetAttribute(tc_gemm3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  T3_SMEM) != cudaSuccess)
             return GP_ERR_CUDA;
-        attr_set[dev] = true;
+        attr_set[dev].store(true, std::memory_order_release);
     }
     // three slices: the per-group kernel, whose stages carry every slice
     const bool three = A.S == 3;

@@ -13,6 +13,8 @@
 // once per solve; the chain of diagonal products is the only serial part.
 // A wait that gives up (1 s) sets *info = -1 and the CTA returns without
 // publishing.
+#include <mutex>
+
 #include "internal.h"
 #include "tc_ptx.cuh"
 
@@ -240,16 +242,21 @@ int trsv_persist(const double *L, int64_t ld, int64_t n, int trans, double *b, i
     if (cudaMemsetAsync(sync, 0, sizeof(int) * (T + 1), s) != cudaSuccess) return GP_ERR_CUDA;
     const int ev = prof_start(s);
     constexpr int dyn = 2 * PB * (PB + 1) * (int)sizeof(double);
+    // the shared-memory attribute, set once per device (host threads may race here)
+    static std::mutex attr_mu;
     static bool attr_set[64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return GP_ERR_CUDA;
-    if (!attr_set[dev]) {
-        if (cudaFuncSetAttribute(trsv_fwd_persist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 dyn) != cudaSuccess ||
-            cudaFuncSetAttribute(trsv_bwd_persist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 dyn) != cudaSuccess)
-            return GP_ERR_CUDA;
-        attr_set[dev] = true;
+    {
+        std::lock_guard<std::mutex> lk(attr_mu);
+        if (!attr_set[dev]) {
+            if (cudaFuncSetAttribute(trsv_fwd_persist_kernel,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) != cudaSuccess ||
+                cudaFuncSetAttribute(trsv_bwd_persist_kernel,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) != cudaSuccess)
+                return GP_ERR_CUDA;
+            attr_set[dev] = true;
+        }
     }
     if (trans == 0)
         trsv_fwd_persist_kernel<<<(unsigned)T, 256, dyn, s>>>(L, ld, n, b, sync, info, skip);

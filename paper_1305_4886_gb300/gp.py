@@ -39,8 +39,11 @@ SYMBOLS = [
     "gp_launch_count",
     "gp_prof_enable",
     "gp_prof_read",
+    "gp_prof_dropped",
     "gp_batched_profile",
     "gp_batched_task_stats",
+    "gp_batched_set_wait_limit",
+    "gp_batched_test_unset_tile",
     "gp_batched_set_tile_policy",
     "gp_batched_tile_policy",
     "gp_batched_autotune",
@@ -123,10 +126,15 @@ def lib():
                                        ctypes.POINTER(ctypes.c_int64),
                                        ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double)]
+            L.gp_prof_dropped.restype = i64
             L.gp_batched_profile.argtypes = [ci]
             L.gp_batched_profile.restype = None
             L.gp_batched_task_stats.argtypes = [p, ctypes.POINTER(ctypes.c_uint64)]
             L.gp_batched_task_stats.restype = ci
+            L.gp_batched_set_wait_limit.argtypes = [ctypes.c_double]
+            L.gp_batched_set_wait_limit.restype = ci
+            L.gp_batched_test_unset_tile.argtypes = [ci, i64, i64]
+            L.gp_batched_test_unset_tile.restype = ci
             L.gp_batched_set_tile_policy.argtypes = [i64]
             L.gp_batched_set_tile_policy.restype = ci
             L.gp_batched_tile_policy.restype = i64
@@ -329,6 +337,17 @@ def gp_batched_profile(on):
     lib().gp_batched_profile(1 if on else 0)
 
 
+def gp_batched_set_wait_limit(seconds):
+    _check(lib().gp_batched_set_wait_limit(float(seconds)), "gp_batched_set_wait_limit")
+
+
+def gp_batched_test_unset_tile(problem, tile_row=0, tile_col=0):
+    """Testing aid: waits for this Cholesky tile of this problem never succeed
+    (problem = -1 turns it off); see include/gp.h."""
+    _check(lib().gp_batched_test_unset_tile(int(problem), int(tile_row), int(tile_col)),
+           "gp_batched_test_unset_tile")
+
+
 def gp_batched_task_stats(ws):
     """Counters of the last batched call on ws (see gp.h): per task class
     cycles, waiting cycles and task counts, plus tensor-core steps."""
@@ -380,15 +399,21 @@ def gp_prof_enable(on):
 
 
 def gp_prof_read(cls):
-    """(total ms, launches, flops, bytes) of one profiled kernel class."""
+    """(total ms, launches, flops, bytes) of one profiled kernel class.
+    Raises if any profiled launch went unrecorded: partial sums are not
+    returned."""
     c = PROF_CLASSES[cls] if isinstance(cls, str) else int(cls)
     ms, fl, by = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     cnt = ctypes.c_int64()
     st = lib().gp_prof_read(c, ctypes.byref(ms), ctypes.byref(cnt), ctypes.byref(fl),
                             ctypes.byref(by))
-    if st not in (GP_OK, GP_ERR_WORKSPACE):
-        raise GpError(st, "gp_prof_read")
+    _check(st, f"gp_prof_read ({lib().gp_prof_dropped()} launches unrecorded)"
+           if st == GP_ERR_WORKSPACE else "gp_prof_read")
     return ms.value, cnt.value, fl.value, by.value
+
+
+def gp_prof_dropped():
+    return int(lib().gp_prof_dropped())
 
 
 # ---------------------------------------------------------------------------

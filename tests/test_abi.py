@@ -81,3 +81,18 @@ def test_invalid_arguments_rejected_before_any_device_work(libgp):
     assert L.gp_cov_fill(dummy, 200, ctypes.byref(good), 0, dummy, 200, None) == libgp.GP_ERR_INVALID
     assert L.gp_cov_fill(dummy, 200, ctypes.byref(good), 7, dummy, 256, None) == libgp.GP_ERR_INVALID
     assert L.gp_backsolve(dummy, 10, 128, 2, dummy, dummy, None) == libgp.GP_ERR_INVALID
+
+
+def test_wait_limit_and_unset_tile_arguments(libgp):
+    """Host-side settings of the batched launch's bounded waits: the limit's
+    accepted range and the testing aid's tile coordinates."""
+    L = libgp.lib()
+    assert L.gp_batched_set_wait_limit(0.0) == libgp.GP_ERR_INVALID
+    assert L.gp_batched_set_wait_limit(1e-4) == libgp.GP_ERR_INVALID
+    assert L.gp_batched_set_wait_limit(float("nan")) == libgp.GP_ERR_INVALID
+    assert L.gp_batched_set_wait_limit(601.0) == libgp.GP_ERR_INVALID
+    assert L.gp_batched_set_wait_limit(20.0) == libgp.GP_OK
+    assert L.gp_batched_test_unset_tile(0, 1, 2) == libgp.GP_ERR_INVALID  # above the diagonal
+    assert L.gp_batched_test_unset_tile(0, 3, -1) == libgp.GP_ERR_INVALID
+    assert L.gp_batched_test_unset_tile(2, 3, 1) == libgp.GP_OK
+    assert L.gp_batched_test_unset_tile(-1, 0, 0) == libgp.GP_OK

@@ -22,18 +22,22 @@ def test_digest_ignores_comments_and_blank_lines(tmp_path):
     assert bench.source_digest(a) != bench.source_digest(c)
 
 
-def test_traffic_profile_is_well_formed():
-    path = os.path.join(bench.ROOT, "profiles", "tc_gemm3_kernel_traffic.md")
-    vals = {}
-    for line in open(path):
-        if line.startswith("- ") and ":" in line:
-            k, v = line[2:].split(":", 1)
-            vals[k.strip()] = v.strip().strip("`")
-    assert len(vals["tc_gemm.cu code sha256 prefix"]) == 16
-    assert float(vals["bytes per slice-product flop (mixed_f16)"]) > 0
-    # when the code matches, the lookup scales the ratio by the flops
-    t = bench.contraction_traffic(2.0e12, "mixed_f16")
-    if t is not None:
-        ratio = float(vals["bytes per slice-product flop (mixed_f16)"])
-        assert abs(t["bytes_per_launch"] - 2.0e12 * ratio) < 1.0
-    assert bench.contraction_traffic(2.0e12, "fp64") is None
+def test_traffic_lookup(tmp_path):
+    import json
+    src = _write(tmp_path / "k.cu", "int f() { return 1; }\n")
+    rec = {"n": 64, "bytes_per_slice_flop": {"mixed_f16": 2.5e-3},
+           "tc_gemm_code_sha256_prefix": bench.source_digest(src)}
+    path = _write(tmp_path / "t.json", json.dumps(rec))
+    t = bench.contraction_traffic(2.0e12, "mixed_f16", path=path, src=src)
+    assert abs(t["bytes_per_launch"] - 5.0e9) < 1.0
+    # another precision, or a changed kernel: no figure
+    assert bench.contraction_traffic(2.0e12, "emu_fp64", path=path, src=src) is None
+    _write(tmp_path / "k.cu", "int f() { return 2; }\n")
+    assert bench.contraction_traffic(2.0e12, "mixed_f16", path=path, src=src) is None
+
+
+def test_committed_traffic_record_is_well_formed():
+    import json
+    rec = json.load(open(bench.TRAFFIC_FILE))
+    assert len(rec["tc_gemm_code_sha256_prefix"]) == 16
+    assert float(rec["bytes_per_slice_flop"]["mixed_f16"]) > 0
