@@ -21,6 +21,9 @@ from .gp_oracle import (  # noqa: F401
     kernel_dlogrho,
     num_threads,
     set_threads,
+    cross_cov,
+    predict,
+    predict_from_data,
     OracleNotPD,
     KERNELS,
 )

@@ -368,3 +368,59 @@ int orc_loglik_grad(const double *x, const double *y, const double *mu, int64_t 
     free(part); free(L); free(W); free(C); free(D); free(a);
     return ORC_OK;
 }
+
+/*
+ * Kriging prediction (Sec. 1: prediction at new locations is the conditional
+ * expectation of the latent process given the data, with its variance;
+ * Sec. 2.2.2: it reuses the Cholesky factor through forward and back
+ * solves; Sec. 4.3: predictions with standard errors on a grid).  For new
+ * locations xs_1..xs_m (latent process Z, so no nugget between a new and a
+ * training point):
+ *   cross covariance  K_ij = s2 k(|x_i - xs_j| / rho)            (n x m)
+ *   mean              m_j  = mu_new + sum_i K_ij alpha_i,  alpha = C^{-1}(y - mu)
+ *   variance          v_j  = s2 - w_j^T w_j,  w_j = L^{-1} K_.j,
+ * i.e. s2 - K_.j^T C^{-1} K_.j, the Schur complement of C in the joint
+ * covariance of (Y, Z(xs_j)).
+ */
+static double dist2d_pair(const double *x, int64_t i, const double *xs, int64_t j) {
+    double dx = x[2 * i] - xs[2 * j];
+    double dy = x[2 * i + 1] - xs[2 * j + 1];
+    return sqrt(dx * dx + dy * dy);
+}
+
+/* K (n x m, row-major): K[i * m + j] = s2 k(|x_i - xs_j| / rho) */
+void orc_cross_cov(const double *x, int64_t n, const double *xs, int64_t m, int kind, double s2,
+                   double rho, double *K) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < m; ++j)
+            K[i * m + j] = s2 * orc_kernel(kind, dist2d_pair(x, i, xs, j) / rho);
+}
+
+/*
+ * mean (m) and, when var is not NULL, variance (m) at the new locations,
+ * given the factor L (n x n row-major, lower) and alpha = C^{-1}(y - mu) of
+ * the training data.  Each new location is independent of the others.
+ */
+void orc_predict(const double *x, int64_t n, const double *xs, int64_t m, int kind, double s2,
+                 double rho, const double *L, const double *alpha, double mu_new, double *mean,
+                 double *var) {
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t j = 0; j < m; ++j) {
+        double *k = (double *)malloc(sizeof(double) * (size_t)n);
+        double *w = (double *)malloc(sizeof(double) * (size_t)n);
+        nsum_t s;
+        ns_init(&s);
+        for (int64_t i = 0; i < n; ++i) {
+            k[i] = s2 * orc_kernel(kind, dist2d_pair(x, i, xs, j) / rho);
+            ns_add(&s, k[i] * alpha[i]);
+        }
+        mean[j] = mu_new + ns_get(&s);
+        if (var) {
+            orc_forward(L, n, k, w);
+            var[j] = s2 - orc_dot(w, w, n);
+        }
+        free(k);
+        free(w);
+    }
+}

@@ -79,6 +79,8 @@ def _load():
             lib.orc_loglik.restype = ci
             lib.orc_loglik_grad.argtypes = [p, p, p, i64, ci, d, d, d, p, p, p, p]
             lib.orc_loglik_grad.restype = ci
+            lib.orc_cross_cov.argtypes = [p, i64, p, i64, ci, d, d, p]
+            lib.orc_predict.argtypes = [p, i64, p, i64, ci, d, d, p, p, d, p, p]
             lib.orc_num_threads.restype = ci
             lib.orc_set_threads.argtypes = [ci]
             _lib = lib
@@ -245,3 +247,31 @@ def loglik_grad(x, y, kernel, s2, rho, tau2, mu=None):
     if st == 1:
         raise OracleNotPD(int(info.value))
     return dict(loglik=out[0], logdet=out[1], quad=out[2], alpha=alpha, grad=grad)
+
+
+def cross_cov(x, xs, kernel, s2, rho):
+    """Cross covariance K (n x m): K[i, j] = s2 k(|x_i - xs_j| / rho)."""
+    x = _f64(x)
+    xs = _f64(xs)
+    K = np.empty((x.shape[0], xs.shape[0]))
+    _load().orc_cross_cov(_ptr(x), x.shape[0], _ptr(xs), xs.shape[0], _kind(kernel), s2, rho,
+                          _ptr(K))
+    return K
+
+
+def predict(x, xs, kernel, s2, rho, L, alpha, mu_new=0.0, want_var=True):
+    """Kriging mean (and variance) at new locations xs from the training
+    factor L and alpha = C^{-1}(y - mu): dict(mean, var)."""
+    x, xs, L, alpha = _f64(x), _f64(xs), _f64(L), _f64(alpha)
+    m = xs.shape[0]
+    mean = np.empty(m)
+    var = np.empty(m) if want_var else None
+    _load().orc_predict(_ptr(x), x.shape[0], _ptr(xs), m, _kind(kernel), s2, rho, _ptr(L),
+                        _ptr(alpha), float(mu_new), _ptr(mean), _ptr(var) if want_var else None)
+    return dict(mean=mean, var=var)
+
+
+def predict_from_data(x, y, xs, kernel, s2, rho, tau2, mu=None, mu_new=0.0, want_var=True):
+    """Factor the training covariance, solve for alpha, then predict."""
+    r = loglik(x, y, kernel, s2, rho, tau2, mu=mu, want_L=True)
+    return predict(x, xs, kernel, s2, rho, r["L"], r["alpha"], mu_new, want_var)
