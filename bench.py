@@ -76,6 +76,11 @@ def parse():
                     help="timed evaluations of the FP64-grade form")
     ap.add_argument("--batched-steps", type=int, default=10,
                     help="timed graph replays of the batched workload")
+    ap.add_argument("--case", default=None,
+                    choices=["fill", "loglik", "loglik_grad", "syrk", "predict"],
+                    help="run one small invocation of a single step (--n, --precision, --reps) "
+                         "for kernel captures, print its CUDA-event times, then exit")
+    ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--cpu-plan", default=None,
                     help="comma-separated n: time the oracle (all cores and one thread) "
                          "and LAPACK's Cholesky at each n, then exit")
@@ -792,6 +797,67 @@ def run_batched(args, rank, world, local):
     return 0
 
 
+def run_case(args):
+    """One step of the path on its own, --reps times, on the config-3 recipe
+    at --n: the case a kernel capture (ncu) runs.  Prints one JSON line with
+    the CUDA-event time of each repetition."""
+    import torch
+
+    from paper_1305_4886_gb300 import gp, inputs
+    n, prec = args.n, args.precision
+    p = inputs.config3(n)
+    prm = gp.params(p.kernel, p.s2, p.rho, p.tau2)
+    x = torch.as_tensor(p.x, device="cuda")
+    z = torch.as_tensor(p.z, device="cuda")
+    np_ = gp.gp_padded_order(n)
+    info = torch.zeros(1, dtype=torch.int64, device="cuda")
+    if args.case == "fill":
+        C = torch.empty(np_ * np_, dtype=torch.float64, device="cuda")
+        fn = lambda: gp.gp_cov_fill(x, prm, C, np_, precision=prec)  # noqa: E731
+        work = {"bytes": 8.0 * np_ * (np_ + 64) / 2}
+    elif args.case in ("loglik", "loglik_grad"):
+        ws = gp.workspace(n, prec, want_grad=args.case == "loglik_grad")
+        if args.case == "loglik":
+            fn = lambda: gp.loglik(x, z, p.kernel, p.s2, p.rho, p.tau2, precision=prec, ws=ws)  # noqa: E731
+        else:
+            fn = lambda: gp.loglik_grad(x, z, p.kernel, p.s2, p.rho, p.tau2, precision=prec, ws=ws)  # noqa: E731
+        work = {"flop": n ** 3 / 3.0 if args.case == "loglik" else float(n) ** 3}
+    elif args.case == "syrk":
+        # one trailing update C -= P P^T with P n x 512 (a Cholesky step)
+        P = torch.randn(512 * n, dtype=torch.float64, device="cuda")
+        C = torch.zeros(n * n, dtype=torch.float64, device="cuda")
+        ws = torch.empty(max(1, gp.gp_syrk_workspace_bytes(n, 512, prec)), dtype=torch.uint8,
+                         device="cuda")
+        fn = lambda: gp.gp_syrk_lower(C, n, P, n, n, 512, prec, ws, info)  # noqa: E731
+        work = {"flop": float(n) * n * 512}
+    else:
+        m = max(1, n // 2)
+        xs = torch.as_tensor(inputs.uniform_points(m, 4242), device="cuda")
+        lk = gp.loglik(x, z, p.kernel, p.s2, p.rho, p.tau2, precision=prec)
+        mean = torch.empty(m, dtype=torch.float64, device="cuda")
+        var = torch.empty(m, dtype=torch.float64, device="cuda")
+        pws = torch.empty(gp.gp_predict_workspace_bytes(n, m, True), dtype=torch.uint8,
+                          device="cuda")
+        L = lk["ws"][: np_ * np_ * 8].view(torch.float64)
+        fn = lambda: gp.gp_predict(x, n, xs, m, prm, lk["alpha"], L, np_, 0.0, mean, var, pws,  # noqa: E731
+                                   info)
+        work = {"flop": float(np_) * np_ * m, "m": m}
+    times = []
+    for _ in range(max(1, args.reps)):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    if int(info.item()) != 0:
+        raise RuntimeError(f"case {args.case} failed, info={int(info.item())}")
+    print(json.dumps({"case": args.case, "n": n, "precision": prec, "ms": times, **work}),
+          flush=True)
+    return 0
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -801,6 +867,8 @@ def main():
         return run_cpu_plan(args) if rank == 0 else 0
     if args.accuracy:
         return run_accuracy(args) if rank == 0 else 0
+    if args.case:
+        return run_case(args) if rank == 0 else 0
     if args.workload == "batched":
         return run_batched(args, rank, world, local)
     return run_ours(args, rank, world, local)

@@ -258,6 +258,34 @@ int gp_batched_autotune(int nprob, const int64_t *h_n, const double *const *h_dx
                         double *d_out, double *d_grad, int64_t *d_info, void *stream,
                         int64_t *h_choice, double *h_ms, int *h_ncand);
 
+/* Kriging prediction at m new locations (Sec. 1: prediction is the
+ * conditional expectation of the latent process given the data, with its
+ * variance; Sec. 2.2.2: the Cholesky factor is reused through triangular
+ * solves; Sec. 4.3: predictions with standard errors on a grid), from a
+ * previous gp_loglik / gp_loglik_grad of the same training data and
+ * parameters:
+ *   d_x (n x 2) training locations, d_xnew (m x 2) new locations, both
+ *   interleaved; d_alpha (n) = C^{-1}(y - mu) as returned by gp_loglik;
+ *   mu_new: the (constant) mean at the new locations.
+ *   d_mean (m):  mu_new + sum_i K_ij alpha_i,  K_ij = sigma2 k(|x_i - xnew_j| / rho)
+ *                (no nugget between a new and a training location: the
+ *                prediction is of the latent process).  Matrix-free, FP64
+ *                kernel evaluations, compensated sums.
+ *   d_var (m, nullable): sigma2 - K_.j^T C^{-1} K_.j = sigma2 - |L^{-1} K_.j|^2
+ *                (the variance of the latent process at xnew_j given the
+ *                data; its square root is the standard error).  Needs d_L:
+ *                the factor as gp_loglik leaves it at the start of its
+ *                workspace (n_p x n_p, column-major, lower, ld = ldl >= n_p,
+ *                identity padding), and d_ws of gp_predict_workspace_bytes(n,
+ *                m, 1) bytes (0 when d_var is NULL: d_L and d_ws may then be
+ *                NULL).  FP64 on the CUDA cores: n_p^2 m flops.
+ * Non-finite locations set *d_info = -2; after any device-side failure
+ * every output is NaN.                                                    */
+size_t gp_predict_workspace_bytes(int64_t n, int64_t m, int want_var);
+int gp_predict(const double *d_x, int64_t n, const double *d_xnew, int64_t m, const gp_params *prm,
+               const double *d_alpha, const double *d_L, int64_t ldl, double mu_new, double *d_mean,
+               double *d_var, void *d_ws, size_t ws_bytes, int64_t *d_info, void *stream);
+
 /* Log-likelihood without any workspace or allocation (GP_FP64 only).  The
  * paper has no counterpart: this entry point serves callers that cannot
  * allocate device memory when they need a log-likelihood -- code running

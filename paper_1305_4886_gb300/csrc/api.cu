@@ -459,6 +459,26 @@ int gp_batched_task_stats(const void *d_ws, unsigned long long *h_out) {
     return dag_stats(d_ws, h_out);
 }
 
+size_t gp_predict_workspace_bytes(int64_t n, int64_t m, int want_var) {
+    if (n < 1 || m < 1) return 0;
+    return predict_ws_bytes(n, m, want_var);
+}
+
+int gp_predict(const double *d_x, int64_t n, const double *d_xnew, int64_t m, const gp_params *prm,
+               const double *d_alpha, const double *d_L, int64_t ldl, double mu_new, double *d_mean,
+               double *d_var, void *d_ws, size_t ws_bytes, int64_t *d_info, void *stream) {
+    if (n < 1 || m < 1 || !d_x || !d_xnew || !d_alpha || !d_mean || !d_info || !params_ok(prm) ||
+        !isfinite(mu_new))
+        return GP_ERR_INVALID;
+    if (d_var) {
+        if (!d_L || ldl < padded(n)) return GP_ERR_INVALID;
+        if (!d_ws || ws_bytes < predict_ws_bytes(n, m, 1)) return GP_ERR_WORKSPACE;
+    }
+    KernParams kp = make_kern(*prm);
+    return predict_run(d_x, n, d_xnew, m, kp, d_alpha, d_L, ldl, mu_new, d_mean, d_var, d_ws, d_info,
+                       (cudaStream_t)stream);
+}
+
 size_t gp_syrk_workspace_bytes(int64_t m, int64_t k, int precision) {
     if (m < 1 || k < 1 || !precision_ok(precision)) return 0;
     return syrk_ws_bytes(m, k, precision, slices_of(precision));

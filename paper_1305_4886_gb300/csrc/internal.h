@@ -78,6 +78,12 @@ int refine_alpha(const double *d_x, int64_t n, int64_t np, const KernParams &kp,
                  double *stats, int *conv, int *tsync, int max_evals, double tol, int64_t *info,
                  cudaStream_t st);
 
+// predict.cu (kriging mean and variance at new locations)
+size_t predict_ws_bytes(int64_t n, int64_t m, int want_var);
+int predict_run(const double *d_x, int64_t n, const double *d_xs, int64_t m, const KernParams &kp,
+                const double *d_alpha, const double *d_L, int64_t ldl, double mu_new,
+                double *d_mean, double *d_var, void *d_ws, int64_t *d_info, cudaStream_t s);
+
 // batch_dag.cu / batch_dag_tc.cu (the batched evaluation as one persistent task-graph launch)
 size_t dag_workspace_bytes(int nprob, const int64_t *h_n, int mixed);
 int dag_run(int nprob, const int64_t *h_n, const double *const *h_dx, const double *const *h_dy,

@@ -33,6 +33,8 @@ SYMBOLS = [
     "gp_loglik_grad",
     "gp_batched_workspace_bytes",
     "gp_loglik_grad_batched",
+    "gp_predict_workspace_bytes",
+    "gp_predict",
     "gp_loglik_noalloc",
     "gp_syrk_workspace_bytes",
     "gp_syrk_lower",
@@ -115,6 +117,11 @@ def lib():
             L.gp_batched_workspace_bytes.restype = sz
             L.gp_loglik_grad_batched.argtypes = [ci, p, p, p, p, p, ci, p, sz, p, p, p, p]
             L.gp_loglik_grad_batched.restype = ci
+            L.gp_predict_workspace_bytes.argtypes = [i64, i64, ci]
+            L.gp_predict_workspace_bytes.restype = sz
+            L.gp_predict.argtypes = [p, i64, p, i64, PP, p, p, i64, ctypes.c_double, p, p, p, sz,
+                                     p, p]
+            L.gp_predict.restype = ci
             L.gp_loglik_noalloc.argtypes = [p, p, p, i64, PP, p, p, p, p]
             L.gp_loglik_noalloc.restype = ci
             L.gp_syrk_workspace_bytes.argtypes = [i64, i64, ci]
@@ -358,6 +365,44 @@ def gp_batched_task_stats(ws):
            for q, name in enumerate(BATCH_TASK_CLASSES)}
     out["steps"] = v[30]
     return out
+
+
+def gp_predict_workspace_bytes(n, m, want_var=True):
+    return lib().gp_predict_workspace_bytes(int(n), int(m), int(bool(want_var)))
+
+
+def gp_predict(x, n, xnew, m, prm, alpha, L, ldl, mu_new, mean, var, ws, info, stream=None):
+    wsb = 0 if ws is None else ws.numel() * ws.element_size()
+    _check(lib().gp_predict(_f64(x), int(n), _f64(xnew), int(m), ctypes.byref(prm), _f64(alpha),
+                            _f64(L), int(ldl), float(mu_new), _f64(mean), _f64(var), _ptr(ws), wsb,
+                            _ptr(info), _stream(stream)), "gp_predict")
+
+
+def predict(x, y, xnew, kernel, sigma2, rho, tau2, mu=None, mu_new=None, precision="fp64",
+            want_var=True, check=True):
+    """Kriging prediction on the device: one gp_loglik (its factor and alpha),
+    then gp_predict.  mu / mu_new: constant means (mu_new defaults to mu).
+    Returns dict of device tensors {mean, var (or None), loglik}."""
+    n, m = x.shape[0], xnew.shape[0]
+    r = loglik(x, y, kernel, sigma2, rho, tau2, mu=mu, precision=precision, check=check)
+    dev = x.device
+    np_ = gp_padded_order(n)
+    mean = torch.empty(m, dtype=torch.float64, device=dev)
+    var = torch.empty(m, dtype=torch.float64, device=dev) if want_var else None
+    ws = None
+    if want_var:
+        ws = torch.empty(max(1, gp_predict_workspace_bytes(n, m, True)), dtype=torch.uint8,
+                         device=dev)
+    info = torch.zeros(1, dtype=torch.int64, device=dev)
+    L = r["ws"][: np_ * np_ * 8].view(torch.float64) if want_var else None
+    mn = float(mu_new) if mu_new is not None else (0.0 if mu is None else float(mu))
+    gp_predict(x, n, xnew, m, params(kernel, sigma2, rho, tau2), r["alpha"], L, np_, mn, mean,
+               var, ws, info)
+    if check:
+        iv = int(info.item())
+        if iv != 0:
+            raise GpDeviceError(iv)
+    return dict(mean=mean, var=var, loglik=r["out"][0])
 
 
 def gp_loglik_noalloc(x, y, mu, n, prm, out, alpha, info, stream=None):

@@ -96,3 +96,18 @@ def test_wait_limit_and_unset_tile_arguments(libgp):
     assert L.gp_batched_test_unset_tile(0, 3, -1) == libgp.GP_ERR_INVALID
     assert L.gp_batched_test_unset_tile(2, 3, 1) == libgp.GP_OK
     assert L.gp_batched_test_unset_tile(-1, 0, 0) == libgp.GP_OK
+
+
+def test_predict_arguments(libgp):
+    L = libgp.lib()
+    prm = libgp.params("exp", 1.0, 0.1, 0.1)
+    d = ctypes.c_void_p(16)
+    call = lambda n, m, Lp, ldl, var, ws, wsb: L.gp_predict(  # noqa: E731
+        d, n, d, m, ctypes.byref(prm), d, Lp, ldl, 0.0, d, var, ws, wsb, d, None)
+    assert call(0, 5, None, 0, None, None, 0) == libgp.GP_ERR_INVALID
+    assert call(10, 0, None, 0, None, None, 0) == libgp.GP_ERR_INVALID
+    assert call(10, 5, None, 128, d, d, 1 << 30) == libgp.GP_ERR_INVALID  # variance needs L
+    assert call(10, 5, d, 64, d, d, 1 << 30) == libgp.GP_ERR_INVALID       # ld below n_p
+    assert call(10, 5, d, 128, d, d, 16) == libgp.GP_ERR_WORKSPACE
+    assert libgp.gp_predict_workspace_bytes(10, 5, False) == 0
+    assert libgp.gp_predict_workspace_bytes(10, 5, True) > 128 * 5 * 8

@@ -4,7 +4,7 @@ pending updates.  Checked against FP64 references at FP64-class tolerances:
   trailing update   |err_ij| <= 3e-11 (|P| |P|^T)_ij   (2^-40 of the row maxima,
                     which can be ~10x the typical entry)
   loglik            1e-10 relative (the FP64 bound)
-  gradient          1e-8 relative (infinity norm)
+  gradient          1e-9 relative (infinity norm; the FP64 bound)
 """
 import numpy as np
 import pytest
@@ -55,7 +55,7 @@ def test_emu_loglik_grad_matches_oracle(g, orc, n, kern):
     out = r["out"].cpu().numpy()
     assert rel_err(out[0], ref["loglik"]) < 1e-10
     gerr = np.max(np.abs(r["grad"].cpu().numpy() - ref["grad"])) / np.max(np.abs(ref["grad"]))
-    assert gerr < 1e-8, gerr
+    assert gerr < 1e-9, gerr
     assert rel_norm(r["alpha"].cpu().numpy(), ref["alpha"]) < 1e-10
 
 
@@ -68,4 +68,4 @@ def test_emu_clustered_matches_fp64_path(g):
     b = g.loglik_grad(x, z, p.kernel, p.s2, p.rho, p.tau2, precision="emu_fp64")
     assert rel_err(float(b["out"][0]), float(a["out"][0])) < 1e-10
     ga, gb = a["grad"].cpu().numpy(), b["grad"].cpu().numpy()
-    assert np.max(np.abs(ga - gb)) / np.max(np.abs(ga)) < 1e-8
+    assert np.max(np.abs(ga - gb)) / np.max(np.abs(ga)) < 1e-9
