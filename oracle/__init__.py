@@ -24,6 +24,10 @@ from .gp_oracle import (  # noqa: F401
     cross_cov,
     predict,
     predict_from_data,
+    philox4x64,
+    normals,
+    simulate,
+    simulate_conditional,
     OracleNotPD,
     KERNELS,
 )

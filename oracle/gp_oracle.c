@@ -424,3 +424,139 @@ void orc_predict(const double *x, int64_t n, const double *xs, int64_t m, int ki
         free(w);
     }
 }
+
+/*
+ * Simulation (Sec. 1: unconditional realisations and realisations
+ * conditional on the data; Sec. 2.3.2: multiplication of the Cholesky factor
+ * by a matrix of standard normals; Sec. 4.3: 1000 posterior realisations).
+ *
+ * Random numbers come from the counter-based generator Philox4x64-10
+ * (Salmon, Moraes, Dror and Shaw, "Parallel random numbers: as easy as
+ * 1, 2, 3", SC 2011): ten rounds on a 4 x 64-bit counter with a 2 x 64-bit
+ * key; each round multiplies words 0 and 2 by the round constants, keeps
+ * the high and low halves, and mixes in the other words and the key, which
+ * is bumped by the Weyl constants between rounds.  The paper's package uses
+ * another parallel generator (L'Ecuyer's, through rlecuyer); the draws
+ * here are defined by this generator instead:
+ *   for realisation c (0-based, offset by `first`) and rows 4q .. 4q+3,
+ *   (w0, w1, w2, w3) = philox(counter = (q, first + c, stream, 0),
+ *                             key = (seed, 0)),
+ *   u_k = ((w_k >> 11) + 1/2) 2^-53, in (0, 1),
+ *   z_{4q} = s0 cos(2 pi u1),  z_{4q+1} = s0 sin(2 pi u1),  s0 = sqrt(-2 ln u0),
+ *   z_{4q+2} = s2 cos(2 pi u3), z_{4q+3} = s2 sin(2 pi u3), s2 = sqrt(-2 ln u2)
+ * (the Box-Muller transform).
+ */
+void orc_philox4x64(const uint64_t *ctr, const uint64_t *key, uint64_t *out) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+    uint64_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint64_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        const unsigned __int128 p0 = (unsigned __int128)M0 * x0;
+        const unsigned __int128 p1 = (unsigned __int128)M1 * x2;
+        const uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+        const uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+        const uint64_t y0 = hi1 ^ x1 ^ k0, y1 = lo1, y2 = hi0 ^ x3 ^ k1, y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+        k0 += W0;
+        k1 += W1;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+static double u01(uint64_t w) { return ((double)(w >> 11) + 0.5) * (1.0 / 9007199254740992.0); }
+
+/* out[c * n + i] = z_i of realisation first + c, i < n, c < r */
+void orc_normals(int64_t n, int64_t r, uint64_t seed, uint64_t stream, uint64_t first, double *out) {
+    const double TWO_PI = 6.283185307179586476925286766559;
+#pragma omp parallel for schedule(static)
+    for (int64_t c = 0; c < r; ++c) {
+        for (int64_t q = 0; 4 * q < n; ++q) {
+            uint64_t ctr[4] = {(uint64_t)q, first + (uint64_t)c, stream, 0};
+            uint64_t key[2] = {seed, 0};
+            uint64_t w[4];
+            double z[4];
+            orc_philox4x64(ctr, key, w);
+            const double s0 = sqrt(-2.0 * log(u01(w[0]))), s2 = sqrt(-2.0 * log(u01(w[2])));
+            z[0] = s0 * cos(TWO_PI * u01(w[1]));
+            z[1] = s0 * sin(TWO_PI * u01(w[1]));
+            z[2] = s2 * cos(TWO_PI * u01(w[3]));
+            z[3] = s2 * sin(TWO_PI * u01(w[3]));
+            for (int k = 0; k < 4 && 4 * q + k < n; ++k) out[c * n + 4 * q + k] = z[k];
+        }
+    }
+}
+
+/* Unconditional realisations: out[c * n + i] = mu + (L e_c)_i, e_c the normals
+ * of realisation first + c (stream 0).  L: n x n row-major lower factor. */
+void orc_simulate(const double *L, int64_t n, int64_t r, uint64_t seed, uint64_t first, double mu,
+                  double *out) {
+    double *E = (double *)malloc(sizeof(double) * (size_t)n * (size_t)r);
+    orc_normals(n, r, seed, 0, first, E);
+#pragma omp parallel for schedule(static)
+    for (int64_t c = 0; c < r; ++c) {
+        for (int64_t i = 0; i < n; ++i) {
+            double t = 0.0;
+            for (int64_t k = 0; k <= i; ++k) t += L[i * n + k] * E[c * n + k];
+            out[c * n + i] = mu + t;
+        }
+    }
+    free(E);
+}
+
+/*
+ * Realisations of the latent process at m new locations conditional on the
+ * data (posterior draws): with K the n x m cross covariance, W = L^{-1} K and
+ * K** the m x m covariance of the new locations (no nugget),
+ *   S  = K** - W^T W           (posterior covariance)
+ *   S  = L* L*^T               (unpivoted Cholesky: a pivot <= 0 fails, Sec. 5)
+ *   out[c * m + j] = mean_j + (L* e_c)_j,  e_c the normals of realisation
+ *   first + c in stream 1, mean as orc_predict.
+ * Returns ORC_OK, or ORC_NOT_PD with *info = failing column + 1.
+ */
+int orc_simulate_conditional(const double *x, int64_t n, const double *xs, int64_t m, int kind,
+                             double s2, double rho, const double *L, const double *alpha,
+                             double mu_new, int64_t r, uint64_t seed, uint64_t first, double *out,
+                             int64_t *info) {
+    double *K = (double *)malloc(sizeof(double) * (size_t)n * (size_t)m);
+    double *W = (double *)malloc(sizeof(double) * (size_t)n * (size_t)m);  /* W[j * n + i] */
+    double *S = (double *)malloc(sizeof(double) * (size_t)m * (size_t)m);
+    double *mean = (double *)malloc(sizeof(double) * (size_t)m);
+    double *E = (double *)malloc(sizeof(double) * (size_t)m * (size_t)r);
+    int st = ORC_OK;
+    *info = 0;
+    orc_cross_cov(x, n, xs, m, kind, s2, rho, K);
+    orc_predict(x, n, xs, m, kind, s2, rho, L, alpha, mu_new, mean, NULL);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t j = 0; j < m; ++j) {
+        double *kc = (double *)malloc(sizeof(double) * (size_t)n);
+        for (int64_t i = 0; i < n; ++i) kc[i] = K[i * m + j];
+        orc_forward(L, n, kc, W + j * n);
+        free(kc);
+    }
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t a = 0; a < m; ++a) {
+        for (int64_t b = 0; b < m; ++b) {
+            const double kab = (a == b) ? s2 : s2 * orc_kernel(kind, dist2d(xs, a, b) / rho);
+            S[a * m + b] = kab - orc_dot(W + a * n, W + b * n, n);
+        }
+    }
+    const int64_t f = orc_cholesky(S, m);
+    if (f != 0) {
+        *info = f;
+        for (int64_t i = 0; i < m * r; ++i) out[i] = NAN;
+        st = ORC_NOT_PD;
+    } else {
+        orc_normals(m, r, seed, 1, first, E);
+#pragma omp parallel for schedule(static)
+        for (int64_t c = 0; c < r; ++c) {
+            for (int64_t j = 0; j < m; ++j) {
+                double t = 0.0;
+                for (int64_t k = 0; k <= j; ++k) t += S[j * m + k] * E[c * m + k];
+                out[c * m + j] = mean[j] + t;
+            }
+        }
+    }
+    free(K); free(W); free(S); free(mean); free(E);
+    return st;
+}

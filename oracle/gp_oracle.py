@@ -81,6 +81,13 @@ def _load():
             lib.orc_loglik_grad.restype = ci
             lib.orc_cross_cov.argtypes = [p, i64, p, i64, ci, d, d, p]
             lib.orc_predict.argtypes = [p, i64, p, i64, ci, d, d, p, p, d, p, p]
+            u64 = ctypes.c_uint64
+            lib.orc_philox4x64.argtypes = [p, p, p]
+            lib.orc_normals.argtypes = [i64, i64, u64, u64, u64, p]
+            lib.orc_simulate.argtypes = [p, i64, i64, u64, u64, d, p]
+            lib.orc_simulate_conditional.argtypes = [p, i64, p, i64, ci, d, d, p, p, d, i64, u64,
+                                                     u64, p, p]
+            lib.orc_simulate_conditional.restype = ci
             lib.orc_num_threads.restype = ci
             lib.orc_set_threads.argtypes = [ci]
             _lib = lib
@@ -275,3 +282,45 @@ def predict_from_data(x, y, xs, kernel, s2, rho, tau2, mu=None, mu_new=0.0, want
     """Factor the training covariance, solve for alpha, then predict."""
     r = loglik(x, y, kernel, s2, rho, tau2, mu=mu, want_L=True)
     return predict(x, xs, kernel, s2, rho, r["L"], r["alpha"], mu_new, want_var)
+
+
+def philox4x64(counter, key):
+    """Philox4x64-10 of one 4-word counter and 2-word key: 4 uint64 words."""
+    c = np.ascontiguousarray(counter, dtype=np.uint64)
+    k = np.ascontiguousarray(key, dtype=np.uint64)
+    out = np.empty(4, dtype=np.uint64)
+    _load().orc_philox4x64(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def normals(n, r, seed, stream=0, first=0):
+    """Standard normals of the simulation, shape (r, n): row c is realisation
+    first + c of the given stream."""
+    out = np.empty((r, n))
+    _load().orc_normals(int(n), int(r), int(seed), int(stream), int(first), _ptr(out))
+    return out
+
+
+def simulate(L, r, seed, first=0, mu=0.0):
+    """Unconditional realisations mu + L e_c, shape (r, n)."""
+    L = _f64(L)
+    n = L.shape[0]
+    out = np.empty((r, n))
+    _load().orc_simulate(_ptr(L), n, int(r), int(seed), int(first), float(mu), _ptr(out))
+    return out
+
+
+def simulate_conditional(x, xs, kernel, s2, rho, L, alpha, r, seed, first=0, mu_new=0.0):
+    """Posterior realisations of the latent process at xs, shape (r, m).
+    Raises OracleNotPD when the posterior covariance is not numerically
+    positive definite."""
+    x, xs, L, alpha = _f64(x), _f64(xs), _f64(L), _f64(alpha)
+    m = xs.shape[0]
+    out = np.empty((r, m))
+    info = ctypes.c_int64(0)
+    st = _load().orc_simulate_conditional(_ptr(x), x.shape[0], _ptr(xs), m, _kind(kernel), s2, rho,
+                                          _ptr(L), _ptr(alpha), float(mu_new), int(r), int(seed),
+                                          int(first), _ptr(out), ctypes.byref(info))
+    if st == 1:
+        raise OracleNotPD(int(info.value))
+    return out
