@@ -286,6 +286,56 @@ int gp_predict(const double *d_x, int64_t n, const double *d_xnew, int64_t m, co
                const double *d_alpha, const double *d_L, int64_t ldl, double mu_new, double *d_mean,
                double *d_var, void *d_ws, size_t ws_bytes, int64_t *d_info, void *stream);
 
+/* ---- simulation (Sec. 1: unconditional realisations and realisations
+ * conditional on the data; Sec. 2.3.2: the Cholesky factor times standard
+ * normals; Sec. 4.3: posterior realisations on the prediction grid) ------
+ *
+ * Standard normals: Philox4x64-10 (Salmon et al., SC 2011), a counter-based
+ * generator, so every draw is a pure function of its indices.  For
+ * realisation c and rows 4q .. 4q+3 the block function of counter
+ * (q, c, stream_id, 0) and key (seed, 0) gives four 64-bit words w_k;
+ * u_k = ((w_k >> 11) + 1/2) 2^-53 lies in (0, 1); rows 4q, 4q+1 are
+ * sqrt(-2 ln u0) (cos, sin)(2 pi u1) and rows 4q+2, 4q+3 the same with
+ * (u2, u3) (Box-Muller).  (The paper's package draws with L'Ecuyer's
+ * generator; results here are defined by this one.)
+ *
+ * gp_rng_normal: d_out[i + c ldo] = row i of realisation first + c, for
+ * i < n, c < r (column-major n x r, ldo >= n).                            */
+int gp_rng_normal(int64_t n, int64_t r, uint64_t seed, uint64_t stream_id, uint64_t first,
+                  double *d_out, int64_t ldo, void *stream);
+
+/* Unconditional realisations of N(mu, C) from its factor: column c of d_out
+ * (n x r, column-major, ldo >= n) = mu + L e_c, e_c the normals of
+ * realisation first + c in stream 0.  d_L: lower factor (ld ldl >= n; its
+ * upper part is never read), e.g. the start of a gp_loglik workspace.
+ * d_ws: gp_simulate_workspace_bytes(n, r) (the normals).  FP64 on the CUDA
+ * cores: n^2 r flops.                                                     */
+size_t gp_simulate_workspace_bytes(int64_t n, int64_t r);
+int gp_simulate(const double *d_L, int64_t n, int64_t ldl, int64_t r, uint64_t seed, uint64_t first,
+                double mu, double *d_out, int64_t ldo, void *d_ws, size_t ws_bytes, void *stream);
+
+/* Realisations of the latent process at m new locations conditional on the
+ * data (posterior draws), from a previous gp_loglik of the training data
+ * (d_alpha, and d_L = the factor at the start of its workspace, ld ldl >=
+ * n_p), with the arguments of gp_predict:
+ *   S = K** - K^T C^{-1} K  (the posterior covariance; K** the new
+ *       locations' covariance without nugget, K the cross covariance),
+ *   S = L* L*^T (unpivoted FP64 Cholesky),
+ *   column c of d_out (m x r, ldo >= m) = mean + L* e_c, mean as gp_predict,
+ *   e_c the normals of realisation first + c in stream 1.
+ * A posterior covariance that is not numerically positive definite (new
+ * locations too close to each other or to noise-free data: the failure of
+ * Sec. 5) sets *d_info = column + 1 and d_out to NaN.  d_ws:
+ * gp_simulate_conditional_workspace_bytes(n, m, r), about 8 (n_p m + m_p^2
+ * + m r) bytes.  FP64 on the CUDA cores: n_p^2 m + m^2 n_p + m^3/3 + m^2 r
+ * flops.                                                                  */
+size_t gp_simulate_conditional_workspace_bytes(int64_t n, int64_t m, int64_t r);
+int gp_simulate_conditional(const double *d_x, int64_t n, const double *d_xnew, int64_t m,
+                            const gp_params *prm, const double *d_alpha, const double *d_L,
+                            int64_t ldl, double mu_new, int64_t r, uint64_t seed, uint64_t first,
+                            double *d_out, int64_t ldo, void *d_ws, size_t ws_bytes,
+                            int64_t *d_info, void *stream);
+
 /* Log-likelihood without any workspace or allocation (GP_FP64 only).  The
  * paper has no counterpart: this entry point serves callers that cannot
  * allocate device memory when they need a log-likelihood -- code running

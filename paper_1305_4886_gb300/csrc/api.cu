@@ -479,6 +479,43 @@ int gp_predict(const double *d_x, int64_t n, const double *d_xnew, int64_t m, co
                        (cudaStream_t)stream);
 }
 
+int gp_rng_normal(int64_t n, int64_t r, uint64_t seed, uint64_t stream_id, uint64_t first,
+                  double *d_out, int64_t ldo, void *stream) {
+    if (n < 1 || r < 1 || !d_out || ldo < n) return GP_ERR_INVALID;
+    return rng_normals(n, n, r, seed, stream_id, first, d_out, ldo, (cudaStream_t)stream);
+}
+
+size_t gp_simulate_workspace_bytes(int64_t n, int64_t r) {
+    if (n < 1 || r < 1) return 0;
+    return simulate_ws_bytes(n, r);
+}
+
+int gp_simulate(const double *d_L, int64_t n, int64_t ldl, int64_t r, uint64_t seed, uint64_t first,
+                double mu, double *d_out, int64_t ldo, void *d_ws, size_t ws_bytes, void *stream) {
+    if (n < 1 || r < 1 || !d_L || !d_out || ldl < n || ldo < n || !isfinite(mu))
+        return GP_ERR_INVALID;
+    if (!d_ws || ws_bytes < simulate_ws_bytes(n, r)) return GP_ERR_WORKSPACE;
+    return simulate_run(d_L, n, ldl, r, seed, first, mu, d_out, ldo, d_ws, (cudaStream_t)stream);
+}
+
+size_t gp_simulate_conditional_workspace_bytes(int64_t n, int64_t m, int64_t r) {
+    if (n < 1 || m < 1 || r < 1) return 0;
+    return simulate_cond_ws_bytes(n, m, r);
+}
+
+int gp_simulate_conditional(const double *d_x, int64_t n, const double *d_xnew, int64_t m,
+                            const gp_params *prm, const double *d_alpha, const double *d_L,
+                            int64_t ldl, double mu_new, int64_t r, uint64_t seed, uint64_t first,
+                            double *d_out, int64_t ldo, void *d_ws, size_t ws_bytes,
+                            int64_t *d_info, void *stream) {
+    if (n < 1 || m < 1 || r < 1 || !d_x || !d_xnew || !d_alpha || !d_L || !d_out || !d_info ||
+        !params_ok(prm) || ldl < padded(n) || ldo < m || !isfinite(mu_new))
+        return GP_ERR_INVALID;
+    if (!d_ws || ws_bytes < simulate_cond_ws_bytes(n, m, r)) return GP_ERR_WORKSPACE;
+    return simulate_cond_run(d_x, n, d_xnew, m, *prm, d_alpha, d_L, ldl, mu_new, r, seed, first,
+                             d_out, ldo, d_ws, d_info, (cudaStream_t)stream);
+}
+
 size_t gp_syrk_workspace_bytes(int64_t m, int64_t k, int precision) {
     if (m < 1 || k < 1 || !precision_ok(precision)) return 0;
     return syrk_ws_bytes(m, k, precision, slices_of(precision));

@@ -335,6 +335,8 @@ __global__ void __launch_bounds__(256) trtri_tiles_kernel(const double *L, int64
 // mask.out_lower: write only entries with row + diag_off >= col.
 // mask.tri_k: op(B)(k, c) vanishes for k < c - tri_off; tiles start their K
 // loop there.
+// mask.a_lower: op(A) is lower triangular (op(A)(r, k) = 0 for k > r, the
+// upper part never read); tiles end their K loop after their last row.
 // ---------------------------------------------------------------------------
 constexpr int GBK = 16;
 
@@ -358,6 +360,7 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(int64_t M, int64_t N, int
     if (mask.out_lower && c0 > r0 + (TB - 1) + mask.diag_off) return;
     int64_t kbeg = 0;
     if (mask.tri_k && c0 - mask.tri_off > 0) kbeg = ((c0 - mask.tri_off) / GBK) * GBK;
+    const int64_t kend = mask.a_lower ? min(K, r0 + TB) : K;  // op(A) lower: k <= r
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     double acc[4][4];
@@ -366,7 +369,7 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(int64_t M, int64_t N, int
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
 
-    for (int64_t k0 = kbeg; k0 < K; k0 += GBK) {
+    for (int64_t k0 = kbeg; k0 < kend; k0 += GBK) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             int idx = tid + 256 * q;
@@ -376,12 +379,12 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(int64_t M, int64_t N, int
                 r = idx & 63;
                 k = idx >> 6;
                 int64_t gr = r0 + r, gk = k0 + k;
-                if (gr < M && gk < K) v = A[gr + gk * lda];
+                if (gr < M && gk < K && (!mask.a_lower || gk <= gr)) v = A[gr + gk * lda];
             } else {
                 k = idx & 15;
                 r = idx >> 4;
                 int64_t gr = r0 + r, gk = k0 + k;
-                if (gr < M && gk < K) v = A[gk + gr * lda];
+                if (gr < M && gk < K && (!mask.a_lower || gk <= gr)) v = A[gk + gr * lda];
             }
             As[k][r] = v;
             double w = 0.0;
@@ -460,6 +463,7 @@ __global__ void __launch_bounds__(SB_THREADS) gemm_f64_s32_kernel(int64_t M, int
         kend = min(K, kbeg + mask.kchunk);
     }
     if (mask.tri_k && c0 - mask.tri_off > kbeg) kbeg = ((c0 - mask.tri_off) / GBK) * GBK;
+    if (mask.a_lower) kend = min(kend, r0 + SB);  // op(A) lower: k <= r
     if (kbeg >= kend) return;
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;  // rows tx + 16a (a < 2), columns ty + 8b (b < 4)
@@ -478,7 +482,8 @@ __global__ void __launch_bounds__(SB_THREADS) gemm_f64_s32_kernel(int64_t M, int
             else { k = idx & 15; r = idx >> 4; }
             {
                 const int64_t gr = r0 + r, gk = k0 + k;
-                if (gr < M && gk < kend) v = opA == 0 ? A[gr + gk * lda] : A[gk + gr * lda];
+                if (gr < M && gk < kend && (!mask.a_lower || gk <= gr))
+                    v = opA == 0 ? A[gr + gk * lda] : A[gk + gr * lda];
             }
             As[k][r] = v;
             if (opB == 0) { kb = idx & 15; c = idx >> 4; }

@@ -22,6 +22,8 @@ struct F64Mask {
     int tri_k;        // op(B)(k, c) vanishes for k < c - tri_off
     int64_t tri_off;
     int64_t kchunk;   // > 0: split K into chunks, accumulate into C with atomics
+    int a_lower = 0;  // op(A)(r, k) is read as 0 for k > r (A lower triangular, its
+                      // upper part never read)
 };
 int gemm_f64_ex(int64_t M, int64_t N, int64_t K, double alpha, const double *A, int64_t lda,
                 int opA, const double *B, int64_t ldb, int opB, double beta, double *C, int64_t ldc,
@@ -83,6 +85,18 @@ size_t predict_ws_bytes(int64_t n, int64_t m, int want_var);
 int predict_run(const double *d_x, int64_t n, const double *d_xs, int64_t m, const KernParams &kp,
                 const double *d_alpha, const double *d_L, int64_t ldl, double mu_new,
                 double *d_mean, double *d_var, void *d_ws, int64_t *d_info, cudaStream_t s);
+
+// simulate.cu (realisations: Philox4x64-10 normals times a triangular factor)
+int rng_normals(int64_t n, int64_t rows, int64_t r, uint64_t seed, uint64_t stream, uint64_t first,
+                double *out, int64_t ldo, cudaStream_t s);
+size_t simulate_ws_bytes(int64_t n, int64_t r);
+int simulate_run(const double *d_L, int64_t n, int64_t ldl, int64_t r, uint64_t seed,
+                 uint64_t first, double mu, double *d_out, int64_t ldo, void *d_ws, cudaStream_t s);
+size_t simulate_cond_ws_bytes(int64_t n, int64_t m, int64_t r);
+int simulate_cond_run(const double *d_x, int64_t n, const double *d_xs, int64_t m,
+                      const gp_params &prm, const double *d_alpha, const double *d_L, int64_t ldl,
+                      double mu_new, int64_t r, uint64_t seed, uint64_t first, double *d_out,
+                      int64_t ldo, void *d_ws, int64_t *d_info, cudaStream_t s);
 
 // batch_dag.cu / batch_dag_tc.cu (the batched evaluation as one persistent task-graph launch)
 size_t dag_workspace_bytes(int nprob, const int64_t *h_n, int mixed);

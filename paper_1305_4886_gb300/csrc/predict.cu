@@ -103,8 +103,7 @@ __global__ void __launch_bounds__(256) cross_cov_kernel(const double2 *__restric
 
 // var[c] = sigma2 - sum_i V(i, c)^2, one warp per column, compensated.
 __global__ void __launch_bounds__(256) column_var_kernel(const double *V, int64_t ldv, int64_t rows,
-                                                         int64_t cols, double s2, double *var,
-                                                         const int64_t *info) {
+                                                         int64_t cols, double s2, double *var) {
     const int64_t c = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (c >= cols) return;
@@ -158,6 +157,9 @@ size_t predict_ws_bytes(int64_t n, int64_t m, int want_var) {
 static int predict_var(const double2 *x, int64_t n, int64_t np, const double2 *xs, int64_t m,
                        const KernParams &kp, const double *d_L, int64_t ldl, double *d_var,
                        void *d_ws, int64_t *d_info, cudaStream_t s);
+int pred_mean_launch(const double2 *x, int64_t n, const double2 *xs, int64_t m, const KernParams &kp,
+                     const double *d_alpha, double mu_new, double *d_mean, int64_t *d_info,
+                     cudaStream_t s);
 
 int predict_run(const double *d_x, int64_t n, const double *d_xs, int64_t m, const KernParams &kp,
                 const double *d_alpha, const double *d_L, int64_t ldl, double mu_new,
@@ -166,13 +168,46 @@ int predict_run(const double *d_x, int64_t n, const double *d_xs, int64_t m, con
     if (cudaMemsetAsync(d_info, 0, sizeof(int64_t), s) != cudaSuccess) return GP_ERR_CUDA;
     const double2 *x = reinterpret_cast<const double2 *>(d_x);
     const double2 *xs = reinterpret_cast<const double2 *>(d_xs);
-    predict_mean_kernel<<<(unsigned)ceil_div(m, PRED_T), PRED_T, 0, s>>>(x, n, xs, m, kp, d_alpha,
-                                                                        mu_new, d_mean, d_info);
-    GP_LAUNCH_CHECK();
+    GP_TRY(pred_mean_launch(x, n, xs, m, kp, d_alpha, mu_new, d_mean, d_info, s));
     if (d_var) GP_TRY(predict_var(x, n, np, xs, m, kp, d_L, ldl, d_var, d_ws, d_info, s));
     nan_on_failure_kernel<<<(unsigned)std::min<int64_t>(ceil_div(2 * m, 256), 1024), 256, 0, s>>>(
         d_info, d_mean, m, d_var, d_var ? m : 0);
     GP_LAUNCH_CHECK();
+    return GP_OK;
+}
+
+// W: the inverses of the 512-row diagonal blocks of L (PRED_NB x PRED_NB each).
+int pred_block_inverses(const double *d_L, int64_t ldl, int64_t np, double *W, double *tmp,
+                        int64_t *d_info, cudaStream_t s) {
+    for (int64_t k0 = 0; k0 < np; k0 += PRED_NB) {
+        const int64_t nb = (np - k0) < PRED_NB ? (np - k0) : PRED_NB;
+        GP_TRY(trtri_fp64_blocked(d_L + k0 + k0 * ldl, ldl, nb, W + (k0 / PRED_NB) * PRED_NB * PRED_NB,
+                                  nb, tmp, d_info, s));
+    }
+    return GP_OK;
+}
+
+// B (n_p x mc, ld n_p) = L^{-1} K(:, j0 .. j0 + mc): the cross covariance,
+// then the left-looking block solve with the block inverses W; T: PRED_NB x mc.
+int pred_solve_cross(const double2 *x, int64_t n, int64_t np, const double2 *xs, int64_t j0,
+                     int64_t mc, const KernParams &kp, const double *d_L, int64_t ldl,
+                     const double *W, double *B, double *T, int64_t *d_info, cudaStream_t s) {
+    dim3 g((unsigned)ceil_div(np, 256 * 4), (unsigned)mc);
+    cross_cov_kernel<<<g, 256, 0, s>>>(x, n, np, xs, j0, kp, B, np);
+    GP_LAUNCH_CHECK();
+    for (int64_t k0 = 0; k0 < np; k0 += PRED_NB) {
+        const int64_t nb = (np - k0) < PRED_NB ? (np - k0) : PRED_NB;
+        // K_I -= L_{I, 0:I} V_{0:I}
+        if (k0 > 0)
+            GP_TRY(gemm_f64(nb, mc, k0, -1.0, d_L + k0, ldl, 0, B, np, 0, 1.0, B + k0, np, 0, d_info,
+                            s));
+        // V_I = L_II^{-1} K_I  (through T)
+        const double *Wk = W + (k0 / PRED_NB) * PRED_NB * PRED_NB;
+        GP_TRY(gemm_f64(nb, mc, nb, 1.0, Wk, nb, 0, B + k0, np, 0, 0.0, T, nb, 0, d_info, s));
+        if (cudaMemcpy2DAsync(B + k0, sizeof(double) * np, T, sizeof(double) * nb,
+                              sizeof(double) * nb, mc, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return GP_ERR_CUDA;
+    }
     return GP_OK;
 }
 
@@ -181,33 +216,23 @@ static int predict_var(const double2 *x, int64_t n, int64_t np, const double2 *x
                        void *d_ws, int64_t *d_info, cudaStream_t s) {
     const int64_t mb = m < PRED_MB ? m : PRED_MB;
     PredWs w = pred_layout(d_ws, np, mb);
-    for (int64_t k0 = 0; k0 < np; k0 += PRED_NB) {
-        const int64_t nb = (np - k0) < PRED_NB ? (np - k0) : PRED_NB;
-        GP_TRY(trtri_fp64_blocked(d_L + k0 + k0 * ldl, ldl, nb, w.W + (k0 / PRED_NB) * PRED_NB * PRED_NB,
-                                  nb, w.tmp, d_info, s));
-    }
+    GP_TRY(pred_block_inverses(d_L, ldl, np, w.W, w.tmp, d_info, s));
     for (int64_t j0 = 0; j0 < m; j0 += mb) {
         const int64_t mc = (m - j0) < mb ? (m - j0) : mb;
-        dim3 g((unsigned)ceil_div(np, 256 * 4), (unsigned)mc);
-        cross_cov_kernel<<<g, 256, 0, s>>>(x, n, np, xs, j0, kp, w.B, np);
-        GP_LAUNCH_CHECK();
-        for (int64_t k0 = 0; k0 < np; k0 += PRED_NB) {
-            const int64_t nb = (np - k0) < PRED_NB ? (np - k0) : PRED_NB;
-            // K_I -= L_{I, 0:I} V_{0:I}
-            if (k0 > 0)
-                GP_TRY(gemm_f64(nb, mc, k0, -1.0, d_L + k0, ldl, 0, w.B, np, 0, 1.0, w.B + k0, np, 0,
-                                d_info, s));
-            // V_I = L_II^{-1} K_I  (through T)
-            const double *Wk = w.W + (k0 / PRED_NB) * PRED_NB * PRED_NB;
-            GP_TRY(gemm_f64(nb, mc, nb, 1.0, Wk, nb, 0, w.B + k0, np, 0, 0.0, w.T, nb, 0, d_info, s));
-            if (cudaMemcpy2DAsync(w.B + k0, sizeof(double) * np, w.T, sizeof(double) * nb,
-                                  sizeof(double) * nb, mc, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-                return GP_ERR_CUDA;
-        }
+        GP_TRY(pred_solve_cross(x, n, np, xs, j0, mc, kp, d_L, ldl, w.W, w.B, w.T, d_info, s));
         column_var_kernel<<<(unsigned)ceil_div(mc, 8), 256, 0, s>>>(w.B, np, np, mc, kp.s2,
-                                                                    d_var + j0, d_info);
+                                                                    d_var + j0);
         GP_LAUNCH_CHECK();
     }
+    return GP_OK;
+}
+
+int pred_mean_launch(const double2 *x, int64_t n, const double2 *xs, int64_t m, const KernParams &kp,
+                     const double *d_alpha, double mu_new, double *d_mean, int64_t *d_info,
+                     cudaStream_t s) {
+    predict_mean_kernel<<<(unsigned)ceil_div(m, PRED_T), PRED_T, 0, s>>>(x, n, xs, m, kp, d_alpha,
+                                                                        mu_new, d_mean, d_info);
+    GP_LAUNCH_CHECK();
     return GP_OK;
 }
 

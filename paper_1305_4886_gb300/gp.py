@@ -35,6 +35,11 @@ SYMBOLS = [
     "gp_loglik_grad_batched",
     "gp_predict_workspace_bytes",
     "gp_predict",
+    "gp_rng_normal",
+    "gp_simulate_workspace_bytes",
+    "gp_simulate",
+    "gp_simulate_conditional_workspace_bytes",
+    "gp_simulate_conditional",
     "gp_loglik_noalloc",
     "gp_syrk_workspace_bytes",
     "gp_syrk_lower",
@@ -122,6 +127,19 @@ def lib():
             L.gp_predict.argtypes = [p, i64, p, i64, PP, p, p, i64, ctypes.c_double, p, p, p, sz,
                                      p, p]
             L.gp_predict.restype = ci
+            u64 = ctypes.c_uint64
+            L.gp_rng_normal.argtypes = [i64, i64, u64, u64, u64, p, i64, p]
+            L.gp_rng_normal.restype = ci
+            L.gp_simulate_workspace_bytes.argtypes = [i64, i64]
+            L.gp_simulate_workspace_bytes.restype = sz
+            L.gp_simulate.argtypes = [p, i64, i64, i64, u64, u64, ctypes.c_double, p, i64, p, sz,
+                                      p]
+            L.gp_simulate.restype = ci
+            L.gp_simulate_conditional_workspace_bytes.argtypes = [i64, i64, i64]
+            L.gp_simulate_conditional_workspace_bytes.restype = sz
+            L.gp_simulate_conditional.argtypes = [p, i64, p, i64, PP, p, p, i64, ctypes.c_double,
+                                                  i64, u64, u64, p, i64, p, sz, p, p]
+            L.gp_simulate_conditional.restype = ci
             L.gp_loglik_noalloc.argtypes = [p, p, p, i64, PP, p, p, p, p]
             L.gp_loglik_noalloc.restype = ci
             L.gp_syrk_workspace_bytes.argtypes = [i64, i64, ci]
@@ -403,6 +421,73 @@ def predict(x, y, xnew, kernel, sigma2, rho, tau2, mu=None, mu_new=None, precisi
         if iv != 0:
             raise GpDeviceError(iv)
     return dict(mean=mean, var=var, loglik=r["out"][0])
+
+
+def gp_rng_normal(n, r, seed, stream_id, first, out, ldo=None, stream=None):
+    _check(lib().gp_rng_normal(int(n), int(r), int(seed), int(stream_id), int(first), _f64(out),
+                               int(ldo if ldo is not None else n), _stream(stream)),
+           "gp_rng_normal")
+
+
+def gp_simulate_workspace_bytes(n, r):
+    return lib().gp_simulate_workspace_bytes(int(n), int(r))
+
+
+def gp_simulate(L, n, ldl, r, seed, first, mu, out, ldo, ws, stream=None):
+    wsb = ws.numel() * ws.element_size()
+    _check(lib().gp_simulate(_f64(L), int(n), int(ldl), int(r), int(seed), int(first), float(mu),
+                             _f64(out), int(ldo), _ptr(ws), wsb, _stream(stream)), "gp_simulate")
+
+
+def gp_simulate_conditional_workspace_bytes(n, m, r):
+    return lib().gp_simulate_conditional_workspace_bytes(int(n), int(m), int(r))
+
+
+def gp_simulate_conditional(x, n, xnew, m, prm, alpha, L, ldl, mu_new, r, seed, first, out, ldo,
+                            ws, info, stream=None):
+    wsb = ws.numel() * ws.element_size()
+    _check(lib().gp_simulate_conditional(_f64(x), int(n), _f64(xnew), int(m), ctypes.byref(prm),
+                                         _f64(alpha), _f64(L), int(ldl), float(mu_new), int(r),
+                                         int(seed), int(first), _f64(out), int(ldo), _ptr(ws), wsb,
+                                         _ptr(info), _stream(stream)), "gp_simulate_conditional")
+
+
+def simulate(x, kernel, sigma2, rho, tau2, r, seed, first=0, mu=0.0, precision="fp64"):
+    """Unconditional realisations of N(mu, C(theta)) at the locations x: the
+    factor from one gp_loglik (its data vector is irrelevant), then
+    gp_simulate.  Returns an (r, n) device tensor (row c = realisation c)."""
+    n = x.shape[0]
+    zero = torch.zeros(n, dtype=torch.float64, device=x.device)
+    lk = loglik(x, zero, kernel, sigma2, rho, tau2, precision=precision)
+    np_ = gp_padded_order(n)
+    out = torch.empty(r, n, dtype=torch.float64, device=x.device)
+    ws = torch.empty(gp_simulate_workspace_bytes(n, r), dtype=torch.uint8, device=x.device)
+    gp_simulate(lk["ws"][: np_ * np_ * 8].view(torch.float64), n, np_, r, seed, first, mu, out, n,
+                ws)
+    return out
+
+
+def simulate_conditional(x, y, xnew, kernel, sigma2, rho, tau2, r, seed, first=0, mu=None,
+                         mu_new=None, precision="fp64", check=True):
+    """Posterior realisations of the latent process at xnew given the data:
+    one gp_loglik (factor and alpha), then gp_simulate_conditional.  Returns
+    an (r, m) device tensor and the status tensor."""
+    n, m = x.shape[0], xnew.shape[0]
+    lk = loglik(x, y, kernel, sigma2, rho, tau2, mu=mu, precision=precision)
+    np_ = gp_padded_order(n)
+    out = torch.empty(r, m, dtype=torch.float64, device=x.device)
+    ws = torch.empty(gp_simulate_conditional_workspace_bytes(n, m, r), dtype=torch.uint8,
+                     device=x.device)
+    info = torch.zeros(1, dtype=torch.int64, device=x.device)
+    mn = float(mu_new) if mu_new is not None else (0.0 if mu is None else float(mu))
+    gp_simulate_conditional(x, n, xnew, m, params(kernel, sigma2, rho, tau2), lk["alpha"],
+                            lk["ws"][: np_ * np_ * 8].view(torch.float64), np_, mn, r, seed, first,
+                            out, m, ws, info)
+    if check:
+        iv = int(info.item())
+        if iv != 0:
+            raise GpDeviceError(iv)
+    return out, info
 
 
 def gp_loglik_noalloc(x, y, mu, n, prm, out, alpha, info, stream=None):

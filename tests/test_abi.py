@@ -111,3 +111,18 @@ def test_predict_arguments(libgp):
     assert call(10, 5, d, 128, d, d, 16) == libgp.GP_ERR_WORKSPACE
     assert libgp.gp_predict_workspace_bytes(10, 5, False) == 0
     assert libgp.gp_predict_workspace_bytes(10, 5, True) > 128 * 5 * 8
+
+
+def test_simulation_arguments(libgp):
+    L = libgp.lib()
+    d = ctypes.c_void_p(16)
+    prm = libgp.params("exp", 1.0, 0.1, 0.1)
+    assert L.gp_rng_normal(0, 1, 1, 0, 0, d, 1, None) == libgp.GP_ERR_INVALID
+    assert L.gp_rng_normal(10, 1, 1, 0, 0, d, 9, None) == libgp.GP_ERR_INVALID  # ldo < n
+    assert L.gp_simulate(d, 10, 10, 2, 1, 0, 0.0, d, 10, d, 8, None) == libgp.GP_ERR_WORKSPACE
+    assert L.gp_simulate(d, 10, 9, 2, 1, 0, 0.0, d, 10, d, 1 << 20, None) == libgp.GP_ERR_INVALID
+    assert libgp.gp_simulate_workspace_bytes(10, 2) >= 160
+    assert L.gp_simulate_conditional(d, 10, d, 3, ctypes.byref(prm), d, d, 64, 0.0, 2, 1, 0, d, 3,
+                                     d, 1 << 30, d, None) == libgp.GP_ERR_INVALID  # ldl < n_p
+    assert L.gp_simulate_conditional(d, 10, d, 3, ctypes.byref(prm), d, d, 128, 0.0, 2, 1, 0, d, 3,
+                                     d, 64, d, None) == libgp.GP_ERR_WORKSPACE
