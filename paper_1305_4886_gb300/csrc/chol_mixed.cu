@@ -21,6 +21,7 @@
 // The pivots and hence the log-determinant come from FP64 factorisations of
 // blocks whose updates carry the slice products' accuracy.
 #include "internal.h"
+#include "kern_df.cuh"
 #include "tc_gemm.h"
 
 namespace gp {
@@ -72,7 +73,7 @@ __global__ void fold_delta2_kernel(double *A, int64_t ld, const float2 *D, int64
     for (int64_t r = c + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows;
          r += (int64_t)gridDim.x * blockDim.x) {
         const float2 d = D[r + c * ldd];
-        A[r + c * ld] += static_cast<double>(d.x) + static_cast<double>(d.y);
+        A[r + c * ld] += f32_to_f64(d.x) + f32_to_f64(d.y);  // conversions by integer operations
     }
 }
 

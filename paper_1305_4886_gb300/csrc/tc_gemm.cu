@@ -232,15 +232,22 @@ __device__ __forceinline__ void epilogue_group(const TcGemmArgs &args, uint32_t 
         double *dst = static_cast<double *>(args.C) + row + colb * args.ldc;
 #pragma unroll
         for (int j = 0; j < TC_EG; ++j) {
-            double v = static_cast<double>(__uint_as_float(a0[j])) +
-                       static_cast<double>(__uint_as_float(a1[j]));
+            // conversions and the exact 2^k scaling by integer operations
+            // (sums of FP32 values are zero or at least 2^-149 in magnitude,
+            // so the scaled value stays a normal FP64 number)
+            double v = f32_to_f64(__uint_as_float(a0[j])) + f32_to_f64(__uint_as_float(a1[j]));
             if (nacc > 2)
-                v += static_cast<double>(__uint_as_float(a2[j])) +
-                     static_cast<double>(__uint_as_float(a3[j]));
-            v *= __longlong_as_double(static_cast<long long>(ksc[j] + 1023) << 52);  // 2^k, exact
+                v += f32_to_f64(__uint_as_float(a2[j])) + f32_to_f64(__uint_as_float(a3[j]));
+            {
+                const long long b = __double_as_longlong(v);
+                if (b & 0x7FFFFFFFFFFFFFFFll)
+                    v = __longlong_as_double(b + (static_cast<long long>(ksc[j]) << 52));
+            }
             if (args.beta != 0.0)
                 v = fma(args.beta, __longlong_as_double(static_cast<long long>(old[j])),
                         args.alpha * v);
+            else if (args.alpha == -1.0)
+                v = -v;
             else if (args.alpha != 1.0)
                 v = args.alpha * v;
             if (okc[j]) dst[j * args.ldc] = v;
@@ -516,11 +523,16 @@ __device__ __forceinline__ void t3_store(const TcGemmArgs &args, const float *h_
             two_sum(s1, e1, hi, lo);
             if (cl + j < lim) *reinterpret_cast<float2 *>(p + j * ld8) = make_float2(hi, lo);
         } else {
-            double v = static_cast<double>(h_[j]) + static_cast<double>(l_[j]);
-            v *= __longlong_as_double(static_cast<long long>(ea + eb - 14 + 1023) << 52);  // exact
+            // (h + l) 2^{e_a + e_b - 14}: the scaling and the conversions by
+            // integer operations, one FP64 add (the FP64 pipe runs at 1/64
+            // of the FP32 rate); alpha = +-1 by the sign bit
+            const int k = ea + eb - 14;
+            double v = f32_to_f64_scaled(h_[j], k) + f32_to_f64_scaled(l_[j], k);
             if (args.beta != 0.0)
                 v = fma(args.beta, __longlong_as_double(static_cast<long long>(old[j])),
                         args.alpha * v);
+            else if (args.alpha == -1.0)
+                v = -v;
             else if (args.alpha != 1.0)
                 v = args.alpha * v;
             if (cl + j < lim) *reinterpret_cast<double *>(p + j * ld8) = v;
@@ -845,7 +857,10 @@ __global__ void acc2_to_f64_kernel(const float2 *acc, int64_t M, int64_t N, doub
     if (r >= M || c >= N) return;
     if (lower && r + diag_off < c) return;
     const float2 v = acc[r + c * M];
-    double x = alpha * (static_cast<double>(v.x) + static_cast<double>(v.y));
+    // the conversions by integer operations, one FP64 add; alpha = +-1 by the sign bit
+    double x = f32_to_f64(v.x) + f32_to_f64(v.y);
+    if (alpha == -1.0) x = -x;
+    else if (alpha != 1.0) x *= alpha;
     if (beta != 0.0) x = fma(beta, C[r + c * ldc], x);
     C[r + c * ldc] = x;
 }
