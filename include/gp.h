@@ -14,7 +14,12 @@
  *   - Pointers prefixed d_ are device pointers; h_ are host pointers.  The
  *     caller owns every buffer, including workspaces; the library never
  *     allocates device memory in these calls and keeps no hidden state
- *     between them.
+ *     between them.  The tensor-core factorisations (GP_MIXED_F16,
+ *     GP_EMU_FP64 in gp_chol, gp_loglik, gp_loglik_grad) run their
+ *     diagonal blocks on a library side stream, forked from and joined back
+ *     to the caller's stream with events: that stream and its two events
+ *     are created on the first such call on a device (make it outside a
+ *     stream capture) and kept for the process.
  *   - Matrices are FP64, column-major, lower triangle referenced, leading
  *     dimension ld >= gp_padded_order(n).  The padded order n_p rounds n up
  *     to a multiple of GP_PAD (the block padding of Sec. 2.2); rows/columns

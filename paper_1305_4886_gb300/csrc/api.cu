@@ -92,7 +92,7 @@ static LoglikWs loglik_ws_layout(void *base, int64_t n, int precision, int want_
 }
 
 static int run_chol(double *A, int64_t np, int64_t ld, int precision, void *ws, double *winv,
-                    int64_t *info, cudaStream_t s) {
+                    int64_t *info, cudaStream_t s, bool lookahead = true) {
     if (precision == GP_FP64) {
         const int ev = prof_start(s);
         GP_TRY(chol_fp64_tiled(A, ld, np, 0, info, s));
@@ -100,18 +100,18 @@ static int run_chol(double *A, int64_t np, int64_t ld, int precision, void *ws, 
         return GP_OK;
     }
     if (precision == GP_MIXED_F16 || precision == GP_EMU_FP64)
-        return chol_mixed(A, ld, np, slices_of(precision), ws, winv, info, s);
+        return chol_mixed(A, ld, np, slices_of(precision), ws, winv, info, s, lookahead);
     return GP_ERR_INVALID;
 }
 
 // fill -> Cholesky -> solves -> reductions; leaves alpha in w.v.
 static int loglik_core(const double *d_x, const double *d_y, const double *d_mu, int64_t n,
                        const KernParams &kp, int precision, const LoglikWs &w, double *d_out,
-                       int64_t *d_info, cudaStream_t s) {
+                       int64_t *d_info, cudaStream_t s, bool lookahead = true) {
     const int64_t np = padded(n);
     if (cudaMemsetAsync(d_info, 0, sizeof(int64_t), s) != cudaSuccess) return GP_ERR_CUDA;
     GP_TRY(launch_cov_fill(d_x, n, np, kp, w.A, np, d_info, s));
-    GP_TRY(run_chol(w.A, np, np, precision, w.chol, w.winv, d_info, s));
+    GP_TRY(run_chol(w.A, np, np, precision, w.chol, w.winv, d_info, s, lookahead));
     GP_TRY(launch_residual(d_y, d_mu, n, np, w.r, d_info, s));
     if (cudaMemcpyAsync(w.v, w.r, sizeof(double) * np, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return GP_ERR_CUDA;
@@ -352,8 +352,9 @@ int gp_loglik_grad_batched(int nprob, const int64_t *h_n, const double *const *h
             LoglikWs w = loglik_ws_layout(static_cast<char *>(d_ws) + off[i], n, precision, 1);
             KernParams kp = make_kern(h_prm[i], precision != GP_FP64);
             const double *mu = h_dmu ? h_dmu[i] : nullptr;
+            // many problems run side by side here: no lookahead side stream
             int st = loglik_core(h_dx[i], h_dy[i], mu, n, kp, precision, w, d_out + 4 * i,
-                                 d_info + i, sk);
+                                 d_info + i, sk, false);
             if (st == GP_OK)
                 st = chol_inverse(w.A, np, np, precision, slices_of(precision), w.chol, w.winv,
                                   d_info + i, sk);

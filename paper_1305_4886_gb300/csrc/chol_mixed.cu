@@ -18,8 +18,15 @@
 //   5. trailing update D_ij -= L_ik L_jk^T on the lower triangle, tensor
 //      cores, double-float accumulation into D ("most of the total work is
 //      in the matrix multiplications", Sec. 2.1).
+// Lookahead: step 5 updates block column k+1 first; steps 1-3 of block k+1
+// then run on a side stream (on the few SMs the rest of the update leaves
+// free) while the rest of step 5 runs, so the latency-bound diagonal
+// blocks leave the critical path (the paper's diagonal blocks are likewise
+// the sequential part of each step, Sec. 2.1).
 // The pivots and hence the log-determinant come from FP64 factorisations of
 // blocks whose updates carry the slice products' accuracy.
+#include <mutex>
+
 #include "internal.h"
 #include "kern_df.cuh"
 #include "tc_gemm.h"
@@ -77,38 +84,116 @@ __global__ void fold_delta2_kernel(double *A, int64_t ld, const float2 *D, int64
     }
 }
 
-int chol_mixed(double *A, int64_t ld, int64_t np, int S, void *ws, double *winv, int64_t *info,
-               cudaStream_t s) {
-    MixedWs w = mixed_layout(ws, np, S);
-    if (cudaMemsetAsync(w.D, 0, sizeof(float2) * (size_t)np * (size_t)np, s) !=
-        cudaSuccess)
+// Lookahead: a side stream and two events per device, created on first use
+// (make the first call outside a stream capture) and kept for the process.
+// The host enqueues one factorisation at a time per device (mu), so that each
+// wait binds to its own factorisation's event record.
+struct LookaheadCtx {
+    std::mutex mu;
+    cudaStream_t side;
+    cudaEvent_t next_ready;  // main stream: the next block column's updates are in D
+    cudaEvent_t diag_done;   // side stream: the next diagonal block is factored and inverted
+    int sms;
+};
+
+static int lookahead_ctx(LookaheadCtx **out) {
+    static std::mutex mu;
+    static LookaheadCtx *ctx[64] = {};
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return GP_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!ctx[dev]) {
+        LookaheadCtx *c = new LookaheadCtx();
+        if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->next_ready, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->diag_done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            delete c;
+            return GP_ERR_CUDA;
+        }
+        ctx[dev] = c;
+    }
+    *out = ctx[dev];
+    return GP_OK;
+}
+
+// SMs left to the diagonal-block work while the rest of a trailing update runs
+constexpr int LOOKAHEAD_SMS = 8;
+
+// Block column k0 (width nb): fold its pending updates (k0 > 0), factor the
+// diagonal block, and, when `inverse`, form W = L_kk^{-1}.
+static int diag_block(double *A, int64_t ld, int64_t np, int64_t k0, int64_t nb, int S,
+                      const MixedWs &w, double *W, bool inverse, int64_t *info, cudaStream_t s) {
+    double *Akk = A + k0 + k0 * ld;
+    const int64_t rows = np - k0;
+    if (k0 > 0) {
+        dim3 g((unsigned)ceil_div(rows, 256 * 4) + 1, (unsigned)nb);
+        const int ev = prof_start(s);
+        fold_delta2_kernel<<<g, 256, 0, s>>>(Akk, ld, w.D + k0 + k0 * np, np, rows, nb, info);
+        GP_LAUNCH_CHECK();
+        prof_stop(ev, s, GP_PROF_FOLD, 0.0, 16.0 * (double)rows * nb);
+    }
+    int ev = prof_start(s);
+    GP_TRY(chol_fp64_tiled(Akk, ld, nb, k0, info, s, S == 3));
+    prof_stop(ev, s, GP_PROF_DIAG, (double)nb * nb * nb / 3.0, 0.0);
+    if (!inverse) return GP_OK;
+    ev = prof_start(s);
+    GP_TRY(trtri_fp64_blocked(Akk, ld, nb, W, nb, w.tmp, info, s));
+    prof_stop(ev, s, GP_PROF_DIAGINV, (double)nb * nb * nb / 3.0, 0.0);
+    return GP_OK;
+}
+
+// Without lookahead: every step on the caller's stream, in order.
+static int chol_mixed_plain(double *A, int64_t ld, int64_t np, int S, const MixedWs &w,
+                            double *winv, int64_t *info, cudaStream_t s) {
+    if (cudaMemsetAsync(w.D, 0, sizeof(float2) * (size_t)np * (size_t)np, s) != cudaSuccess)
         return GP_ERR_CUDA;
     for (int64_t k0 = 0; k0 < np; k0 += NB) {
         const int64_t nb = (np - k0) < NB ? (np - k0) : NB;
-        double *Akk = A + k0 + k0 * ld;
-        const int64_t rows = np - k0;
-        if (k0 > 0) {
-            dim3 g((unsigned)ceil_div(rows, 256 * 4) + 1, (unsigned)nb);
-            const int ev = prof_start(s);
-            fold_delta2_kernel<<<g, 256, 0, s>>>(Akk, ld, w.D + k0 + k0 * np, np, rows, nb, info);
-            GP_LAUNCH_CHECK();
-            prof_stop(ev, s, GP_PROF_FOLD, 0.0, 16.0 * (double)rows * nb);
-        }
-        int ev = prof_start(s);
-        GP_TRY(chol_fp64_tiled(Akk, ld, nb, k0, info, s, S == 3));
-        prof_stop(ev, s, GP_PROF_DIAG, (double)nb * nb * nb / 3.0, 0.0);
         const int64_t m = np - k0 - nb;
-        if (m <= 0 && !winv) break;
-        // W = L_kk^{-1} (kept for the gradient's inverse when asked: then the
-        // last block's inverse is formed too)
         double *W = winv ? winv + (k0 / NB) * NB * NB : w.W;
-        ev = prof_start(s);
-        GP_TRY(trtri_fp64_blocked(Akk, ld, nb, W, nb, w.tmp, info, s));
-        prof_stop(ev, s, GP_PROF_DIAGINV, (double)nb * nb * nb / 3.0, 0.0);
+        GP_TRY(diag_block(A, ld, np, k0, nb, S, w, W, m > 0 || winv, info, s));
+        if (m <= 0) break;
+        double *P = A + k0 + k0 * ld + nb;
+        int *exA = S == 3 ? w.exA : nullptr, *exB = S == 3 ? w.exB : nullptr;
+        GP_TRY(split_rows(W, nb, nb, nb, nb, 0, 0, 1, S, w.SB, exB, NB, NB, 0, 0, s));
+        GP_TRY(split_rows(P, ld, m, nb, nb, 0, 0, 0, S, w.SA, exA, np, NB, 0, 0, s));
+        TcOperand opA{w.SA, np, NB, S, 0, 0, exA, tc_ex_ld(NB)};
+        TcOperand opW{w.SB, NB, NB, S, 0, 0, exB, tc_ex_ld(NB)};
+        TcOut o1{P, ld, 0, 1.0, 0.0, 0, 0};
+        GP_TRY(tc_gemm(opA, opW, m, nb, nb, o1, 0, 0, info, s));
+        GP_TRY(split_rows(P, ld, m, nb, nb, 0, 0, 0, S, w.SA, exA, np, NB, 0, 0, s));
+        TcOut o2{w.D + (k0 + nb) + (k0 + nb) * np, np, 2, -1.0, 0.0, 1, 0};
+        GP_TRY(tc_gemm(opA, opA, m, m, nb, o2, 0, 0, info, s));
+    }
+    return GP_OK;
+}
+
+int chol_mixed(double *A, int64_t ld, int64_t np, int S, void *ws, double *winv, int64_t *info,
+               cudaStream_t s, bool lookahead) {
+    MixedWs w = mixed_layout(ws, np, S);
+    if (!lookahead) return chol_mixed_plain(A, ld, np, S, w, winv, info, s);
+    LookaheadCtx *la = nullptr;
+    GP_TRY(lookahead_ctx(&la));
+    std::lock_guard<std::mutex> enqueue(la->mu);
+    if (cudaMemsetAsync(w.D, 0, sizeof(float2) * (size_t)np * (size_t)np, s) !=
+        cudaSuccess)
+        return GP_ERR_CUDA;
+    // W = L_kk^{-1} (kept for the gradient's inverse when asked: then the
+    // last block's inverse is formed too)
+    auto W_of = [&](int64_t k0) { return winv ? winv + (k0 / NB) * NB * NB : w.W; };
+    {
+        const int64_t nb0 = np < NB ? np : NB;
+        GP_TRY(diag_block(A, ld, np, 0, nb0, S, w, W_of(0), np > nb0 || winv, info, s));
+    }
+    for (int64_t k0 = 0; k0 < np; k0 += NB) {
+        const int64_t nb = (np - k0) < NB ? (np - k0) : NB;
+        double *Akk = A + k0 + k0 * ld;
+        const int64_t m = np - k0 - nb;
         if (m <= 0) break;
         double *P = Akk + nb;  // m x nb panel below the diagonal block
         int *exA = S == 3 ? w.exA : nullptr, *exB = S == 3 ? w.exB : nullptr;
-        GP_TRY(split_rows(W, nb, nb, nb, nb, 0, 0, 1, S, w.SB, exB, NB, NB, 0, 0, s));
+        GP_TRY(split_rows(W_of(k0), nb, nb, nb, nb, 0, 0, 1, S, w.SB, exB, NB, NB, 0, 0, s));
         GP_TRY(split_rows(P, ld, m, nb, nb, 0, 0, 0, S, w.SA, exA, np, NB, 0, 0, s));
         TcOperand opA{w.SA, np, NB, S, 0, 0, exA, tc_ex_ld(NB)};
         TcOperand opW{w.SB, NB, NB, S, 0, 0, exB, tc_ex_ld(NB)};
@@ -116,9 +201,25 @@ int chol_mixed(double *A, int64_t ld, int64_t np, int S, void *ws, double *winv,
         TcOut o1{P, ld, 0, 1.0, 0.0, 0, 0};
         GP_TRY(tc_gemm(opA, opW, m, nb, nb, o1, 0, 0, info, s));
         GP_TRY(split_rows(P, ld, m, nb, nb, 0, 0, 0, S, w.SA, exA, np, NB, 0, 0, s));
-        // D_22 -= L_ik L_ik^T (lower, double-float)
-        TcOut o2{w.D + (k0 + nb) + (k0 + nb) * np, np, 2, -1.0, 0.0, 1, 0};
-        GP_TRY(tc_gemm(opA, opA, m, m, nb, o2, 0, 0, info, s));
+        // D_22 -= L_ik L_ik^T (lower, double-float), the next block column
+        // first: its diagonal block is then folded, factored and inverted on
+        // the side stream while the rest of the update runs on the other SMs
+        const int64_t k1 = k0 + nb, nbn = m < NB ? m : NB, m1 = m - nbn;
+        TcOut o2a{w.D + k1 + k1 * np, np, 2, -1.0, 0.0, 1, 0};
+        GP_TRY(tc_gemm(opA, opA, m, nbn, nb, o2a, 0, 0, info, s));
+        if (cudaEventRecord(la->next_ready, s) != cudaSuccess ||
+            cudaStreamWaitEvent(la->side, la->next_ready, 0) != cudaSuccess)
+            return GP_ERR_CUDA;
+        GP_TRY(diag_block(A, ld, np, k1, nbn, S, w, W_of(k1), m1 > 0 || winv, info, la->side));
+        if (cudaEventRecord(la->diag_done, la->side) != cudaSuccess) return GP_ERR_CUDA;
+        if (m1 > 0) {
+            TcOperand opR = opA;
+            opR.row_off = nbn;
+            TcOut o2b{w.D + (k1 + nbn) + (k1 + nbn) * np, np, 2, -1.0, 0.0, 1, 0};
+            o2b.max_ctas = la->sms > 2 * LOOKAHEAD_SMS ? la->sms - LOOKAHEAD_SMS : 0;
+            GP_TRY(tc_gemm(opR, opR, m1, m1, nb, o2b, 0, 0, info, s));
+        }
+        if (cudaStreamWaitEvent(s, la->diag_done, 0) != cudaSuccess) return GP_ERR_CUDA;
     }
     return GP_OK;
 }

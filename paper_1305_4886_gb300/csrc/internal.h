@@ -58,8 +58,11 @@ size_t chol_mixed_ws_bytes(int64_t np, int S);
 // winv (nullable, chol_winv_doubles(np) doubles): receives L_kk^{-1} of every
 // 512-column diagonal block (NB x NB each, in block order) for the inverse
 size_t chol_winv_doubles(int64_t np);
+// lookahead: run each next diagonal block on the device's side stream while
+// the trailing update finishes (off for callers that already run many
+// factorisations side by side)
 int chol_mixed(double *A, int64_t ld, int64_t np, int S, void *ws, double *winv, int64_t *info,
-               cudaStream_t s);
+               cudaStream_t s, bool lookahead = true);
 size_t syrk_ws_bytes(int64_t m, int64_t k, int precision, int S);
 int syrk_lower(double *C, int64_t ldc, const double *P, int64_t ldp, int64_t m, int64_t k,
                int precision, int S, void *ws, int64_t *info, cudaStream_t s);

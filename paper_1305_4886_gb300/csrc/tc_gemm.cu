@@ -1014,7 +1014,8 @@ int tc_gemm(const TcOperand &A, const TcOperand &B, int64_t M, int64_t N, int64_
     a.npairs = np;
     const int64_t ntiles = (int64_t)a.tiles_m * a.tiles_n;
     const int sms = num_sms();
-    const int grid = (int)(ntiles < sms ? ntiles : (sms > 0 ? sms : 148));
+    int grid = (int)(ntiles < sms ? ntiles : (sms > 0 ? sms : 148));
+    if (out.max_ctas > 0 && grid > out.max_ctas) grid = out.max_ctas;
     const int ev = prof_start(s);
     if (three)
         tc_gemm3_kernel<<<grid, T3_THREADS, T3_SMEM, s>>>(ma, mb, a);

@@ -46,6 +46,8 @@ struct TcOut {
     void *acc2 = nullptr;  // mode 0 with K > 512: M x N float2 scratch; the
                            // accumulators are flushed per 512-deep chunk into it
                            // in double-float and converted to FP64 at the end
+    int max_ctas = 0;      // > 0: at most this many persistent CTAs (leaves the
+                           // other SMs to work on another stream)
 };
 
 // out(M x N) <- sum over slice pairs p + q < S of A_p B_q^T, K columns.
