@@ -25,6 +25,8 @@
 // the sequential part of each step, Sec. 2.1).
 // The pivots and hence the log-determinant come from FP64 factorisations of
 // blocks whose updates carry the slice products' accuracy.
+#include <stdlib.h>
+
 #include <mutex>
 
 #include "internal.h"
@@ -72,12 +74,14 @@ size_t chol_mixed_ws_bytes(int64_t np, int S) { return mixed_layout(nullptr, np,
 
 size_t chol_winv_doubles(int64_t np) { return (size_t)ceil_div(np, NB) * NB * NB; }
 
-// A[r, c] += D.hi[r, c] + D.lo[r, c] (double-float pending updates).
+// A[r, c] += D.hi[r, c] + D.lo[r, c] (double-float pending updates) for the
+// lower entries r + roff >= c of a rows x cols block.
 __global__ void fold_delta2_kernel(double *A, int64_t ld, const float2 *D, int64_t ldd,
-                                   int64_t rows, int64_t cols, const int64_t *info) {
+                                   int64_t rows, int64_t cols, int64_t roff, const int64_t *info) {
     if (failed(info)) return;
     const int64_t c = blockIdx.y;
-    for (int64_t r = c + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows;
+    const int64_t rfirst = c - roff > 0 ? c - roff : 0;
+    for (int64_t r = rfirst + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows;
          r += (int64_t)gridDim.x * blockDim.x) {
         const float2 d = D[r + c * ldd];
         A[r + c * ld] += f32_to_f64(d.x) + f32_to_f64(d.y);  // conversions by integer operations
@@ -117,22 +121,46 @@ static int lookahead_ctx(LookaheadCtx **out) {
     return GP_OK;
 }
 
-// SMs left to the diagonal-block work while the rest of a trailing update runs
-constexpr int LOOKAHEAD_SMS = 8;
-
-// Block column k0 (width nb): fold its pending updates (k0 > 0), factor the
-// diagonal block, and, when `inverse`, form W = L_kk^{-1}.
-static int diag_block(double *A, int64_t ld, int64_t np, int64_t k0, int64_t nb, int S,
-                      const MixedWs &w, double *W, bool inverse, int64_t *info, cudaStream_t s) {
-    double *Akk = A + k0 + k0 * ld;
-    const int64_t rows = np - k0;
-    if (k0 > 0) {
-        dim3 g((unsigned)ceil_div(rows, 256 * 4) + 1, (unsigned)nb);
-        const int ev = prof_start(s);
-        fold_delta2_kernel<<<g, 256, 0, s>>>(Akk, ld, w.D + k0 + k0 * np, np, rows, nb, info);
-        GP_LAUNCH_CHECK();
-        prof_stop(ev, s, GP_PROF_FOLD, 0.0, 16.0 * (double)rows * nb);
+// SMs left to the diagonal-block work while the rest of a trailing update
+// runs: a fixed share while that update is large, more once it is small and
+// the diagonal block would otherwise be the critical path (GP_LOOKAHEAD_SMS
+// in the environment overrides the large-update share).
+static int lookahead_sms(int64_t m1) {
+    static int base = -1;
+    if (base < 0) {
+        const char *e = getenv("GP_LOOKAHEAD_SMS");
+        const int v = e ? atoi(e) : 0;
+        base = (v > 0 && v < 128) ? v : 4;
     }
+    if (m1 < 8192) return base * 4;
+    if (m1 < 16384) return base * 2;
+    return base;
+}
+
+// Pending updates of rows [r0, r1) of block column k0 (width nb) into A.
+static int fold_rows(double *A, int64_t ld, int64_t np, int64_t k0, int64_t nb, int64_t r0,
+                     int64_t r1, const MixedWs &w, int64_t *info, cudaStream_t s) {
+    const int64_t rows = r1 - r0;
+    if (rows <= 0) return GP_OK;
+    dim3 g((unsigned)ceil_div(rows, 256 * 4) + 1, (unsigned)nb);
+    const int ev = prof_start(s);
+    // rows are counted from the block's first column: an offset r0 - k0 shifts the
+    // kernel's lower-triangle start (row >= column) accordingly
+    fold_delta2_kernel<<<g, 256, 0, s>>>(A + r0 + k0 * ld, ld, w.D + r0 + k0 * np, np, rows, nb,
+                                         r0 - k0, info);
+    GP_LAUNCH_CHECK();
+    prof_stop(ev, s, GP_PROF_FOLD, 0.0, 16.0 * (double)rows * nb);
+    return GP_OK;
+}
+
+// Block column k0 (width nb): fold the pending updates of its rows below
+// fold_end (k0 > 0; the rest is folded by the caller), factor the diagonal
+// block, and, when `inverse`, form W = L_kk^{-1}.
+static int diag_block(double *A, int64_t ld, int64_t np, int64_t k0, int64_t nb, int S,
+                      const MixedWs &w, double *W, bool inverse, int64_t *info, cudaStream_t s,
+                      int64_t fold_end = -1) {
+    double *Akk = A + k0 + k0 * ld;
+    if (k0 > 0) GP_TRY(fold_rows(A, ld, np, k0, nb, k0, fold_end < 0 ? np : fold_end, w, info, s));
     int ev = prof_start(s);
     GP_TRY(chol_fp64_tiled(Akk, ld, nb, k0, info, s, S == 3));
     prof_stop(ev, s, GP_PROF_DIAG, (double)nb * nb * nb / 3.0, 0.0);
@@ -210,13 +238,18 @@ int chol_mixed(double *A, int64_t ld, int64_t np, int S, void *ws, double *winv,
         if (cudaEventRecord(la->next_ready, s) != cudaSuccess ||
             cudaStreamWaitEvent(la->side, la->next_ready, 0) != cudaSuccess)
             return GP_ERR_CUDA;
-        GP_TRY(diag_block(A, ld, np, k1, nbn, S, w, W_of(k1), m1 > 0 || winv, info, la->side));
+        GP_TRY(diag_block(A, ld, np, k1, nbn, S, w, W_of(k1), m1 > 0 || winv, info, la->side,
+                          k1 + nbn));
         if (cudaEventRecord(la->diag_done, la->side) != cudaSuccess) return GP_ERR_CUDA;
+        // the rows below the next diagonal block: folded here on all SMs (a
+        // pass over memory), not on the few the side stream gets
+        GP_TRY(fold_rows(A, ld, np, k1, nbn, k1 + nbn, np, w, info, s));
         if (m1 > 0) {
             TcOperand opR = opA;
             opR.row_off = nbn;
             TcOut o2b{w.D + (k1 + nbn) + (k1 + nbn) * np, np, 2, -1.0, 0.0, 1, 0};
-            o2b.max_ctas = la->sms > 2 * LOOKAHEAD_SMS ? la->sms - LOOKAHEAD_SMS : 0;
+            const int keep = lookahead_sms(m1);
+            o2b.max_ctas = la->sms > 2 * keep ? la->sms - keep : 0;
             GP_TRY(tc_gemm(opR, opR, m1, m1, nb, o2b, 0, 0, info, s));
         }
         if (cudaStreamWaitEvent(s, la->diag_done, 0) != cudaSuccess) return GP_ERR_CUDA;
