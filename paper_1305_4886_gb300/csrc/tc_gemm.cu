@@ -96,6 +96,14 @@ struct TcGemmArgs {
     const int *ex_a, *ex_b;      // normalized slices: row exponents per 512-chunk, else null
     int64_t ex_ld_a, ex_ld_b;
     int64_t *info;
+    // three-slice kernel, chunked contraction into an FP64 output: C above is
+    // the double-float running sum (written, not read, by a tile's first
+    // chunk); the last chunk writes Cf = alpha_f64 (running sum + chunk)
+    // instead (a tile with no K range writes zeros)
+    int fuse_f64;
+    double *Cf;
+    int64_t ldcf;
+    double alpha_f64;
 };
 
 struct TileInfo {
@@ -107,7 +115,7 @@ struct TileInfo {
 // kchunk == 0, else the non-empty kchunk-aligned pieces of [kb_lo, kb_hi).
 __device__ __forceinline__ int tile_chunks(const TcGemmArgs &a, int kb_lo, int kb_hi) {
     if (a.kchunk <= 0) return 1;
-    if (kb_lo >= kb_hi) return 0;
+    if (kb_lo >= kb_hi) return a.fuse_f64 ? 1 : 0;
     return (kb_hi - 1) / a.kchunk - kb_lo / a.kchunk + 1;
 }
 
@@ -508,7 +516,8 @@ __device__ __forceinline__ void t3_fetch(const char *p, int64_t ld8, int cl, int
 // representable (a power of two down to 2^-149).
 __device__ __forceinline__ void t3_store(const TcGemmArgs &args, const float *h_, const float *l_,
                                          char *p, int64_t ld8, int cl, int lim, float fa, int ea,
-                                         int ebr, int lane0, const unsigned long long (&old)[T3_EG]) {
+                                         int ebr, int lane0, const unsigned long long (&old)[T3_EG],
+                                         char *pf, int64_t ld8f, bool to_f64) {
 #pragma unroll
     for (int j = 0; j < T3_EG; ++j) {
         const int eb = __shfl_sync(0xffffffffu, ebr, lane0 + j);
@@ -521,7 +530,15 @@ __device__ __forceinline__ void t3_store(const TcGemmArgs &args, const float *h_
             two_sum(ox, h, s1, e1);
             e1 = __fadd_rn(e1, __fadd_rn(oy, l));
             two_sum(s1, e1, hi, lo);
-            if (cl + j < lim) *reinterpret_cast<float2 *>(p + j * ld8) = make_float2(hi, lo);
+            if (to_f64) {
+                // the last chunk of a fused chunked contraction: FP64 out
+                double v = f32_to_f64(hi) + f32_to_f64(lo);
+                if (args.alpha_f64 == -1.0) v = -v;
+                else if (args.alpha_f64 != 1.0) v *= args.alpha_f64;
+                if (cl + j < lim) *reinterpret_cast<double *>(pf + j * ld8f) = v;
+            } else if (cl + j < lim) {
+                *reinterpret_cast<float2 *>(p + j * ld8) = make_float2(hi, lo);
+            }
         } else {
             // (h + l) 2^{e_a + e_b - 14}: the scaling and the conversions by
             // integer operations, one FP64 add (the FP64 pipe runs at 1/64
@@ -717,9 +734,18 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                 }
                 const int64_t ld8 = args.ldc * 8;
                 char *p_row = static_cast<char *>(args.C) + (row_ok ? (row + col0 * args.ldc) * 8 : 0);
+                // fused chunked FP64 output: the first chunk starts the running
+                // sum (no old values), the last one writes the FP64 result
+                const bool fresh = args.fuse_f64 && c == 0;
+                const bool to_f64 = args.fuse_f64 && c == nch - 1;
+                const bool read_old = need_old && !fresh;
+                const int64_t ld8f = args.ldcf * 8;
+                char *pf_row = (to_f64 && row_ok)
+                                   ? reinterpret_cast<char *>(args.Cf) + (row + col0 * args.ldcf) * 8
+                                   : nullptr;
                 // old values of this row into L2 while the unit's instructions
                 // run (one line request per column and lane pair)
-                if (need_old)
+                if (read_old)
                     for (int j = 0; j < lim; ++j)
                         asm volatile("prefetch.global.L2 [%0];" ::"l"(p_row + j * ld8));
                 // row exponents of this unit's 512-deep chunk: this thread's A
@@ -738,7 +764,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                         if (cm < args.N) eb[m] = args.ex_b[(args.b_row_off + cm) * args.ex_ld_b + chb];
                     }
                 }
-                const int flim = need_old ? lim : 0;  // columns whose old values are read
+                const int flim = read_old ? lim : 0;  // columns whose old values are read
                 const float fa = __fmul_rn(alpha_f, __int_as_float((ea + 127) << 23));
                 // a ring of T3_INFL output steps of old values; the first ones
                 // are in flight during the wait
@@ -828,7 +854,8 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                                      old[(st + T3_INFL - 1) % T3_INFL]);
                         const int cl = g * T3_EG;
                         t3_store(args, H + st * T3_EG, L + st * T3_EG, p_row + cl * ld8, ld8, cl,
-                                 lim, fa, ea, ebr, cl & 31, old[st % T3_INFL]);
+                                 lim, fa, ea, ebr, cl & 31, old[st % T3_INFL],
+                                 pf_row + cl * ld8f, ld8f, to_f64);
                     }
 #pragma unroll
                     for (int j = 0; j < T3_COLS - 16; ++j) L[j] = L[j + 16];
@@ -971,6 +998,9 @@ int tc_gemm(const TcOperand &A, const TcOperand &B, int64_t M, int64_t N, int64_
     // through the double-float buffer acc2.
     const bool deep = K > TC_CHUNK_K;
     const bool via_acc2 = deep && out.mode == 0;
+    // the three-slice kernel writes the FP64 result from the last chunk itself
+    // (no zeroing of acc2 before, no conversion pass after) when beta = 0
+    const bool fused = via_acc2 && A.S == 3 && out.beta == 0.0;
     if (deep) a.kchunk = (int)(TC_CHUNK_K / TC_BK);
     if (via_acc2) {
         if (!out.acc2) return GP_ERR_INVALID;
@@ -980,8 +1010,15 @@ int tc_gemm(const TcOperand &A, const TcOperand &B, int64_t M, int64_t N, int64_
         a.ldc = M;
         a.alpha = 1.0;
         a.beta = 0.0;
-        if (cudaMemsetAsync(out.acc2, 0, sizeof(float2) * (size_t)M * (size_t)N, s) != cudaSuccess)
+        if (fused) {
+            a.fuse_f64 = 1;
+            a.Cf = static_cast<double *>(out.C);
+            a.ldcf = out.ldc;
+            a.alpha_f64 = out.alpha;
+        } else if (cudaMemsetAsync(out.acc2, 0, sizeof(float2) * (size_t)M * (size_t)N, s) !=
+                   cudaSuccess) {
             return GP_ERR_CUDA;
+        }
     }
     a.tiles_m = (int)ceil_div(M, TC_BM);
     a.tiles_n = (int)ceil_div(N, TC_BN);
@@ -1024,7 +1061,7 @@ int tc_gemm(const TcOperand &A, const TcOperand &B, int64_t M, int64_t N, int64_
     else
         tc_gemm_kernel<2><<<grid, TC_THREADS, TC_SMEM, s>>>(ma, mb, a);
     GP_LAUNCH_CHECK();
-    if (via_acc2) {
+    if (via_acc2 && !fused) {
         dim3 g2((unsigned)N, (unsigned)ceil_div(M, 256));
         acc2_to_f64_kernel<<<g2, 256, 0, s>>>(static_cast<const float2 *>(out.acc2), M, N,
                                                out.alpha, out.beta,
