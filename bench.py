@@ -535,6 +535,7 @@ def run_ours(args, rank, world, local):
     elapsed_ms = e0.elapsed_time(e1)
     # every profiled launch of the timed region is recorded, or this raises
     prof = {c: gp.gp_prof_read(c) for c in gp.PROF_CLASSES}
+    roles = {c: gp.gp_prof_read(c) for c in gp.PROF_CONTRACT_ROLES}
     gp.gp_prof_enable(False)
     if int(info.item()) != 0:
         raise RuntimeError(f"timed steps failed, info={int(info.item())}")
@@ -630,6 +631,10 @@ def run_ours(args, rank, world, local):
         "per_step_ms": per_step,
         "per_step_ms_profiled_sum": sum(per_step.values()),
         "per_step_launches": {c: prof[c][1] / args.steps for c in prof},
+        "contract_by_role": {c: {"ms_per_step": roles[c][0] / args.steps,
+                                 "alg_tflops": (roles[c][2] / pairs / (roles[c][0] / 1e3) / 1e12)
+                                 if roles[c][0] > 0 and pairs else None}
+                             for c in roles},
         "cholesky_alg_flop": chol_alg,
         "y": f"L z with the {y_form} factor",
         "parallelism": "replicas" if world > 1 else "single GPU",

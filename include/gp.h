@@ -396,6 +396,11 @@ int64_t gp_launch_count(void);
 #define GP_PROF_PACK 7     /* FP64 -> 16-bit slice packing */
 #define GP_PROF_FOLD 8     /* double-float pending-update fold into the FP64
                               block column */
+/* The contractions of GP_PROF_CONTRACT by role (gp_prof_read of
+ * GP_PROF_CONTRACT sums all of them):                                     */
+#define GP_PROF_CONTRACT_CHOL 9    /* Cholesky panel solves and trailing updates */
+#define GP_PROF_CONTRACT_TRTRI 10  /* blocked inverse of the factor */
+#define GP_PROF_CONTRACT_LAUUM 11  /* C^{-1} = X^T X from the inverse factor */
 
 /* gp_prof_enable(1) clears the counters and brackets each later launch of
  * the classes above with a pair of CUDA events recorded on the launch's own

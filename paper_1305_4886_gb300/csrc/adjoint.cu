@@ -219,7 +219,11 @@ static int lauum_inplace(double *A, int64_t ld, int64_t np, GradWs &w, int64_t *
 int chol_inverse(double *A, int64_t ld, int64_t np, int precision, int S, void *ws,
                  const double *winv, int64_t *info, cudaStream_t s) {
     GradWs w = grad_layout(ws, np, precision, S);
-    GP_TRY(trtri_inplace(A, ld, np, w, winv, info, s));
+    {
+        ProfContractRole role(GP_PROF_CONTRACT_TRTRI);
+        GP_TRY(trtri_inplace(A, ld, np, w, winv, info, s));
+    }
+    ProfContractRole role(GP_PROF_CONTRACT_LAUUM);
     GP_TRY(lauum_inplace(A, ld, np, w, info, s));
     return GP_OK;
 }

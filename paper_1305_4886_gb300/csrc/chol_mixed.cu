@@ -200,6 +200,7 @@ static int chol_mixed_plain(double *A, int64_t ld, int64_t np, int S, const Mixe
 int chol_mixed(double *A, int64_t ld, int64_t np, int S, void *ws, double *winv, int64_t *info,
                cudaStream_t s, bool lookahead) {
     MixedWs w = mixed_layout(ws, np, S);
+    ProfContractRole role(GP_PROF_CONTRACT_CHOL);
     if (!lookahead) return chol_mixed_plain(A, ld, np, S, w, winv, info, s);
     LookaheadCtx *la = nullptr;
     GP_TRY(lookahead_ctx(&la));

@@ -10,6 +10,14 @@ struct KernParams;
 // prof.cu (event timing of selected launches; no-ops unless enabled)
 int prof_start(cudaStream_t s);
 void prof_stop(int idx, cudaStream_t s, int cls, double flops, double bytes);
+// the profiling class of the contractions issued by this host thread (a role
+// of GP_PROF_CONTRACT), set for a scope
+int prof_contract_class();
+struct ProfContractRole {
+    int prev;
+    explicit ProfContractRole(int cls);
+    ~ProfContractRole();
+};
 
 // fill.cu
 int launch_cov_fill(const double *d_x, int64_t n, int64_t np, const KernParams &kp, double *d_C,

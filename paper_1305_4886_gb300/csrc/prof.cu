@@ -71,6 +71,18 @@ void prof_stop(int idx, cudaStream_t s, int cls, double flops, double bytes) {
     }
 }
 
+thread_local int t_contract_cls = GP_PROF_CONTRACT;
+int prof_contract_class() { return t_contract_cls; }
+ProfContractRole::ProfContractRole(int cls) : prev(t_contract_cls) { t_contract_cls = cls; }
+ProfContractRole::~ProfContractRole() { t_contract_cls = prev; }
+
+static bool class_matches(int want, int have) {
+    if (want == have) return true;
+    return want == GP_PROF_CONTRACT &&
+           (have == GP_PROF_CONTRACT_CHOL || have == GP_PROF_CONTRACT_TRTRI ||
+            have == GP_PROF_CONTRACT_LAUUM);
+}
+
 }  // namespace gp
 
 using namespace gp;
@@ -92,7 +104,7 @@ int gp_prof_read(int cls, double *ms_total, int64_t *launches, double *flops, do
     int64_t cnt = 0;
     for (size_t i = 0; i < g_used; ++i) {
         Rec &r = g_pool[i];
-        if (r.cls != cls) continue;
+        if (r.cls < 0 || !class_matches(cls, r.cls)) continue;
         if (cudaEventSynchronize(r.b) != cudaSuccess) return GP_ERR_CUDA;
         float t = 0.0f;
         if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) return GP_ERR_CUDA;

@@ -1082,7 +1082,7 @@ int tc_gemm(const TcOperand &A, const TcOperand &B, int64_t M, int64_t N, int64_
             if (tri_k && c - tri_off > 0) keff = K - (c - tri_off) > 0 ? K - (c - tri_off) : 0;
             useful += (double)rows * (double)keff;
         }
-        prof_stop(ev, s, GP_PROF_CONTRACT, 2.0 * np * useful, 0.0);
+        prof_stop(ev, s, prof_contract_class(), 2.0 * np * useful, 0.0);
     }
     return GP_OK;
 }

@@ -518,6 +518,8 @@ def gp_syrk_lower(C, ldc, P, ldp, m, k, precision, ws, info=None, stream=None):
 
 PROF_CLASSES = {"contract": 0, "fill": 1, "residual": 2, "grad": 3, "diag_chol": 4,
                 "diag_inv": 5, "solve": 6, "pack": 7, "fold": 8}
+# roles of the "contract" class (gp_prof_read of "contract" sums them)
+PROF_CONTRACT_ROLES = {"contract_chol": 9, "contract_trtri": 10, "contract_lauum": 11}
 
 
 def gp_launch_count():
@@ -532,7 +534,7 @@ def gp_prof_read(cls):
     """(total ms, launches, flops, bytes) of one profiled kernel class.
     Raises if any profiled launch went unrecorded: partial sums are not
     returned."""
-    c = PROF_CLASSES[cls] if isinstance(cls, str) else int(cls)
+    c = ({**PROF_CLASSES, **PROF_CONTRACT_ROLES}[cls] if isinstance(cls, str) else int(cls))
     ms, fl, by = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     cnt = ctypes.c_int64()
     st = lib().gp_prof_read(c, ctypes.byref(ms), ctypes.byref(cnt), ctypes.byref(fl),
