@@ -24,6 +24,11 @@ from .gp_oracle import (  # noqa: F401
     cross_cov,
     predict,
     predict_from_data,
+    bessel_k,
+    matern2,
+    matern2_dlogrho,
+    prod_cov_fill,
+    prod_loglik_grad,
     philox4x64,
     normals,
     simulate,

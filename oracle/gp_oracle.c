@@ -560,3 +560,146 @@ int orc_simulate_conditional(const double *x, int64_t n, const double *xs, int64
     free(K); free(W); free(S); free(mean); free(E);
     return st;
 }
+
+/*
+ * The paper's example covariance (Sec. 4.2): the flux Y_i at phase t_i and
+ * log wavelength w_i is a Gaussian-process value plus a random effect of its
+ * phase plus measurement error of known variance v_i, so
+ *   C_ij = s2 k(|t_i - t_j| / rho_t) k(|w_i - w_j| / rho_w)
+ *          + tau2 [t_i == t_j] + v_i [i == j],
+ * a separable product of two Matern correlations of smoothness nu = 2, taken
+ * here in the Rasmussen & Williams scaling a = sqrt(2 nu) u = 2u:
+ *   k(u) = (2^{1-nu} / Gamma(nu)) a^nu K_nu(a) = a^2 K_2(a) / 2,  k(0) = 1.
+ * Its derivative in log rho is -u k'(u) = a^3 K_1(a) / 2 (from
+ * d/da [a^2 K_2(a)] = -a^2 K_1(a)).
+ *
+ * K_nu(x), x > 0, from its integral representation
+ *   K_nu(x) = int_0^inf exp(-x cosh s) cosh(nu s) ds
+ *           = exp(-x) int_0^inf exp(-2 x sinh^2(s/2)) cosh(nu s) ds
+ * by the trapezoidal rule with step min(1/16, 1/(4 sqrt(x))) (the integrand
+ * is analytic in the strip |Im s| < pi/2 and decays double exponentially, so
+ * the rule's error falls like exp(-pi^2 / h); for large x it is a peak of
+ * width about 1/sqrt(x), which the step resolves), summed until the terms
+ * vanish.
+ */
+double orc_bessel_k(double nu, double x) {
+    if (!(x > 0.0)) return INFINITY;
+    /* exp(-x cosh s) = exp(-x) exp(-2 x sinh^2(s/2)): the factor exp(-x) is
+       taken out so that large x keeps its relative accuracy */
+    /* for large x the integrand is a peak of width about 1/sqrt(x) at s = 0:
+       the step shrinks with it (error about exp(-2 pi^2 / (x h^2))) */
+    const double h = fmin(1.0 / 16.0, 0.25 / sqrt(x));
+    nsum_t s;
+    ns_init(&s);
+    ns_add(&s, 0.5);
+    for (int64_t k = 1; k < 100000; ++k) {
+        const double t = h * (double)k;
+        const double sh = sinh(0.5 * t);
+        const double e = 2.0 * x * sh * sh;
+        const double term = exp(-e) * cosh(nu * t);
+        ns_add(&s, term);
+        if (term < 1e-30 * ns_get(&s) && e > 1.0) break;
+    }
+    return exp(-x) * h * ns_get(&s);
+}
+
+/* k(u) = a^2 K_2(a) / 2, a = 2u (Matern nu = 2) */
+double orc_matern2(double u) {
+    if (u == 0.0) return 1.0;
+    const double a = 2.0 * u;
+    return 0.5 * a * a * orc_bessel_k(2.0, a);
+}
+
+/* -u k'(u) = a^3 K_1(a) / 2 */
+double orc_matern2_dlogrho(double u) {
+    if (u == 0.0) return 0.0;
+    const double a = 2.0 * u;
+    return 0.5 * a * a * a * orc_bessel_k(1.0, a);
+}
+
+/* C of the product model, full symmetric n x n (v may be NULL: all zero) */
+void orc_prod_cov_fill(const double *x, int64_t n, const double *v, double s2, double rho_t,
+                       double rho_w, double tau2, double *C) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t j = 0; j < n; ++j) {
+            const double dt = fabs(x[2 * i] - x[2 * j]), dw = fabs(x[2 * i + 1] - x[2 * j + 1]);
+            double c = s2 * orc_matern2(dt / rho_t) * orc_matern2(dw / rho_w);
+            if (dt == 0.0) c += tau2;
+            if (i == j && v) c += v[i];
+            C[i * n + j] = c;
+        }
+    }
+}
+
+/*
+ * Log-likelihood (out[0..2] as orc_loglik) and its gradient with respect to
+ * (log s2, log rho_t, log rho_w, log tau2) of the product model:
+ *   dC/dlog s2    = s2 k_t k_w
+ *   dC/dlog rho_t = s2 (-u_t k'(u_t)) k_w,   dC/dlog rho_w = s2 k_t (-u_w k'(u_w))
+ *   dC/dlog tau2  = tau2 [t_i == t_j]
+ *   g_j = 1/2 alpha^T dC_j alpha - 1/2 sum_{i,k} W_ik (dC_j)_ik,  W = C^{-1}.
+ */
+int orc_prod_loglik_grad(const double *x, const double *y, const double *mu, const double *v,
+                         int64_t n, double s2, double rho_t, double rho_w, double tau2,
+                         double *out, double *alpha, double *grad, int64_t *info) {
+    if (info) *info = 0;
+    if (n < 1 || !(s2 > 0.0) || !(rho_t > 0.0) || !(rho_w > 0.0) || !(tau2 >= 0.0))
+        return ORC_INVALID;
+    for (int64_t i = 0; i < 2 * n; ++i)
+        if (!isfinite(x[i])) return ORC_INVALID;
+    const size_t nn = (size_t)n * (size_t)n;
+    double *C = (double *)malloc(sizeof(double) * nn);
+    double *L = (double *)malloc(sizeof(double) * nn);
+    double *r = (double *)malloc(sizeof(double) * (size_t)n);
+    double *w = (double *)malloc(sizeof(double) * (size_t)n);
+    double *a = (double *)malloc(sizeof(double) * (size_t)n);
+    orc_prod_cov_fill(x, n, v, s2, rho_t, rho_w, tau2, C);
+    memcpy(L, C, sizeof(double) * nn);
+    const int64_t f = orc_cholesky(L, n);
+    if (f != 0) {
+        if (info) *info = f;
+        out[0] = out[1] = out[2] = NAN;
+        if (grad) grad[0] = grad[1] = grad[2] = grad[3] = NAN;
+        free(C); free(L); free(r); free(w); free(a);
+        return ORC_NOT_PD;
+    }
+    for (int64_t i = 0; i < n; ++i) r[i] = y[i] - (mu ? mu[i] : 0.0);
+    orc_forward(L, n, r, w);
+    const double logdet = orc_logdet(L, n), q = orc_dot(w, w, n);
+    out[0] = -0.5 * logdet - 0.5 * q - 0.5 * (double)n * log(2.0 * M_PI);
+    out[1] = logdet;
+    out[2] = q;
+    orc_backward(L, n, w, a);
+    if (alpha) memcpy(alpha, a, sizeof(double) * (size_t)n);
+    if (grad) {
+        double *W = (double *)malloc(sizeof(double) * nn);
+        orc_inverse_from_chol(L, n, W);
+        double *part = (double *)calloc((size_t)n * 4, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 16)
+        for (int64_t i = 0; i < n; ++i) {
+            nsum_t g[4];
+            for (int c = 0; c < 4; ++c) ns_init(&g[c]);
+            for (int64_t j = 0; j < n; ++j) {
+                const double dt = fabs(x[2 * i] - x[2 * j]), dw = fabs(x[2 * i + 1] - x[2 * j + 1]);
+                const double kt = orc_matern2(dt / rho_t), kw = orc_matern2(dw / rho_w);
+                const double d[4] = {s2 * kt * kw, s2 * orc_matern2_dlogrho(dt / rho_t) * kw,
+                                     s2 * kt * orc_matern2_dlogrho(dw / rho_w),
+                                     dt == 0.0 ? tau2 : 0.0};
+                const double cbar = 0.5 * (a[i] * a[j] - W[i * n + j]);
+                for (int c = 0; c < 4; ++c) ns_add(&g[c], cbar * d[c]);
+            }
+            for (int c = 0; c < 4; ++c) part[4 * i + c] = ns_get(&g[c]);
+        }
+        for (int c = 0; c < 4; ++c) {
+            nsum_t s;
+            ns_init(&s);
+            for (int64_t i = 0; i < n; ++i) ns_add(&s, part[4 * i + c]);
+            grad[c] = ns_get(&s);
+        }
+        free(part);
+        free(W);
+    }
+    free(C); free(L); free(r); free(w); free(a);
+    return ORC_OK;
+}

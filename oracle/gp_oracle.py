@@ -88,6 +88,15 @@ def _load():
             lib.orc_simulate_conditional.argtypes = [p, i64, p, i64, ci, d, d, p, p, d, i64, u64,
                                                      u64, p, p]
             lib.orc_simulate_conditional.restype = ci
+            lib.orc_bessel_k.argtypes = [d, d]
+            lib.orc_bessel_k.restype = d
+            lib.orc_matern2.argtypes = [d]
+            lib.orc_matern2.restype = d
+            lib.orc_matern2_dlogrho.argtypes = [d]
+            lib.orc_matern2_dlogrho.restype = d
+            lib.orc_prod_cov_fill.argtypes = [p, i64, p, d, d, d, d, p]
+            lib.orc_prod_loglik_grad.argtypes = [p, p, p, p, i64, d, d, d, d, p, p, p, p]
+            lib.orc_prod_loglik_grad.restype = ci
             lib.orc_num_threads.restype = ci
             lib.orc_set_threads.argtypes = [ci]
             _lib = lib
@@ -324,3 +333,55 @@ def simulate_conditional(x, xs, kernel, s2, rho, L, alpha, r, seed, first=0, mu_
     if st == 1:
         raise OracleNotPD(int(info.value))
     return out
+
+
+def bessel_k(nu, x):
+    """K_nu(x) by the trapezoidal rule on its integral representation."""
+    return _load().orc_bessel_k(float(nu), float(x))
+
+
+def matern2(u):
+    """Matern nu = 2 correlation k(u) = a^2 K_2(a) / 2, a = 2u."""
+    return _load().orc_matern2(float(u))
+
+
+def matern2_dlogrho(u):
+    """-u k'(u) = a^3 K_1(a) / 2 for the Matern nu = 2 correlation."""
+    return _load().orc_matern2_dlogrho(float(u))
+
+
+def prod_cov_fill(x, s2, rho_t, rho_w, tau2, v=None):
+    """C of the paper's example model (Sec. 4.2): product Matern nu = 2 in
+    (phase, log wavelength), tau2 between equal phases, v_i on the diagonal."""
+    x = _f64(x)
+    n = x.shape[0]
+    vv = _f64(v) if v is not None else None
+    C = np.empty((n, n))
+    _load().orc_prod_cov_fill(_ptr(x), n, _ptr(vv) if vv is not None else None, s2, rho_t, rho_w,
+                              tau2, _ptr(C))
+    return C
+
+
+def prod_loglik_grad(x, y, s2, rho_t, rho_w, tau2, v=None, mu=None, want_grad=True):
+    """dict(loglik, logdet, quad, alpha[, grad]) of the product model; grad
+    with respect to (log s2, log rho_t, log rho_w, log tau2)."""
+    x = _f64(x)
+    y = _f64(y)
+    n = x.shape[0]
+    m, mp = _mu_arg(mu, n)
+    vv = _f64(v) if v is not None else None
+    out = np.empty(3)
+    alpha = np.empty(n)
+    grad = np.empty(4) if want_grad else None
+    info = ctypes.c_int64(0)
+    st = _load().orc_prod_loglik_grad(_ptr(x), _ptr(y), mp, _ptr(vv) if vv is not None else None,
+                                      n, s2, rho_t, rho_w, tau2, _ptr(out), _ptr(alpha),
+                                      _ptr(grad) if want_grad else None, ctypes.byref(info))
+    if st == 2:
+        raise ValueError("invalid oracle arguments")
+    if st == 1:
+        raise OracleNotPD(int(info.value))
+    res = dict(loglik=out[0], logdet=out[1], quad=out[2], alpha=alpha)
+    if want_grad:
+        res["grad"] = grad
+    return res
