@@ -77,7 +77,7 @@ def parse():
     ap.add_argument("--batched-steps", type=int, default=10,
                     help="timed graph replays of the batched workload")
     ap.add_argument("--case", default=None,
-                    choices=["fill", "loglik", "loglik_grad", "syrk", "predict"],
+                    choices=["fill", "loglik", "loglik_grad", "syrk", "predict", "product"],
                     help="run one small invocation of a single step (--n, --precision, --reps) "
                          "for kernel captures, print its CUDA-event times, then exit")
     ap.add_argument("--reps", type=int, default=3)
@@ -835,6 +835,17 @@ def run_case(args):
                          device="cuda")
         fn = lambda: gp.gp_syrk_lower(C, n, P, n, n, 512, prec, ws, info)  # noqa: E731
         work = {"flop": float(n) * n * 512}
+    elif args.case == "product":
+        # the paper's example model on its data set's shape: 25 phases x n/25
+        # log wavelengths (n = 67,275 is the paper's 25 x 2691)
+        q = inputs.product_grid(25, max(1, n // 25))
+        xq = torch.as_tensor(q.x, device="cuda")
+        yq = torch.as_tensor(q.z, device="cuda") * 0.1
+        vq = torch.as_tensor(q.meta["v"], device="cuda")
+        wsq = gp.workspace(q.n, prec, want_grad=True)
+        fn = lambda: gp.loglik_product(xq, yq, q.s2, q.rho, q.meta["rho_w"], q.tau2, v=vq,  # noqa: E731
+                                       precision=prec, ws=wsq)
+        work = {"flop": float(q.n) ** 3, "n_product": q.n}
     else:
         m = max(1, n // 2)
         xs = torch.as_tensor(inputs.uniform_points(m, 4242), device="cuda")

@@ -174,6 +174,38 @@ int gp_loglik_grad(const double *d_x, const double *d_y, const double *d_mu, int
                    const gp_params *prm, int precision, void *d_ws, size_t ws_bytes,
                    double *d_out, double *d_alpha, double *d_grad, int64_t *d_info, void *stream);
 
+/* The paper's example model (Sec. 4.2): observation i at phase t_i and log
+ * wavelength w_i (the two location coordinates, interleaved as for the other
+ * entry points) is a Gaussian-process value plus a random effect of its
+ * phase plus measurement error of known variance v_i:
+ *   C_ij = sigma2 k(|t_i - t_j| / rho_t) k(|w_i - w_j| / rho_w)
+ *          + tau2 [t_i == t_j] + v_i [i == j],
+ * k the Matern correlation of smoothness 2 in the Rasmussen & Williams
+ * scaling: k(u) = a^2 K_2(a) / 2 with a = 2u (K_2 the modified Bessel
+ * function of the second kind; entries with a >= 48, below 1e-18 sigma2,
+ * are 0).  "Same phase" is exact equality of the first coordinate.        */
+typedef struct {
+    double sigma2; /* variance of the latent process, > 0 */
+    double rho_t;  /* range in the first coordinate (phase), > 0 */
+    double rho_w;  /* range in the second coordinate (log wavelength), > 0 */
+    double tau2;   /* variance of the per-phase random effect, >= 0 */
+} gp_product_params;
+
+/* Log-likelihood of the product model, and its gradient with respect to
+ * (log sigma2, log rho_t, log rho_w, log tau2) when d_grad (4 values) is not
+ * NULL.  d_v: n known variances (>= 0), or NULL for none; d_mu, d_out,
+ * d_alpha, d_info as gp_loglik.  d_ws: gp_workspace_bytes(n, precision,
+ * d_grad != NULL).  Every precision form factors and inverts as for the
+ * other models; this model's covariance entries (fill, the refinement's
+ * C alpha, the gradient's dC) are evaluated in FP64 in every form, from
+ * piecewise Chebyshev tables of a^2 K_2(a) / 2 and a^3 K_1(a) / 2 built once
+ * per process on the host (about 1e-15 relative).  Non-finite locations or
+ * variances, or a negative variance, set *d_info = -2.                    */
+int gp_loglik_product(const double *d_x, const double *d_y, const double *d_mu, const double *d_v,
+                      int64_t n, const gp_product_params *prm, int precision, void *d_ws,
+                      size_t ws_bytes, double *d_out, double *d_alpha, double *d_grad,
+                      int64_t *d_info, void *stream);
+
 /* Batched log-likelihood + gradient of nprob independent problems of uneven
  * n (independent data sets or a theta grid; the paper evaluates one
  * problem per session, Sec. 2.3.4).  Host arrays, one entry per problem:

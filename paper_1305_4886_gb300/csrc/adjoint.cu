@@ -159,7 +159,8 @@ static GradWs grad_layout(void *base, int64_t np, int precision, int S) {
     w.T = reinterpret_cast<double *>(take(sizeof(double) * GNB * (size_t)np));
     w.Wd = reinterpret_cast<double *>(take(sizeof(double) * GNB * GNB));
     w.tmp = reinterpret_cast<double *>(take(sizeof(double) * TB * GNB));
-    w.part = reinterpret_cast<double *>(take(sizeof(double) * 3 * (size_t)ntiles64(np)));
+    // per-tile gradient shares: 3 per tile, 4 for the product model
+    w.part = reinterpret_cast<double *>(take(sizeof(double) * 4 * (size_t)ntiles64(np)));
     if (!f64) w.acc2 = take(sizeof(float) * 2 * GNB * (size_t)np);
     w.bytes = a256(off);
     return w;
@@ -400,6 +401,7 @@ int grad_contract(const double *d_x, int64_t n, int64_t np, const KernParams &kp
                   int64_t ld, const double *alpha, void *ws, int precision, int S, double *grad,
                   const int64_t *info, cudaStream_t s) {
     GradWs w = grad_layout(ws, np, precision, S);
+    if (kp.product) return prod_grad(d_x, n, np, kp, W, ld, alpha, w.part, grad, info, s);
     const int64_t nt = ntiles64(np);
     const int ev = prof_start(s);
     if (kp.use_df)

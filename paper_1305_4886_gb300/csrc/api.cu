@@ -240,6 +240,49 @@ int gp_loglik_grad(const double *d_x, const double *d_y, const double *d_mu, int
 }
 
 // ---------------------------------------------------------------------------
+// The paper's example model (product Matern nu = 2, per-phase random effect,
+// known per-point variances): the common path with the product model's fill,
+// refinement product and gradient (product.cu).
+// ---------------------------------------------------------------------------
+static bool product_params_ok(const gp_product_params *p) {
+    if (!p) return false;
+    if (!(p->sigma2 > 0.0) || !(p->rho_t > 0.0) || !(p->rho_w > 0.0) || !(p->tau2 >= 0.0))
+        return false;
+    return isfinite(p->sigma2) && isfinite(p->rho_t) && isfinite(p->rho_w) && isfinite(p->tau2);
+}
+
+int gp_loglik_product(const double *d_x, const double *d_y, const double *d_mu, const double *d_v,
+                      int64_t n, const gp_product_params *prm, int precision, void *d_ws,
+                      size_t ws_bytes, double *d_out, double *d_alpha, double *d_grad,
+                      int64_t *d_info, void *stream) {
+    if (n < 1 || !d_x || !d_y || !d_out || !d_info || !product_params_ok(prm) ||
+        !precision_ok(precision))
+        return GP_ERR_INVALID;
+    const int want_grad = d_grad ? 1 : 0;
+    LoglikWs w = loglik_ws_layout(d_ws, n, precision, want_grad);
+    if (!d_ws || ws_bytes < w.bytes) return GP_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t np = padded(n);
+    gp_params base{GP_KERNEL_EXP, prm->sigma2, 1.0, prm->tau2};
+    KernParams kp = make_kern(base, false);
+    kp.product = 1;
+    kp.prod_st = 2.0 / prm->rho_t;  // Matern nu = 2: a = sqrt(2 nu) d / rho
+    kp.prod_sw = 2.0 / prm->rho_w;
+    kp.prod_v = d_v;
+    kp.diag = prm->sigma2 + prm->tau2;
+    GP_TRY(loglik_core(d_x, d_y, d_mu, n, kp, precision, w, d_out, d_info, s));
+    if (want_grad) {
+        GP_TRY(chol_inverse(w.A, np, np, precision, slices_of(precision), w.chol, w.winv, d_info, s));
+        GP_TRY(grad_contract(d_x, n, np, kp, w.A, np, w.v, w.chol, precision, slices_of(precision),
+                             d_grad, d_info, s));
+    }
+    if (d_alpha &&
+        cudaMemcpyAsync(d_alpha, w.v, sizeof(double) * n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return GP_ERR_CUDA;
+    return GP_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Batched evaluation: independent problems on a pool of library streams,
 // forked from and joined back to the caller's stream with events, so that a
 // capture of the caller's stream records the whole batch as one graph.

@@ -103,6 +103,7 @@ __global__ void __launch_bounds__(256) cov_fill_df_kernel(const double2 *__restr
 
 int launch_cov_fill(const double *d_x, int64_t n, int64_t np, const KernParams &kp, double *d_C,
                     int64_t ldc, int64_t *d_info, cudaStream_t s) {
+    if (kp.product) return prod_fill(d_x, n, np, kp, d_C, ldc, d_info, s);
     const int64_t T = np / TB;
     const int64_t ntiles = T * (T + 1) / 2;
     if (ntiles > 0x7fffffffLL) return GP_ERR_INVALID;

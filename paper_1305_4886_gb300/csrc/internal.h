@@ -91,6 +91,15 @@ int refine_alpha(const double *d_x, int64_t n, int64_t np, const KernParams &kp,
                  double *stats, int *conv, int *tsync, int max_evals, double tol, int64_t *info,
                  cudaStream_t st);
 
+// product.cu (the product model: fill, C alpha for the refinement, 4-component gradient)
+int prod_fill(const double *d_x, int64_t n, int64_t np, const KernParams &kp, double *d_C,
+              int64_t ldc, int64_t *d_info, cudaStream_t s);
+int prod_matvec(const double *d_x, int64_t n, int64_t np, const KernParams &kp, const double *a,
+                double *acc, const int *skip, const int64_t *info, cudaStream_t s);
+int prod_grad(const double *d_x, int64_t n, int64_t np, const KernParams &kp, const double *W,
+              int64_t ld, const double *alpha, double *part, double *grad, const int64_t *info,
+              cudaStream_t s);
+
 // predict.cu (kriging mean and variance at new locations)
 size_t predict_ws_bytes(int64_t n, int64_t m, int want_var);
 int predict_run(const double *d_x, int64_t n, const double *d_xs, int64_t m, const KernParams &kp,

@@ -36,6 +36,11 @@ struct KernParams {
     double tab[EXP_TAB];  // 2^(-j/64)
     int use_df;           // evaluate off-diagonal entries in double-float (FP32 pipe)
     KernDf kd;
+    // the product model of product.cu (its fill, C alpha and gradient replace
+    // the ones above): scales 2 / rho_t, 2 / rho_w and the per-point variances
+    int product = 0;
+    double prod_st = 0.0, prod_sw = 0.0;
+    const double *prod_v = nullptr;
 };
 
 // use_df: the tensor-core forms, whose operand slices carry 2^-32 of the row

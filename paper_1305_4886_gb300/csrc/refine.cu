@@ -200,7 +200,9 @@ int cov_matvec(const double *d_x, int64_t n, int64_t np, const KernParams &kp, c
     if (cudaMemsetAsync(acc, 0, sizeof(double) * n, s) != cudaSuccess) return GP_ERR_CUDA;
     const int64_t T = np / TB;
     const int ev = prof_start(s);
-    if (kp.use_df)
+    if (kp.product)
+        GP_TRY(prod_matvec(d_x, n, np, kp, a, acc, skip, info, s));
+    else if (kp.use_df)
         cov_matvec_df_kernel<<<(unsigned)(T * (T + 1) / 2), 256, 0, s>>>(
             reinterpret_cast<const double2 *>(d_x), n, kp, a, acc, skip, info);
     else

@@ -31,6 +31,7 @@ SYMBOLS = [
     "gp_mult_chol",
     "gp_loglik",
     "gp_loglik_grad",
+    "gp_loglik_product",
     "gp_batched_workspace_bytes",
     "gp_loglik_grad_batched",
     "gp_predict_workspace_bytes",
@@ -61,6 +62,11 @@ SYMBOLS = [
 class GpParams(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("sigma2", ctypes.c_double),
                 ("rho", ctypes.c_double), ("tau2", ctypes.c_double)]
+
+
+class GpProductParams(ctypes.Structure):
+    _fields_ = [("sigma2", ctypes.c_double), ("rho_t", ctypes.c_double),
+                ("rho_w", ctypes.c_double), ("tau2", ctypes.c_double)]
 
 
 class GpError(RuntimeError):
@@ -118,6 +124,9 @@ def lib():
             L.gp_mult_chol.argtypes = [p, i64, i64, p, p, p]
             L.gp_loglik.argtypes = [p, p, p, i64, PP, ci, p, sz, p, p, p, p]
             L.gp_loglik_grad.argtypes = [p, p, p, i64, PP, ci, p, sz, p, p, p, p, p]
+            L.gp_loglik_product.argtypes = [p, p, p, p, i64, ctypes.POINTER(GpProductParams), ci,
+                                            p, sz, p, p, p, p, p]
+            L.gp_loglik_product.restype = ci
             L.gp_batched_workspace_bytes.argtypes = [ci, p, ci]
             L.gp_batched_workspace_bytes.restype = sz
             L.gp_loglik_grad_batched.argtypes = [ci, p, p, p, p, p, ci, p, sz, p, p, p, p]
@@ -503,6 +512,38 @@ def gp_loglik_grad(x, y, mu, n, prm, precision, ws, out, alpha, grad, info, stre
     _check(lib().gp_loglik_grad(_f64(x), _f64(y), _f64(mu), int(n), ctypes.byref(prm),
                                 _prec(precision), _ptr(ws), wsb, _f64(out), _f64(alpha),
                                 _f64(grad), _ptr(info), _stream(stream)), "gp_loglik_grad")
+
+
+def gp_loglik_product(x, y, mu, v, n, prm, precision, ws, out, alpha, grad, info, stream=None):
+    wsb = ws.numel() * ws.element_size()
+    _check(lib().gp_loglik_product(_f64(x), _f64(y), _f64(mu), _f64(v), int(n), ctypes.byref(prm),
+                                   _prec(precision), _ptr(ws), wsb, _f64(out), _f64(alpha),
+                                   _f64(grad), _ptr(info), _stream(stream)), "gp_loglik_product")
+
+
+def loglik_product(x, y, sigma2, rho_t, rho_w, tau2, v=None, mu=None, precision="fp64",
+                   want_grad=True, ws=None, check=True):
+    """The paper's example model on the device: dict of device tensors {out,
+    grad (4: d/d log(sigma2, rho_t, rho_w, tau2)) or None, alpha, info, ws}."""
+    n = x.shape[0]
+    dev = x.device
+    if ws is None:
+        ws = workspace(n, precision, want_grad, dev)
+    out = torch.empty(4, dtype=torch.float64, device=dev)
+    grad = torch.empty(4, dtype=torch.float64, device=dev) if want_grad else None
+    alpha = torch.empty(n, dtype=torch.float64, device=dev)
+    info = torch.zeros(1, dtype=torch.int64, device=dev)
+    mu_t = None
+    if mu is not None:
+        mu_t = mu if torch.is_tensor(mu) else torch.full((n,), float(mu), dtype=torch.float64,
+                                                         device=dev)
+    prm = GpProductParams(float(sigma2), float(rho_t), float(rho_w), float(tau2))
+    gp_loglik_product(x, y, mu_t, v, n, prm, precision, ws, out, alpha, grad, info)
+    if check:
+        iv = int(info.item())
+        if iv != 0:
+            raise GpDeviceError(iv)
+    return dict(out=out, grad=grad, alpha=alpha, info=info, ws=ws)
 
 
 def gp_syrk_workspace_bytes(m, k, precision="mixed_f16"):

@@ -124,3 +124,24 @@ def config5(nprob=512, n_lo=256, n_hi=4096):
         probs.append(Problem("batch-%d" % i, n, kern, float(s2[i]), float(rho[i]),
                              float(tau2[i]), x, 0.0, None, z))
     return probs
+
+
+def product_grid(n_t=25, n_w=2691, seed=48866):
+    """The shape of the paper's example data set (Sec. 4.1: 25 spectra of a
+    supernova at phases between -15 and 24 days, 2691 wavelengths each,
+    n = 67,275), synthetic: phases sorted uniform in [-15, 24] days, log
+    wavelengths on an even grid over [log 3500, log 7000] (angstrom), point
+    (t, w) = (phase, log wavelength) phase-major; known measurement-error
+    variances v_i uniform in [0.5e-5, 2e-5]; parameters at the maximum-
+    likelihood values the paper reports for its fit (Sec. 4.3: sigma2 =
+    0.0071, rho_t = 2.33, rho_w = 0.0089, tau2 = 2.6e-5); y = L z."""
+    rng = np.random.default_rng(seed)
+    t = np.sort(rng.uniform(-15.0, 24.0, size=n_t))
+    w = np.linspace(np.log(3500.0), np.log(7000.0), n_w)
+    x = np.stack([np.repeat(t, n_w), np.tile(w, n_t)], axis=1)
+    n = n_t * n_w
+    v = rng.uniform(0.5e-5, 2e-5, size=n)
+    p = Problem("product-%dx%d" % (n_t, n_w), n, "product_matern2", 0.0071, 2.33, 2.6e-5, x, 0.0,
+                None, np.random.default_rng(seed + 100).standard_normal(n))
+    p.meta = {"rho_w": 0.0089, "v": v, "n_t": n_t, "n_w": n_w}
+    return p
