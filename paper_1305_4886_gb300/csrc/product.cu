@@ -141,10 +141,21 @@ struct ProdPar {
     const double *v;          // per-point variances (nullable)
 };
 
+// The phase factor k(|t_i - t_j| / rho_t) of the last pair a thread saw: rows
+// and columns of a tile mostly share their phase (the data are phase by
+// phase), so the factor is reused instead of re-evaluated.
+struct PhaseMemo {
+    double dt = -1.0, kt = 0.0, gt = 0.0;
+};
+
 __device__ __forceinline__ double prod_entry(const M2Tab &T, const ProdPar &p, double2 xi,
-                                             double2 xj) {
+                                             double2 xj, PhaseMemo &m) {
     const double dt = fabs(xi.x - xj.x), dw = fabs(xi.y - xj.y);
-    double c = p.s2 * m2_eval(T, 0, dt * p.st) * m2_eval(T, 0, dw * p.sw);
+    if (dt != m.dt) {
+        m.dt = dt;
+        m.kt = m2_eval(T, 0, dt * p.st);
+    }
+    double c = p.s2 * m.kt * m2_eval(T, 0, dw * p.sw);
     if (dt == 0.0) c += p.tau2;
     return c;
 }
@@ -179,16 +190,19 @@ __global__ void __launch_bounds__(256) prod_fill_kernel(const double2 *__restric
     const int64_t i = row0 + r;
     const double2 xi = i < n ? x[i] : make_double2(0.0, 0.0);
     double *col = C + i;
+    PhaseMemo memo;
     for (int c = cg; c < TB; c += 4) {
         const int64_t j = col0 + c;
         double v;
-        if (i < n && j < n) v = (i == j) ? prod_diag(p, i) : prod_entry(T, p, xi, xc[c]);
+        if (i < n && j < n) v = (i == j) ? prod_diag(p, i) : prod_entry(T, p, xi, xc[c], memo);
         else v = (i == j) ? 1.0 : 0.0;
         col[j * ldc] = v;
     }
 }
 
-// acc += C a over one lower tile (each pair once, applied to both rows).
+// acc += C a over one lower tile (each pair once, applied to both rows):
+// row sums in registers, column sums by warp reductions (one lane writes each
+// half-column partial), then one FP64 atomic per row and column.
 __global__ void __launch_bounds__(256) prod_matvec_kernel(const double2 *__restrict__ x, int64_t n,
                                                           ProdPar p,
                                                           const __grid_constant__ M2Tab T,
@@ -197,39 +211,44 @@ __global__ void __launch_bounds__(256) prod_matvec_kernel(const double2 *__restr
                                                           const int64_t *info) {
     __shared__ double2 xc[TB];
     __shared__ double ac[TB];
-    __shared__ double colsum[4][TB];
+    __shared__ double colpart[2][TB];
     if ((skip && *skip) || failed(info)) return;
     int64_t ti, tj;
     lower_tile_coords(blockIdx.x, ti, tj);
     const int64_t row0 = ti * TB, col0 = tj * TB;
     if (row0 >= n) return;
-    const int tid = threadIdx.x;
-    const int r = tid & (TB - 1), cg = tid >> 6;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int r = tid & (TB - 1), cg = tid >> 6, half = (tid >> 5) & 1;
     if (tid < TB) {
         const int64_t j = col0 + tid;
         xc[tid] = (j < n) ? x[j] : make_double2(0.0, 0.0);
         ac[tid] = (j < n) ? a[j] : 0.0;
     }
-    for (int c = tid; c < 4 * TB; c += blockDim.x) colsum[c / TB][c % TB] = 0.0;
     __syncthreads();
     const int64_t i = row0 + r;
     const bool diag = ti == tj, row_ok = i < n;
     const double2 xi = row_ok ? x[i] : make_double2(0.0, 0.0);
     const double ai = row_ok ? a[i] : 0.0;
     double rs = 0.0;
+    PhaseMemo memo;
     for (int c = cg; c < TB; c += 4) {
         const int64_t j = col0 + c;
-        if (!row_ok || j >= n) continue;
-        if (diag && j > i) continue;  // the diagonal tile: each pair once
-        const double v = (i == j) ? prod_diag(p, i) : prod_entry(T, p, xi, xc[c]);
-        rs = fma(v, ac[c], rs);
-        if (i != j) atomicAdd(&colsum[cg][c], v * ai);  // C_ji a_i into row j
+        double cs = 0.0;
+        // the diagonal tile: each pair once (j <= i)
+        if (row_ok && j < n && !(diag && j > i)) {
+            const double v = (i == j) ? prod_diag(p, i) : prod_entry(T, p, xi, xc[c], memo);
+            rs = fma(v, ac[c], rs);
+            if (i != j) cs = v * ai;  // C_ji a_i into row j
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
+        if (lane == 0) colpart[half][c] = cs;
     }
     if (row_ok) atomicAdd(acc + i, rs);
     __syncthreads();
     if (tid < TB) {
         const int64_t j = col0 + tid;
-        const double cs = colsum[0][tid] + colsum[1][tid] + colsum[2][tid] + colsum[3][tid];
+        const double cs = colpart[0][tid] + colpart[1][tid];
         if (j < n && cs != 0.0) atomicAdd(acc + j, cs);
     }
 }
@@ -259,6 +278,7 @@ __global__ void __launch_bounds__(256) prod_grad_kernel(const double2 *__restric
     const int r = tid & (TB - 1), cg = tid >> 6;
     const int64_t i = row0 + r;
     double g[4] = {0.0, 0.0, 0.0, 0.0};
+    PhaseMemo memo;
     if (i < n) {
         const double2 xi = x[i];
         const double ai = a[i];
@@ -273,11 +293,16 @@ __global__ void __launch_bounds__(256) prod_grad_kernel(const double2 *__restric
             } else {
                 const double cb2 = fma(ai, ac[c], -w);  // 2 Cbar_ik
                 const double dt = fabs(xi.x - xc[c].x), dw = fabs(xi.y - xc[c].y);
-                const double at = dt * p.st, aw = dw * p.sw;
-                const double kt = m2_eval(T, 0, at), kw = m2_eval(T, 0, aw);
+                if (dt != memo.dt) {
+                    memo.dt = dt;
+                    memo.kt = m2_eval(T, 0, dt * p.st);
+                    memo.gt = m2_eval(T, 1, dt * p.st);
+                }
+                const double aw = dw * p.sw;
+                const double kt = memo.kt, kw = m2_eval(T, 0, aw);
                 const double ks = p.s2 * cb2;
                 g[0] = fma(ks * kt, kw, g[0]);
-                g[1] = fma(ks * m2_eval(T, 1, at), kw, g[1]);
+                g[1] = fma(ks * memo.gt, kw, g[1]);
                 g[2] = fma(ks * kt, m2_eval(T, 1, aw), g[2]);
                 if (dt == 0.0) g[3] = fma(cb2, p.tau2, g[3]);
             }
