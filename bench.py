@@ -109,6 +109,39 @@ def lpt_partition(sizes, world, rank):
     return sorted(mine)
 
 
+def gather_batched(local, mine, nprob, dist, device):
+    """The batched results of every rank on every rank: `local` holds this
+    rank's rows (k columns) for its problems `mine` (ascending indices);
+    returns the nprob x k array with every problem's row in its place.  One
+    all-gather of fixed-size row blocks (the ranks' shares differ in length:
+    each is padded to the longest) and of the index lists; without a process
+    group, the local rows in place."""
+    import torch
+    local = torch.as_tensor(local, dtype=torch.float64, device=device)
+    k = local.shape[1]
+    full = torch.full((nprob, k), float("nan"), dtype=torch.float64, device=device)
+    if dist is None:
+        full[torch.as_tensor(mine, device=device)] = local
+        return full
+    world = dist.get_world_size()
+    cnt = torch.tensor([len(mine)], dtype=torch.int64, device=device)
+    cnts = [torch.zeros_like(cnt) for _ in range(world)]
+    dist.all_gather(cnts, cnt)
+    m = int(max(int(c.item()) for c in cnts))
+    rows = torch.full((m, k), float("nan"), dtype=torch.float64, device=device)
+    rows[: len(mine)] = local
+    idx = torch.full((m,), -1, dtype=torch.int64, device=device)
+    idx[: len(mine)] = torch.as_tensor(mine, dtype=torch.int64, device=device)
+    all_rows = [torch.empty_like(rows) for _ in range(world)]
+    all_idx = [torch.empty_like(idx) for _ in range(world)]
+    dist.all_gather(all_rows, rows)
+    dist.all_gather(all_idx, idx)
+    for r in range(world):
+        sel = all_idx[r] >= 0
+        full[all_idx[r][sel]] = all_rows[r][sel]
+    return full
+
+
 def max_over_ranks(value, dist, device):
     """The largest of every rank's value (the slowest rank's time); the value
     itself without a process group."""
@@ -778,8 +811,11 @@ def run_batched(args, rank, world, local):
     clocks.start()
     res = batched_measure(sel, args.precision, args.steps, args.warmup)
     clk = clocks.stop()
-    res.pop("out")
-    res.pop("grad")
+    # every problem's loglik and gradient on rank 0's side too (host gather)
+    outs = gather_batched(res.pop("out"), mine, len(probs), dist, "cuda")
+    grads = gather_batched(res.pop("grad"), mine, len(probs), dist, "cuda")
+    res["gathered_problems"] = int(torch.isfinite(outs[:, 0]).sum().item())
+    res["gathered_grad_finite"] = bool(torch.isfinite(grads).all().item())
     ms = max_over_ranks(res["ms_per_batch"] * args.steps, dist, "cuda")
     value = len(probs) * args.steps / (ms / 1e3)
     prec = args.precision
