@@ -22,6 +22,8 @@
 // (XT[j][l] = X[l][j]) that the later TRTRI steps and LAUUM read.
 // Blocked LAUUM, block row I:  W[I, 0:I] = sum_{l >= I0} X[l, I]^T X[l, 0:I],
 // one contraction over XT per block row, written in place.
+#include <stdlib.h>
+
 #include "internal.h"
 #include "kern.cuh"
 #include "tc_gemm.h"
@@ -38,9 +40,10 @@ struct Store {
     int64_t rows = 0, kld = 0;
     int f64 = 0;
     int S = 3;
+    int64_t kch = TC_CHUNK_K;  // K width of one row bound (three slices: 512 or 1024)
     size_t slice_bytes() const { return (size_t)rows * kld * (f64 ? 8 : 2 * S); }
     size_t ex_bytes() const {
-        return (f64 || S != 3) ? 0 : sizeof(int) * (size_t)rows * tc_ex_ld(kld);
+        return (f64 || S != 3) ? 0 : sizeof(int) * (size_t)rows * tc_ex_ld(kld, kch);
     }
 };
 
@@ -85,7 +88,8 @@ static int pack(const Store &st, const double *src, int64_t ld, int64_t R, int64
         return GP_OK;
     }
     return split_rows(src, ld, R, K, Kvalid, trans, diag_off, lower_mask, st.S,
-                      static_cast<uint16_t *>(st.p), st.ex, st.rows, st.kld, row_off, k_off, s);
+                      static_cast<uint16_t *>(st.p), st.ex, st.rows, st.kld, row_off, k_off, s,
+                      st.kch);
 }
 
 // C (M x N, FP64) = beta C + alpha A[a_row.., a_k..] B[b_row.., b_k..]^T over K.
@@ -101,9 +105,9 @@ static int contract(const Store &A, int64_t a_row, int64_t a_k, const Store &B, 
         return gemm_f64_ex(M, N, K, alpha, a, A.kld, 1, b, B.kld, 0, beta, C, ldc, 0, m, info, s);
     }
     TcOperand ta{static_cast<const uint16_t *>(A.p), A.rows, A.kld, A.S, a_row, a_k,
-                 A.ex, tc_ex_ld(A.kld)};
+                 A.ex, tc_ex_ld(A.kld, A.kch), A.kch};
     TcOperand tb{static_cast<const uint16_t *>(B.p), B.rows, B.kld, B.S, b_row, b_k,
-                 B.ex, tc_ex_ld(B.kld)};
+                 B.ex, tc_ex_ld(B.kld, B.kch), B.kch};
     TcOut o{C, ldc, 0, alpha, beta, lower, diag_off, acc2};
     return tc_gemm(ta, tb, M, N, K, o, tri_k, tri_off, info, s);
 }
@@ -130,6 +134,11 @@ static int64_t ntiles64(int64_t np) {
     return T * (T + 1) / 2;
 }
 
+static bool wide_chunks() {
+    static const bool v = !(getenv("GP_WIDE_CHUNKS") && atoi(getenv("GP_WIDE_CHUNKS")) == 0);
+    return v;
+}
+
 static GradWs grad_layout(void *base, int64_t np, int precision, int S) {
     GradWs w;
     char *b = static_cast<char *>(base);
@@ -154,6 +163,13 @@ static GradWs grad_layout(void *base, int64_t np, int precision, int S) {
     const int64_t kldp = round_up(np, 64);
     w.XT = mk(np, kldp);
     w.SArow = mk(GNB, kldp);
+    if (!f64 && S == 3 && wide_chunks()) {
+        // the inverse's deep contractions (T = L X and X^T X) on 1024-column row
+        // bounds: half as many accumulator flushes (the exponent arrays were
+        // sized for 512-column chunks, so they have room)
+        w.XT.kch = 2 * TC_CHUNK_K;
+        w.SArow.kch = 2 * TC_CHUNK_K;
+    }
     w.SW = mk(GNB, GNB);
     w.ST = mk(np, GNB);
     w.T = reinterpret_cast<double *>(take(sizeof(double) * GNB * (size_t)np));
@@ -199,20 +215,29 @@ static int trtri_inplace(double *A, int64_t ld, int64_t np, GradWs &w, const dou
         }
         copy_lower_kernel<<<dim3(1, (unsigned)nb), 256, 0, s>>>(Wd, nb, Akk, ld, nb, info);
         GP_LAUNCH_CHECK();
-        // XT[j][l] = X[l][j] for l in block k, j < k0 + nb (zero above the diagonal)
-        GP_TRY(pack(w.XT, A + k0, ld, k0 + nb, nb, nb, 1, k0, 1, 0, k0, s));
+        // XT[j][l] = X[l][j] for l in block k, j < k0 + nb (zero above the
+        // diagonal).  With 1024-column row bounds a block that completes a
+        // chunk packs the chunk's two blocks together (one bound over both);
+        // a block that opens one packs itself, bounded over its own columns,
+        // which is what the next block's T = L X reads of the open chunk.
+        const int64_t kc = w.XT.kch;
+        const int64_t c0 = (k0 / kc) * kc;
+        GP_TRY(pack(w.XT, A + c0, ld, k0 + nb, k0 + nb - c0, k0 + nb - c0, 1, c0, 1, 0, c0, s));
     }
     return GP_OK;
 }
 
-// In place: A (lower X) -> W = X^T X (lower), reading X from w.XT.
+// In place: A (lower X) -> W = X^T X (lower), reading X from w.XT.  Each
+// block row's K range starts at its chunk boundary (with 1024-column row
+// bounds below i0; the extra columns l < i0 multiply X(l, i0 + r) = 0).
 static int lauum_inplace(double *A, int64_t ld, int64_t np, GradWs &w, int64_t *info,
                          cudaStream_t s) {
+    const Store &X = w.XT;
     for (int64_t i0 = 0; i0 < np; i0 += GNB) {
         const int64_t nb = (np - i0) < GNB ? (np - i0) : GNB;
-        const int64_t K = np - i0;
-        GP_TRY(contract(w.XT, i0, i0, w.XT, 0, i0, nb, i0 + nb, K, 1.0, 0.0, A + i0, ld, 1, i0, 0, 0,
-                        w.acc2, info, s));
+        const int64_t k0 = (i0 / X.kch) * X.kch;
+        GP_TRY(contract(X, i0, k0, X, 0, k0, nb, i0 + nb, np - k0, 1.0, 0.0, A + i0, ld, 1, i0, 0,
+                        0, w.acc2, info, s));
     }
     return GP_OK;
 }

@@ -36,6 +36,7 @@ struct SplitArgs {
     int *dst_ex;
     int64_t ex_ld;
     int64_t dst_rows, dst_kld, dst_row_off, dst_k_off;
+    int64_t kch;  // K chunk of one CTA and of one row bound
 };
 
 // raw bits of operand element (r, k); masked and out-of-range entries are +0
@@ -105,8 +106,8 @@ __global__ void __launch_bounds__(256) split_rows_kernel(SplitArgs a) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t r0 = (int64_t)blockIdx.x * 32;
     // this CTA's K chunk; each (row, chunk) gets its own bound 2^e
-    const int64_t kb = (int64_t)blockIdx.y * SPLIT_KCH;
-    const int64_t ke = min(a.K, kb + SPLIT_KCH);
+    const int64_t kb = (int64_t)blockIdx.y * a.kch;
+    const int64_t ke = min(a.K, kb + a.kch);
     const int64_t kev = min(ke, a.Kvalid);
     constexpr unsigned long long ABS = 0x7FFFFFFFFFFFFFFFull;
     // pass 1: row bounds, as the largest magnitude's bit pattern
@@ -147,7 +148,7 @@ __global__ void __launch_bounds__(256) split_rows_kernel(SplitArgs a) {
         sc_s[threadIdx.x] = ldexpf(1.0f, 7 - e);
         isc_s[threadIdx.x] = ldexpf(1.0f, e - 7);
         if (a.dst_ex && r0 + threadIdx.x < a.R)
-            a.dst_ex[(a.dst_row_off + r0 + threadIdx.x) * a.ex_ld + (a.dst_k_off + kb) / SPLIT_KCH] = e;
+            a.dst_ex[(a.dst_row_off + r0 + threadIdx.x) * a.ex_ld + (a.dst_k_off + kb) / a.kch] = e;
     }
     __syncthreads();
     const int64_t slice = a.dst_rows * a.dst_kld;
@@ -243,8 +244,8 @@ __global__ void __launch_bounds__(256) split3_vec_kernel(SplitArgs a) {
     constexpr unsigned long long ABS = 0x7FFFFFFFFFFFFFFFull;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t r0 = (int64_t)blockIdx.x * 32;
-    const int64_t kb = (int64_t)blockIdx.y * SPLIT_KCH;
-    const int64_t ke = min(a.K, kb + SPLIT_KCH);
+    const int64_t kb = (int64_t)blockIdx.y * a.kch;
+    const int64_t ke = min(a.K, kb + a.kch);
     const int64_t slice = a.dst_rows * a.dst_kld;
     uint16_t *d0 = a.dst + (a.dst_row_off + r0) * a.dst_kld + a.dst_k_off;
     // warp: rows r0 + warp + 8i; lane: K quads kb + 4 lane + 128 j
@@ -271,7 +272,7 @@ __global__ void __launch_bounds__(256) split3_vec_kernel(SplitArgs a) {
         e = max(-100, min(e, 120));
         sc_s[threadIdx.x] = ldexpf(1.0f, 7 - e);
         if (r0 + threadIdx.x < a.R)
-            a.dst_ex[(a.dst_row_off + r0 + threadIdx.x) * a.ex_ld + (a.dst_k_off + kb) / SPLIT_KCH] = e;
+            a.dst_ex[(a.dst_row_off + r0 + threadIdx.x) * a.ex_ld + (a.dst_k_off + kb) / a.kch] = e;
     }
     __syncthreads();
     for (int i = 0; i < 4; ++i) {
@@ -390,21 +391,24 @@ __global__ void __launch_bounds__(SPP_THREADS) split3_panel_kernel(SplitArgs a) 
 int split_rows(const double *src, int64_t ld, int64_t R, int64_t K, int64_t Kvalid, int trans,
                int64_t diag_off, int lower_mask, int S, uint16_t *dst, int *dst_ex,
                int64_t dst_rows, int64_t dst_kld, int64_t dst_row_off, int64_t dst_k_off,
-               cudaStream_t s) {
+               cudaStream_t s, int64_t kch) {
     if (R <= 0 || K <= 0) return GP_OK;
     if ((S != 3 && S != 5) || (S == 3) != (dst_ex != nullptr) || dst_row_off + R > dst_rows ||
-        dst_k_off + K > dst_kld || dst_k_off % SPLIT_KCH)
+        dst_k_off + K > dst_kld || !(kch == SPLIT_KCH || (kch == 2 * SPLIT_KCH && S == 3)) ||
+        dst_k_off % kch)
         return GP_ERR_INVALID;
     SplitArgs a{src, ld, R, K, Kvalid < K ? Kvalid : K, trans, diag_off, lower_mask, S,
-                dst, dst_ex, tc_ex_ld(dst_kld), dst_rows, dst_kld, dst_row_off, dst_k_off};
+                dst, dst_ex, tc_ex_ld(dst_kld, kch), dst_rows, dst_kld, dst_row_off, dst_k_off,
+                kch};
     const int ev = prof_start(s);
-    dim3 g((unsigned)ceil_div(R, 32), (unsigned)ceil_div(K, SPLIT_KCH));
+    dim3 g((unsigned)ceil_div(R, 32), (unsigned)ceil_div(K, kch));
     const bool vec = S == 3 && K % 64 == 0 && ld % 2 == 0 &&
                      reinterpret_cast<uintptr_t>(src) % 16 == 0 &&
                      reinterpret_cast<uintptr_t>(dst) % 16 == 0 && dst_kld % 64 == 0;
-    if (vec && !trans)
+    // the one-pass panel kernel holds one 512-column chunk in registers
+    if (vec && !trans && kch == SPLIT_KCH)
         split3_panel_kernel<<<g, SPP_THREADS, 0, s>>>(a);
-    else if (vec)
+    else if (vec && trans)
         split3_vec_kernel<<<g, 256, 0, s>>>(a);
     else
         split_rows_kernel<<<g, 256, 0, s>>>(a);

@@ -93,8 +93,9 @@ struct TcGemmArgs {
     int first_of[TC_MAX_PAIRS];  // pair opens its accumulator
     int nacc, nbuf;              // accumulators per tile, tile buffers (nacc*nbuf <= 4)
     uint32_t idesc;              // MMA instruction descriptor (FP16 or BF16 operands)
-    const int *ex_a, *ex_b;      // normalized slices: row exponents per 512-chunk, else null
+    const int *ex_a, *ex_b;      // normalized slices: row exponents per kch-chunk, else null
     int64_t ex_ld_a, ex_ld_b;
+    int kch;                     // K width of one row bound (and of one flush of a deep contraction)
     int64_t *info;
     // three-slice kernel, chunked contraction into an FP64 output: C above is
     // the double-float running sum (written, not read, by a tile's first
@@ -413,8 +414,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             // col0 + 32 + lane, shuffled to the column steps below
             int ea = 0, eb0 = 0, eb1 = 0;
             if (args.ex_b && clo < chi) {
-                const int64_t cha = (args.a_k_off + (int64_t)clo * TC_BK) / TC_CHUNK_K;
-                const int64_t chb = (args.b_k_off + (int64_t)clo * TC_BK) / TC_CHUNK_K;
+                const int64_t cha = (args.a_k_off + (int64_t)clo * TC_BK) / args.kch;
+                const int64_t chb = (args.b_k_off + (int64_t)clo * TC_BK) / args.kch;
                 if (row_ok) ea = args.ex_a[(args.a_row_off + row) * args.ex_ld_a + cha];
                 const int64_t c0 = col0 + lane, c1 = col0 + 32 + lane;
                 if (c0 < args.N) eb0 = args.ex_b[(args.b_row_off + c0) * args.ex_ld_b + chb];
@@ -755,8 +756,8 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
 #pragma unroll
                 for (int m = 0; m < T3_NEB; ++m) eb[m] = 14;
                 if (args.ex_b && has_acc) {
-                    const int64_t cha = (args.a_k_off + (int64_t)clo * TC_BK) / TC_CHUNK_K;
-                    const int64_t chb = (args.b_k_off + (int64_t)clo * TC_BK) / TC_CHUNK_K;
+                    const int64_t cha = (args.a_k_off + (int64_t)clo * TC_BK) / args.kch;
+                    const int64_t chb = (args.b_k_off + (int64_t)clo * TC_BK) / args.kch;
                     if (row_ok) ea = args.ex_a[(args.a_row_off + row) * args.ex_ld_a + cha];
 #pragma unroll
                     for (int m = 0; m < T3_NEB; ++m) {
@@ -947,7 +948,11 @@ int tc_gemm(const TcOperand &A, const TcOperand &B, int64_t M, int64_t N, int64_
     // both operands must line up with the stores' 512-column chunks
     const bool normalized = A.S == 3;
     if (normalized && (!A.ex || !B.ex)) return GP_ERR_INVALID;
-    if (A.k_off % TC_CHUNK_K || B.k_off % TC_CHUNK_K) return GP_ERR_INVALID;
+    // one chunk width for both operands: 512, or 1024 for three-slice stores
+    const int64_t kch = A.kch;
+    if (B.kch != kch || !(kch == TC_CHUNK_K || (kch == 2 * TC_CHUNK_K && A.S == 3)))
+        return GP_ERR_INVALID;
+    if (A.k_off % kch || B.k_off % kch) return GP_ERR_INVALID;
     // the shared-memory opt-in is per device (setting it twice is harmless)
     // set once per device; a race between host threads only repeats the
     // (idempotent) attribute call
@@ -996,12 +1001,13 @@ int tc_gemm(const TcOperand &A, const TcOperand &B, int64_t M, int64_t N, int64_
     // scales) change every 512 columns of K, so the accumulators are flushed
     // per chunk: double-float outputs take each chunk directly, FP64 outputs
     // through the double-float buffer acc2.
-    const bool deep = K > TC_CHUNK_K;
+    a.kch = (int)kch;
+    const bool deep = K > kch;
     const bool via_acc2 = deep && out.mode == 0;
     // the three-slice kernel writes the FP64 result from the last chunk itself
     // (no zeroing of acc2 before, no conversion pass after) when beta = 0
     const bool fused = via_acc2 && A.S == 3 && out.beta == 0.0;
-    if (deep) a.kchunk = (int)(TC_CHUNK_K / TC_BK);
+    if (deep) a.kchunk = (int)(kch / TC_BK);
     if (via_acc2) {
         if (!out.acc2) return GP_ERR_INVALID;
         if (N > 0x7fffffffLL || ceil_div(M, 256) > 65535) return GP_ERR_INVALID;

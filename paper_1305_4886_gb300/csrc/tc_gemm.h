@@ -26,10 +26,12 @@ struct TcOperand {
     int64_t k_off;
     const int *ex = nullptr;
     int64_t ex_ld = 0;
+    int64_t kch = TC_CHUNK_K;  // K width of one row bound (512, or 1024 for a
+                               // three-slice store packed with wider chunks)
 };
 
-// Exponent columns of a store with Kld columns.
-inline int64_t tc_ex_ld(int64_t Kld) { return (Kld + TC_CHUNK_K - 1) / TC_CHUNK_K; }
+// Exponent columns of a store with Kld columns and row bounds per kch columns.
+inline int64_t tc_ex_ld(int64_t Kld, int64_t kch = TC_CHUNK_K) { return (Kld + kch - 1) / kch; }
 
 // Output of a contraction.  mode 0: C is FP64, C = beta C + alpha acc;
 // mode 2: C is an FP32 pair (float2 hi, lo) updated in double-float
@@ -63,9 +65,11 @@ int tc_gemm(const TcOperand &A, const TcOperand &B, int64_t M, int64_t N, int64_
 // with dst_rows rows and dst_kld columns (dst_k_off a multiple of 512).
 // Columns k >= Kvalid are zero.  S = 3 also writes the row exponents to
 // dst_ex (dst_rows x tc_ex_ld(dst_kld) ints).
+// kch: K width of one row bound (512; 1024 allowed for three slices, where
+// group 0 stays exact in FP32 for K <= 1024).
 int split_rows(const double *src, int64_t ld, int64_t R, int64_t K, int64_t Kvalid, int trans,
                int64_t diag_off, int lower_mask, int S, uint16_t *dst, int *dst_ex,
                int64_t dst_rows, int64_t dst_kld, int64_t dst_row_off, int64_t dst_k_off,
-               cudaStream_t s);
+               cudaStream_t s, int64_t kch = TC_CHUNK_K);
 
 }  // namespace gp
