@@ -22,8 +22,6 @@
 // (XT[j][l] = X[l][j]) that the later TRTRI steps and LAUUM read.
 // Blocked LAUUM, block row I:  W[I, 0:I] = sum_{l >= I0} X[l, I]^T X[l, 0:I],
 // one contraction over XT per block row, written in place.
-#include <stdlib.h>
-
 #include "internal.h"
 #include "kern.cuh"
 #include "tc_gemm.h"
@@ -134,11 +132,6 @@ static int64_t ntiles64(int64_t np) {
     return T * (T + 1) / 2;
 }
 
-static bool wide_chunks() {
-    static const bool v = !(getenv("GP_WIDE_CHUNKS") && atoi(getenv("GP_WIDE_CHUNKS")) == 0);
-    return v;
-}
-
 static GradWs grad_layout(void *base, int64_t np, int precision, int S) {
     GradWs w;
     char *b = static_cast<char *>(base);
@@ -163,7 +156,7 @@ static GradWs grad_layout(void *base, int64_t np, int precision, int S) {
     const int64_t kldp = round_up(np, 64);
     w.XT = mk(np, kldp);
     w.SArow = mk(GNB, kldp);
-    if (!f64 && S == 3 && wide_chunks()) {
+    if (!f64 && S == 3) {
         // the inverse's deep contractions (T = L X and X^T X) on 1024-column row
         // bounds: half as many accumulator flushes (the exponent arrays were
         // sized for 512-column chunks, so they have room)
@@ -195,8 +188,9 @@ static int trtri_inplace(double *A, int64_t ld, int64_t np, GradWs &w, const dou
         const int64_t nb = (np - k0) < GNB ? (np - k0) : GNB;
         double *Akk = A + k0 + k0 * ld;
         const double *Wd = w.Wd;
+        int64_t wld = nb;
         if (winv) {
-            Wd = winv + (k0 / GNB) * GNB * GNB;
+            Wd = winv_block(winv, np, w.XT.S, k0, &wld);
         } else {
             const int ev = prof_start(s);
             GP_TRY(trtri_fp64_blocked(Akk, ld, nb, w.Wd, nb, w.tmp, info, s));
@@ -208,12 +202,12 @@ static int trtri_inplace(double *A, int64_t ld, int64_t np, GradWs &w, const dou
             GP_TRY(contract(w.SArow, 0, 0, w.XT, 0, 0, nb, k0, k0, 1.0, 0.0, w.T, nb, 0, 0, 1, 0,
                             w.acc2, info, s));
             // X[k, 0:k0] = -X_kk T
-            GP_TRY(pack(w.SW, Wd, nb, nb, nb, nb, 0, 0, 1, 0, 0, s));
+            GP_TRY(pack(w.SW, Wd, wld, nb, nb, nb, 0, 0, 1, 0, 0, s));
             GP_TRY(pack(w.ST, w.T, nb, k0, nb, nb, 1, 0, 0, 0, 0, s));
             GP_TRY(contract(w.SW, 0, 0, w.ST, 0, 0, nb, k0, nb, -1.0, 0.0, A + k0, ld, 0, 0, 0, 0,
                             w.acc2, info, s));
         }
-        copy_lower_kernel<<<dim3(1, (unsigned)nb), 256, 0, s>>>(Wd, nb, Akk, ld, nb, info);
+        copy_lower_kernel<<<dim3(1, (unsigned)nb), 256, 0, s>>>(Wd, wld, Akk, ld, nb, info);
         GP_LAUNCH_CHECK();
         // XT[j][l] = X[l][j] for l in block k, j < k0 + nb (zero above the
         // diagonal).  With 1024-column row bounds a block that completes a

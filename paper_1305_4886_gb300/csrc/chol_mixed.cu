@@ -35,7 +35,13 @@
 
 namespace gp {
 
-constexpr int64_t NB = 512;
+constexpr int64_t NB_MAX = 512;
+
+// Outer block width, 512 columns in both tensor-core forms.  (1024-column
+// blocks, with the trailing update's K and its row bounds over 1024 columns,
+// were measured 4% faster over the headline step but 10x less accurate in
+// the log-determinant, 1.5e-6 in the gradient at n = 16,384: not kept.)
+int64_t chol_block_cols(int) { return NB_MAX; }
 
 struct MixedWs {
     double *W = nullptr;            // NB x NB, inverse of the diagonal block
@@ -44,13 +50,17 @@ struct MixedWs {
     uint16_t *SB = nullptr;         // S x NB x NB  inverse slices
     int *exA = nullptr, *exB = nullptr;  // their row exponents (three-slice form)
     float2 *D = nullptr;            // np x np pending trailing updates (double-float)
+    int64_t np = 0;
     size_t bytes = 0;
 };
+
+static int64_t np_of(const MixedWs &w) { return w.np; }
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 static MixedWs mixed_layout(void *base, int64_t np, int S) {
     MixedWs w;
+    const int64_t NB = NB_MAX;  // sized for the widest block
     char *b = static_cast<char *>(base);
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -63,16 +73,30 @@ static MixedWs mixed_layout(void *base, int64_t np, int S) {
     w.tmp = reinterpret_cast<double *>(take(sizeof(double) * TB * NB));
     w.SA = reinterpret_cast<uint16_t *>(take(2ull * S * (size_t)np * NB));
     w.SB = reinterpret_cast<uint16_t *>(take(2ull * S * NB * NB));
-    w.exA = reinterpret_cast<int *>(take(sizeof(int) * (size_t)np * tc_ex_ld(NB)));
-    w.exB = reinterpret_cast<int *>(take(sizeof(int) * NB * tc_ex_ld(NB)));
+    w.exA = reinterpret_cast<int *>(take(sizeof(int) * (size_t)np * tc_ex_ld(NB, 512)));
+    w.exB = reinterpret_cast<int *>(take(sizeof(int) * NB * tc_ex_ld(NB, 512)));
     w.D = reinterpret_cast<float2 *>(take(sizeof(float2) * (size_t)np * (size_t)np));
+    w.np = np;
     w.bytes = align256(off);
     return w;
 }
 
 size_t chol_mixed_ws_bytes(int64_t np, int S) { return mixed_layout(nullptr, np, S).bytes; }
 
-size_t chol_winv_doubles(int64_t np) { return (size_t)ceil_div(np, NB) * NB * NB; }
+size_t chol_winv_doubles(int64_t np) { return (size_t)ceil_div(np, NB_MAX) * NB_MAX * NB_MAX; }
+
+// The inverse of the 512-column diagonal block at k0 inside the stored
+// inverses of the factorisation's diagonal blocks (blocks of
+// chol_block_cols(S) columns, each stored with ld = its width): a diagonal
+// sub-block of a block's inverse is the sub-block's inverse.
+const double *winv_block(const double *winv, int64_t np, int S, int64_t k0, int64_t *ld) {
+    const int64_t NB = chol_block_cols(S);
+    const int64_t q0 = (k0 / NB) * NB;
+    const int64_t w = (np - q0) < NB ? (np - q0) : NB;
+    const int64_t off = k0 - q0;
+    *ld = w;
+    return winv + (q0 / NB) * NB * NB + off + off * w;
+}
 
 // A[r, c] += D.hi[r, c] + D.lo[r, c] (double-float pending updates) for the
 // lower entries r + roff >= c of a rows x cols block.
@@ -171,9 +195,52 @@ static int diag_block(double *A, int64_t ld, int64_t np, int64_t k0, int64_t nb,
     return GP_OK;
 }
 
+// Panel solve L_ik = A_ik L_kk^{-T} of block column k0 (width nb) in place in
+// P (m x nb, ld), by tensor-core contractions with the diagonal block's
+// inverse W (ld nb).  Blocks wider than 512 are solved in two 512-column
+// steps, each with the inverse of its own 512 diagonal sub-block (W's
+// diagonal sub-blocks): L_i1 = A_i1 W_11^T, then
+// L_i2 = (A_i2 - L_i1 L_21^T) W_22^T; the error of an explicit-inverse solve
+// grows with the condition of the block it inverts, and the 512 sub-blocks
+// keep it at the 512-block level.  On return w.SA holds the slices of the
+// solved panel over the whole width (row bounds per kch columns).
+static int panel_solve(double *P, int64_t ld, int64_t m, int64_t nb, const double *Akk,
+                       const double *W, int S, const MixedWs &w, int64_t kch, int64_t *info,
+                       cudaStream_t s) {
+    int *exA = S == 3 ? w.exA : nullptr, *exB = S == 3 ? w.exB : nullptr;
+    const int64_t NB = NB_MAX;
+    const int64_t h = nb > TC_CHUNK_K ? TC_CHUNK_K : nb;  // first step's width
+    const int64_t k5 = TC_CHUNK_K;                         // row bounds of the steps
+    TcOperand opA{w.SA, np_of(w), NB, S, 0, 0, exA, tc_ex_ld(NB, k5), k5};
+    TcOperand opW{w.SB, NB, NB, S, 0, 0, exB, tc_ex_ld(NB, k5), k5};
+    // L_i1 = A_i1 W_11^T
+    GP_TRY(split_rows(W, nb, h, h, h, 0, 0, 1, S, w.SB, exB, NB, NB, 0, 0, s, k5));
+    GP_TRY(split_rows(P, ld, m, h, h, 0, 0, 0, S, w.SA, exA, np_of(w), NB, 0, 0, s, k5));
+    TcOut o1{P, ld, 0, 1.0, 0.0, 0, 0};
+    GP_TRY(tc_gemm(opA, opW, m, h, h, o1, 0, 0, info, s));
+    if (nb > h) {
+        const int64_t h2 = nb - h;
+        double *P2 = P + h * ld;
+        // A_i2 -= L_i1 L_21^T
+        GP_TRY(split_rows(P, ld, m, h, h, 0, 0, 0, S, w.SA, exA, np_of(w), NB, 0, 0, s, k5));
+        GP_TRY(split_rows(Akk + h, ld, h2, h, h, 0, 0, 0, S, w.SB, exB, NB, NB, 0, 0, s, k5));
+        TcOut o2{P2, ld, 0, -1.0, 1.0, 0, 0};
+        GP_TRY(tc_gemm(opA, opW, m, h2, h, o2, 0, 0, info, s));
+        // L_i2 = A_i2 W_22^T
+        GP_TRY(split_rows(W + h + h * nb, nb, h2, h2, h2, 0, 0, 1, S, w.SB, exB, NB, NB, 0, 0, s,
+                          k5));
+        GP_TRY(split_rows(P2, ld, m, h2, h2, 0, 0, 0, S, w.SA, exA, np_of(w), NB, 0, 0, s, k5));
+        TcOut o3{P2, ld, 0, 1.0, 0.0, 0, 0};
+        GP_TRY(tc_gemm(opA, opW, m, h2, h2, o3, 0, 0, info, s));
+    }
+    // the solved panel, for the trailing update
+    return split_rows(P, ld, m, nb, nb, 0, 0, 0, S, w.SA, exA, np_of(w), NB, 0, 0, s, kch);
+}
+
 // Without lookahead: every step on the caller's stream, in order.
 static int chol_mixed_plain(double *A, int64_t ld, int64_t np, int S, const MixedWs &w,
                             double *winv, int64_t *info, cudaStream_t s) {
+    const int64_t NB = chol_block_cols(S), kch = S == 3 ? NB : TC_CHUNK_K;
     if (cudaMemsetAsync(w.D, 0, sizeof(float2) * (size_t)np * (size_t)np, s) != cudaSuccess)
         return GP_ERR_CUDA;
     for (int64_t k0 = 0; k0 < np; k0 += NB) {
@@ -182,15 +249,11 @@ static int chol_mixed_plain(double *A, int64_t ld, int64_t np, int S, const Mixe
         double *W = winv ? winv + (k0 / NB) * NB * NB : w.W;
         GP_TRY(diag_block(A, ld, np, k0, nb, S, w, W, m > 0 || winv, info, s));
         if (m <= 0) break;
-        double *P = A + k0 + k0 * ld + nb;
-        int *exA = S == 3 ? w.exA : nullptr, *exB = S == 3 ? w.exB : nullptr;
-        GP_TRY(split_rows(W, nb, nb, nb, nb, 0, 0, 1, S, w.SB, exB, NB, NB, 0, 0, s));
-        GP_TRY(split_rows(P, ld, m, nb, nb, 0, 0, 0, S, w.SA, exA, np, NB, 0, 0, s));
-        TcOperand opA{w.SA, np, NB, S, 0, 0, exA, tc_ex_ld(NB)};
-        TcOperand opW{w.SB, NB, NB, S, 0, 0, exB, tc_ex_ld(NB)};
-        TcOut o1{P, ld, 0, 1.0, 0.0, 0, 0};
-        GP_TRY(tc_gemm(opA, opW, m, nb, nb, o1, 0, 0, info, s));
-        GP_TRY(split_rows(P, ld, m, nb, nb, 0, 0, 0, S, w.SA, exA, np, NB, 0, 0, s));
+        double *Akk = A + k0 + k0 * ld;
+        double *P = Akk + nb;
+        int *exA = S == 3 ? w.exA : nullptr;
+        GP_TRY(panel_solve(P, ld, m, nb, Akk, W, S, w, kch, info, s));
+        TcOperand opA{w.SA, np, NB_MAX, S, 0, 0, exA, tc_ex_ld(NB_MAX, kch), kch};
         TcOut o2{w.D + (k0 + nb) + (k0 + nb) * np, np, 2, -1.0, 0.0, 1, 0};
         GP_TRY(tc_gemm(opA, opA, m, m, nb, o2, 0, 0, info, s));
     }
@@ -200,6 +263,7 @@ static int chol_mixed_plain(double *A, int64_t ld, int64_t np, int S, const Mixe
 int chol_mixed(double *A, int64_t ld, int64_t np, int S, void *ws, double *winv, int64_t *info,
                cudaStream_t s, bool lookahead) {
     MixedWs w = mixed_layout(ws, np, S);
+    const int64_t NB = chol_block_cols(S), kch = S == 3 ? NB : TC_CHUNK_K;
     ProfContractRole role(GP_PROF_CONTRACT_CHOL);
     if (!lookahead) return chol_mixed_plain(A, ld, np, S, w, winv, info, s);
     LookaheadCtx *la = nullptr;
@@ -221,15 +285,10 @@ int chol_mixed(double *A, int64_t ld, int64_t np, int S, void *ws, double *winv,
         const int64_t m = np - k0 - nb;
         if (m <= 0) break;
         double *P = Akk + nb;  // m x nb panel below the diagonal block
-        int *exA = S == 3 ? w.exA : nullptr, *exB = S == 3 ? w.exB : nullptr;
-        GP_TRY(split_rows(W_of(k0), nb, nb, nb, nb, 0, 0, 1, S, w.SB, exB, NB, NB, 0, 0, s));
-        GP_TRY(split_rows(P, ld, m, nb, nb, 0, 0, 0, S, w.SA, exA, np, NB, 0, 0, s));
-        TcOperand opA{w.SA, np, NB, S, 0, 0, exA, tc_ex_ld(NB)};
-        TcOperand opW{w.SB, NB, NB, S, 0, 0, exB, tc_ex_ld(NB)};
-        // L_ik = A_ik W^T  (FP64 out)
-        TcOut o1{P, ld, 0, 1.0, 0.0, 0, 0};
-        GP_TRY(tc_gemm(opA, opW, m, nb, nb, o1, 0, 0, info, s));
-        GP_TRY(split_rows(P, ld, m, nb, nb, 0, 0, 0, S, w.SA, exA, np, NB, 0, 0, s));
+        int *exA = S == 3 ? w.exA : nullptr;
+        // L_ik = A_ik L_kk^{-T} (FP64 out), then its slices for the update
+        GP_TRY(panel_solve(P, ld, m, nb, Akk, W_of(k0), S, w, kch, info, s));
+        TcOperand opA{w.SA, np, NB_MAX, S, 0, 0, exA, tc_ex_ld(NB_MAX, kch), kch};
         // D_22 -= L_ik L_ik^T (lower, double-float), the next block column
         // first: its diagonal block is then folded, factored and inverted on
         // the side stream while the rest of the update runs on the other SMs

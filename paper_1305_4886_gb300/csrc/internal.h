@@ -66,6 +66,10 @@ size_t chol_mixed_ws_bytes(int64_t np, int S);
 // winv (nullable, chol_winv_doubles(np) doubles): receives L_kk^{-1} of every
 // 512-column diagonal block (NB x NB each, in block order) for the inverse
 size_t chol_winv_doubles(int64_t np);
+// outer block width of the mixed factorisation for S slices, and the
+// inverse of the 512-column diagonal block at k0 within winv (its ld in *ld)
+int64_t chol_block_cols(int S);
+const double *winv_block(const double *winv, int64_t np, int S, int64_t k0, int64_t *ld);
 // lookahead: run each next diagonal block on the device's side stream while
 // the trailing update finishes (off for callers that already run many
 // factorisations side by side)
