@@ -37,10 +37,12 @@ namespace gp {
 
 constexpr int64_t NB_MAX = 512;
 
-// Outer block width, 512 columns in both tensor-core forms.  (1024-column
-// blocks, with the trailing update's K and its row bounds over 1024 columns,
-// were measured 4% faster over the headline step but 10x less accurate in
-// the log-determinant, 1.5e-6 in the gradient at n = 16,384: not kept.)
+// Outer block width, 512 columns in both tensor-core forms.  Measured and not
+// kept: 1024-column blocks with the trailing update's row bounds over 1024
+// columns (4% faster over the headline step, 10x less accurate in the
+// log-determinant, gradient 1.5e-6 at n = 16,384), and 1024-column blocks
+// with 512-column row bounds (the update flushed twice per tile: as
+// accurate, 3% slower).
 int64_t chol_block_cols(int) { return NB_MAX; }
 
 struct MixedWs {
@@ -240,7 +242,7 @@ static int panel_solve(double *P, int64_t ld, int64_t m, int64_t nb, const doubl
 // Without lookahead: every step on the caller's stream, in order.
 static int chol_mixed_plain(double *A, int64_t ld, int64_t np, int S, const MixedWs &w,
                             double *winv, int64_t *info, cudaStream_t s) {
-    const int64_t NB = chol_block_cols(S), kch = S == 3 ? NB : TC_CHUNK_K;
+    const int64_t NB = chol_block_cols(S), kch = TC_CHUNK_K;
     if (cudaMemsetAsync(w.D, 0, sizeof(float2) * (size_t)np * (size_t)np, s) != cudaSuccess)
         return GP_ERR_CUDA;
     for (int64_t k0 = 0; k0 < np; k0 += NB) {
@@ -263,7 +265,7 @@ static int chol_mixed_plain(double *A, int64_t ld, int64_t np, int S, const Mixe
 int chol_mixed(double *A, int64_t ld, int64_t np, int S, void *ws, double *winv, int64_t *info,
                cudaStream_t s, bool lookahead) {
     MixedWs w = mixed_layout(ws, np, S);
-    const int64_t NB = chol_block_cols(S), kch = S == 3 ? NB : TC_CHUNK_K;
+    const int64_t NB = chol_block_cols(S), kch = TC_CHUNK_K;
     ProfContractRole role(GP_PROF_CONTRACT_CHOL);
     if (!lookahead) return chol_mixed_plain(A, ld, np, S, w, winv, info, s);
     LookaheadCtx *la = nullptr;
