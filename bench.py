@@ -663,6 +663,9 @@ def run_ours(args, rank, world, local):
         "loglik_grad_alg_tflops": n ** 3 / (elapsed_ms / args.steps / 1e3) / 1e12,
         "per_step_ms": per_step,
         "per_step_ms_profiled_sum": sum(per_step.values()),
+        "per_step_ms_note": ("diag_chol, diag_inv and the diagonal rows' fold run on a side "
+                             "stream under the trailing updates (lookahead): the classes "
+                             "overlap, so their sum exceeds ms_per_step"),
         "per_step_launches": {c: prof[c][1] / args.steps for c in prof},
         "contract_by_role": {c: {"ms_per_step": roles[c][0] / args.steps,
                                  "alg_tflops": (roles[c][2] / pairs / (roles[c][0] / 1e3) / 1e12)

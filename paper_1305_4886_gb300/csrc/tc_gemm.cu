@@ -475,28 +475,38 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // one per 88).  TMEM: hi [0, 128), d1 [128, 256), d2 [256, 384); columns
 // [384, 512) hold the epilogue's staged high parts.
 //
-// Epilogue (warps 3-10, 32 rows x 64 columns each): as soon as a unit's
-// accumulators are complete it reads hi and d1, adds them error-free into a
-// double-float pair (h, l) per entry, writes h to the staging columns, keeps
-// l in registers and frees hi and d1 for issuer A; then it adds d2 into l
-// and frees d2 for issuer B.  The read-modify-write of
-// the outputs then runs while the next unit's instructions execute; its old
-// values are prefetched into L2 while the unit's own instructions execute.
+// Epilogue (EPI warps from warp 3 on, EPI / 4 per TMEM lane quarter, each
+// 32 rows x 512 / EPI columns): as soon as a unit's accumulators are
+// complete it reads hi and d1, adds them error-free into a double-float pair
+// (h, l) per entry, writes h to the staging columns, keeps l in registers
+// and frees hi and d1 for issuer A; then it adds d2 into l and frees d2 for
+// issuer B.  The read-modify-write of the outputs then runs while the next
+// unit's instructions execute; its old values are prefetched into L2 while
+// the unit's own instructions execute.  That output pass is latency bound
+// (dependent FP32 chains, old-value loads): where every tile is a single
+// 512-deep unit (the Cholesky's trailing updates, one unit per output) it
+// outlasts the unit's instructions with 8 warps, and 16 warps (two steps of
+// old values in flight each, to stay within the register budget) take it
+// about a quarter faster; deep contractions, whose units are several
+// instructions long per output, keep 8 warps, which leave the issuers more
+// of the SM.
 // ---------------------------------------------------------------------------
 constexpr int T3_STAGES = 2;
 constexpr int T3_SLICE = TC_BM * TC_BK * 2;  // 16 KB: one slice of one operand
 constexpr int T3_OPER = 3 * T3_SLICE;        // 48 KB: every slice of one operand
 constexpr int T3_STAGE = 2 * T3_OPER;        // 96 KB
 constexpr int T3_SMEM = T3_STAGES * T3_STAGE + 1024 /*barriers*/ + 1024 /*align*/;
-#ifndef T3_EPI_WARPS
-#define T3_EPI_WARPS 8
-#endif
-constexpr int T3_EPI = T3_EPI_WARPS;           // epilogue warps (4: one per TMEM lane quarter)
-constexpr int T3_THREADS = 32 * (3 + T3_EPI);  // producer, two issuers, epilogue
-constexpr int T3_COLS = TC_BN * 4 / T3_EPI;    // columns per epilogue warp
-constexpr int T3_NEB = T3_COLS / 32;           // B-row exponents per lane
-constexpr int T3_EG = 4;                       // columns per output step
-constexpr int T3_INFL = 4;                     // output steps with old values in flight
+constexpr int T3_EG = 4;  // columns per output step
+
+// Epilogue shape for EPI epilogue warps (8 or 16).
+template <int EPI>
+struct T3Epi {
+    static constexpr int THREADS = 32 * (3 + EPI);  // producer, two issuers, epilogue
+    static constexpr int COLS = TC_BN * 4 / EPI;    // columns per epilogue warp
+    static constexpr int NEB = COLS / 32;           // B-row exponents per lane
+    static constexpr int INFL = EPI >= 16 ? 2 : 4;  // output steps with old values in flight
+    static_assert(EPI == 8 || EPI == 16, "8 or 16 epilogue warps");
+};
 
 // Previous output values of T3_EG consecutive columns of this thread's row:
 // p points at column cl of the row (8-byte entries, stride ld8 bytes), lim is
@@ -558,9 +568,11 @@ __device__ __forceinline__ void t3_store(const TcGemmArgs &args, const float *h_
     }
 }
 
-__global__ void __launch_bounds__(T3_THREADS, 1)
+template <int EPI>
+__global__ void __launch_bounds__(T3Epi<EPI>::THREADS, 1)
     tc_gemm3_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     TcGemmArgs args) {
+    using E = T3Epi<EPI>;
     extern __shared__ uint8_t smem_raw[];
     if (args.info && failed(args.info)) return;
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -583,8 +595,8 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
         }
         mbar_init(fullA, 1);
         mbar_init(fullB, 1);
-        mbar_init(freeA, T3_EPI);
-        mbar_init(freeB, T3_EPI);
+        mbar_init(freeA, EPI);
+        mbar_init(freeB, EPI);
         mbar_init(&drain[0], 1);
         mbar_init(&drain[1], 1);
         abort_flag = 0;
@@ -708,7 +720,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
     } else if (warp >= 3) {
         // ---------------- epilogue ----------------
         const int q = warp & 3;                        // TMEM lane quarter of this warp
-        const int cbeg = ((warp - 3) >> 2) * T3_COLS;  // its columns in the tile
+        const int cbeg = ((warp - 3) >> 2) * E::COLS;  // its columns in the tile
         uint32_t local = 0;
         const float alpha_f = static_cast<float>(args.alpha);
         const bool need_old = args.out_mode == 2 || args.beta != 0.0;
@@ -731,7 +743,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                     int64_t e = args.N;
                     if (args.lower && row + args.diag_off + 1 < e) e = row + args.diag_off + 1;
                     e -= col0;
-                    lim = e <= 0 ? 0 : (e >= T3_COLS ? T3_COLS : (int)e);
+                    lim = e <= 0 ? 0 : (e >= E::COLS ? E::COLS : (int)e);
                 }
                 const int64_t ld8 = args.ldc * 8;
                 char *p_row = static_cast<char *>(args.C) + (row_ok ? (row + col0 * args.ldc) * 8 : 0);
@@ -752,26 +764,26 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                 // row exponents of this unit's 512-deep chunk: this thread's A
                 // row, and the B rows of columns col0 + 32 m + lane
                 // (unscaled sums: ea = 0, eb = 14)
-                int ea = 0, eb[T3_NEB];
+                int ea = 0, eb[E::NEB];
 #pragma unroll
-                for (int m = 0; m < T3_NEB; ++m) eb[m] = 14;
+                for (int m = 0; m < E::NEB; ++m) eb[m] = 14;
                 if (args.ex_b && has_acc) {
                     const int64_t cha = (args.a_k_off + (int64_t)clo * TC_BK) / args.kch;
                     const int64_t chb = (args.b_k_off + (int64_t)clo * TC_BK) / args.kch;
                     if (row_ok) ea = args.ex_a[(args.a_row_off + row) * args.ex_ld_a + cha];
 #pragma unroll
-                    for (int m = 0; m < T3_NEB; ++m) {
+                    for (int m = 0; m < E::NEB; ++m) {
                         const int64_t cm = col0 + 32 * m + lane;
                         if (cm < args.N) eb[m] = args.ex_b[(args.b_row_off + cm) * args.ex_ld_b + chb];
                     }
                 }
                 const int flim = read_old ? lim : 0;  // columns whose old values are read
                 const float fa = __fmul_rn(alpha_f, __int_as_float((ea + 127) << 23));
-                // a ring of T3_INFL output steps of old values; the first ones
+                // a ring of E::INFL output steps of old values; the first ones
                 // are in flight during the wait
-                unsigned long long old[T3_INFL][T3_EG];
+                unsigned long long old[E::INFL][T3_EG];
 #pragma unroll
-                for (int g = 0; g < T3_INFL - 1; ++g)
+                for (int g = 0; g < E::INFL - 1; ++g)
                     t3_fetch(p_row + g * T3_EG * ld8, ld8, g * T3_EG, flim, old[g]);
                 bool ok = mbar_wait(fullB, local & 1) && mbar_wait(fullA, local & 1);
                 ok = __all_sync(0xffffffffu, ok) && !abort_flag;
@@ -783,10 +795,10 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                 tc_fence_after();
                 const uint32_t tl = tmem + (static_cast<uint32_t>(q * 32) << 16) + cbeg;
                 const uint32_t th = tl + 3 * TC_BN;  // staged high parts
-                float L[T3_COLS];
+                float L[E::COLS];
                 if (has_acc) {
 #pragma unroll
-                    for (int g = 0; g < T3_COLS; g += 16) {
+                    for (int g = 0; g < E::COLS; g += 16) {
                         uint32_t a0[16], a1[16];
                         tmem_ld_32x32b_x16(tl + g, a0);
                         tmem_ld_32x32b_x16(tl + TC_BN + g, a1);
@@ -804,14 +816,14 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                     }
                 } else {
 #pragma unroll
-                    for (int j = 0; j < T3_COLS; ++j) L[j] = 0.0f;
+                    for (int j = 0; j < E::COLS; ++j) L[j] = 0.0f;
                 }
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(freeA);
                 if (has_acc) {
 #pragma unroll
-                    for (int g = 0; g < T3_COLS; g += 16) {
+                    for (int g = 0; g < E::COLS; g += 16) {
                         uint32_t a2[16];
                         tmem_ld_32x32b_x16(tl + 2 * TC_BN + g, a2);
                         tmem_ld_wait();
@@ -826,11 +838,11 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                 // l from L[0..15] (L rotates by 16 per block, so that the loop
                 // stays rolled: unrolled over 128 columns the code outgrows the
                 // instruction cache); step g's old values were requested
-                // T3_INFL - 1 steps earlier
-                static_assert(16 % T3_EG == 0 && (16 / T3_EG) % T3_INFL == 0, "ring");
-                constexpr int NSTEP = T3_COLS / T3_EG;
+                // E::INFL - 1 steps earlier
+                static_assert(16 % T3_EG == 0 && (16 / T3_EG) % E::INFL == 0, "ring");
+                constexpr int NSTEP = E::COLS / T3_EG;
 #pragma unroll 1
-                for (int blk = 0; blk < T3_COLS / 16; ++blk) {
+                for (int blk = 0; blk < E::COLS / 16; ++blk) {
                     float H[16];
                     if (has_acc) {
                         uint32_t hv[16];
@@ -844,22 +856,22 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                     }
                     int ebr = eb[0];
 #pragma unroll
-                    for (int m = 1; m < T3_NEB; ++m)
+                    for (int m = 1; m < E::NEB; ++m)
                         if ((blk >> 1) == m) ebr = eb[m];
 #pragma unroll
                     for (int st = 0; st < 16 / T3_EG; ++st) {
                         const int g = blk * (16 / T3_EG) + st;
-                        const int gf = g + T3_INFL - 1;
+                        const int gf = g + E::INFL - 1;
                         if (gf < NSTEP)
                             t3_fetch(p_row + gf * T3_EG * ld8, ld8, gf * T3_EG, flim,
-                                     old[(st + T3_INFL - 1) % T3_INFL]);
+                                     old[(st + E::INFL - 1) % E::INFL]);
                         const int cl = g * T3_EG;
                         t3_store(args, H + st * T3_EG, L + st * T3_EG, p_row + cl * ld8, ld8, cl,
-                                 lim, fa, ea, ebr, cl & 31, old[st % T3_INFL],
+                                 lim, fa, ea, ebr, cl & 31, old[st % E::INFL],
                                  pf_row + cl * ld8f, ld8f, to_f64);
                     }
 #pragma unroll
-                    for (int j = 0; j < T3_COLS - 16; ++j) L[j] = L[j + 16];
+                    for (int j = 0; j < E::COLS - 16; ++j) L[j] = L[j + 16];
                 }
                 ++local;
             }
@@ -964,7 +976,9 @@ int tc_gemm(const TcOperand &A, const TcOperand &B, int64_t M, int64_t N, int64_
                                  TC_SMEM) != cudaSuccess ||
             cudaFuncSetAttribute(tc_gemm_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  TC_SMEM) != cudaSuccess ||
-            cudaFuncSetAttribute(tc_gemm3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            cudaFuncSetAttribute(tc_gemm3_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 T3_SMEM) != cudaSuccess ||
+            cudaFuncSetAttribute(tc_gemm3_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  T3_SMEM) != cudaSuccess)
             return GP_ERR_CUDA;
         attr_set[dev].store(true, std::memory_order_release);
@@ -1060,8 +1074,10 @@ int tc_gemm(const TcOperand &A, const TcOperand &B, int64_t M, int64_t N, int64_
     int grid = (int)(ntiles < sms ? ntiles : (sms > 0 ? sms : 148));
     if (out.max_ctas > 0 && grid > out.max_ctas) grid = out.max_ctas;
     const int ev = prof_start(s);
-    if (three)
-        tc_gemm3_kernel<<<grid, T3_THREADS, T3_SMEM, s>>>(ma, mb, a);
+    if (three && deep)
+        tc_gemm3_kernel<8><<<grid, T3Epi<8>::THREADS, T3_SMEM, s>>>(ma, mb, a);
+    else if (three)
+        tc_gemm3_kernel<16><<<grid, T3Epi<16>::THREADS, T3_SMEM, s>>>(ma, mb, a);
     else if (a.nacc == 4)
         tc_gemm_kernel<4><<<grid, TC_THREADS, TC_SMEM, s>>>(ma, mb, a);
     else
