@@ -427,93 +427,247 @@ __device__ void stage_points(TcCtx &c, const DagProb &P, int tile) {
     }
 }
 
-// 64 x 64 FP64 product on staged operands (sA [t][r], sB [t][c]) with a
-// blocked thread mapping (rows 4 tx.., columns 4 ty..) over t in [tlo, thi):
-// the diagonal tile's products have triangular factors, and a thread skips
-// the t range where its factor block vanishes.  FP64-pipe bound, so the
-// shared-memory access pattern does not matter.
+// ---------------------------------------------------------------------------
+// The diagonal tile in double-float (FP32 pairs): the FP64 pipe of this part
+// runs at 1/64 of the FP32 rate, and the 64 x 64 blocks of the diagonal tile
+// (their factors, inverses and products) took most of the FP64 work of the
+// batched launch.  The pairs carry about 48 bits, the FP64 scratch blocks
+// stay the interface (converted by integer operations on load, one FP64 add
+// per entry on store).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ dfl ld_df(const double *p) {
+    return f64_to_df(static_cast<unsigned long long>(__double_as_longlong(__ldcg(p))));
+}
+
+// stage_a / stage_b of a 64 x 64 FP64 block as double-float pairs
+template <int TA>
+__device__ __forceinline__ void stage_a_df(const double *A, dfl *sA) {
+    for (int e = threadIdx.x; e < DB * DB; e += DAG_THREADS) {
+        const dfl v = ld_df(A + e);
+        const int lo = e & (DB - 1), hi = e >> 6;
+        if (TA == 0) sA[hi * DLD + lo] = v;
+        else sA[lo * DLD + hi] = v;
+    }
+}
+
+template <int TB>
+__device__ __forceinline__ void stage_b_df(const double *B, dfl *sB) {
+    for (int e = threadIdx.x; e < DB * DB; e += DAG_THREADS) {
+        const dfl v = ld_df(B + e);
+        const int lo = e & (DB - 1), hi = e >> 6;
+        if (TB == 0) sB[lo * DLD + hi] = v;
+        else sB[hi * DLD + lo] = v;
+    }
+}
+
+// (h, l) += a b with the product's error terms and the sum's rounding error
+// gathered in l (renormalized once at the end of a product).
+__device__ __forceinline__ void df_acc(float &h, float &l, dfl a, dfl b) {
+    const float p = __fmul_rn(a.h, b.h);
+    float pe = __fmaf_rn(a.h, b.h, -p);
+    pe = __fmaf_rn(a.h, b.l, pe);
+    pe = __fmaf_rn(a.l, b.h, pe);
+    const float s = __fadd_rn(h, p);
+    const float bb = __fsub_rn(s, h);
+    const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    h = s;
+    l = __fadd_rn(l, __fadd_rn(e, pe));
+}
+
+// 64 x 64 product on staged double-float operands (sA [t][r], sB [t][c])
+// with a blocked thread mapping: acc (rows 4 tx + a, columns 4 ty + b) +/-=
+// sum over t in [tlo, thi) of sA[t][r] sB[t][c].  The diagonal tile's
+// products have triangular factors, and a thread skips the t range where its
+// factor block vanishes.
 template <bool NEG>
-__device__ __forceinline__ void blk_mma(double (&acc)[4][4], const double *sA, const double *sB,
-                                        int tlo, int thi) {
+__device__ __forceinline__ void blk_mma_df(float (&ah)[4][4], float (&al)[4][4], const dfl *sA,
+                                           const dfl *sB, int tlo, int thi) {
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll 2
     for (int t = tlo; t < thi; ++t) {
-        double av[4], bv[4];
+        dfl av[4], bv[4];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) av[a] = NEG ? -sA[t * DLD + 4 * tx + a] : sA[t * DLD + 4 * tx + a];
+        for (int a = 0; a < 4; ++a) {
+            av[a] = sA[t * DLD + 4 * tx + a];
+            if (NEG) av[a] = df_neg(av[a]);
+        }
 #pragma unroll
         for (int b = 0; b < 4; ++b) bv[b] = sB[t * DLD + 4 * ty + b];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+            for (int b = 0; b < 4; ++b) df_acc(ah[a][b], al[a][b], av[a], bv[b]);
     }
 }
 
-__device__ __forceinline__ void blk_store(const double (&acc)[4][4], double *G) {
+__device__ __forceinline__ void acc_zero_df(float (&ah)[4][4], float (&al)[4][4]) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) ah[a][b] = al[a][b] = 0.0f;
+}
+
+// the block of blk_mma_df into the FP64 block G (ld 64)
+__device__ __forceinline__ void blk_store_df(const float (&ah)[4][4], const float (&al)[4][4],
+                                             double *G) {
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
     for (int b = 0; b < 4; ++b)
 #pragma unroll
-        for (int a = 0; a < 4; ++a) G[(4 * tx + a) + DB * (4 * ty + b)] = acc[a][b];
+        for (int a = 0; a < 4; ++a)
+            G[(4 * tx + a) + DB * (4 * ty + b)] = df_to_double(df_quick_sum(ah[a][b], al[a][b]));
 }
 
-// FP64 factor and inverse of the diagonal tile held in the scratch (blocks
-// 0 = A11, 1 = A21, 3 = A22): L11, W11; L21 = A21 W11^T; L22, W22 from
-// A22 - L21 L21^T (lower half); W21 = -W22 (L21 W11).  Returns the tile's
-// log-det share.
+// potrf_inv_tile in double-float: the 64 x 64 block staged (as pairs) in
+// sm.sA is factored (right-looking, the unscaled form a_rc -= a_rj a_cj /
+// a_jj, then L_rc = a_rc / sqrt(a_cc)); L is written to G and W = L^{-1} to
+// Wg (FP64, ld 64), and the block's log-det share to *logpart.  Pivots that
+// are not positive are reported as in potrf_inv_tile.
+__device__ void potrf_inv_tile_df(const DagProb &P, int j, double *G, double *Wg,
+                                  double *logpart, DagSmem &sm) {
+    const int tid = threadIdx.x;
+    dfl *S = reinterpret_cast<dfl *>(sm.sA);
+    dfl *Y = reinterpret_cast<dfl *>(sm.sB);
+    dfl *dinv = reinterpret_cast<dfl *>(sm.dinv);
+    dfl *lj = reinterpret_cast<dfl *>(sm.lj);
+    if (tid == 0) {
+        sm.bad = 0;
+        sm.badcol = 0;
+    }
+    __syncthreads();
+    for (int jj = 0; jj < DB; ++jj) {
+        const dfl *cj = S + jj * DLD;
+        if (tid < DB) {
+            const dfl d = cj[jj];
+            if (!(d.h > 0.0f)) {
+                if (tid == 0) {
+                    sm.bad = 1;
+                    sm.badcol = jj;
+                }
+            } else {
+                const dfl inv = df_rcp(d);
+                if (tid == 0) dinv[jj] = inv;
+                if (tid > jj) lj[tid] = df_mul(cj[tid], inv);
+            }
+        }
+        __syncthreads();
+        if (sm.bad) break;
+        const int ntri = (DB - 1 - jj) * (DB - jj) / 2;
+        for (int e = tid; e < ntri; e += DAG_THREADS) {
+            int r, c;
+            tri_desc_entry(e, DB, r, c);
+            S[c * DLD + r] = df_fms(S[c * DLD + r], cj[r], lj[c]);
+        }
+        __syncthreads();
+    }
+    if (sm.bad) {
+        if (tid == 0) set_info(P.info, (int64_t)j * DB + sm.badcol + 1);
+        return;
+    }
+    if (tid < DB) dinv[tid] = df_sqrt(dinv[tid]);
+    __syncthreads();
+    for (int e = tid; e < DB * DB; e += DAG_THREADS) {
+        const int r = e & (DB - 1), c = e >> 6;
+        const dfl v = (r >= c) ? df_mul(S[c * DLD + r], dinv[c]) : dfl{0.0f, 0.0f};
+        S[c * DLD + r] = v;
+        G[e] = df_to_double(v);
+    }
+    __syncthreads();
+    if (tid < DB) {
+        const dfl d = S[tid * DLD + tid];
+        lj[tid] = df_rcp(d);  // 1 / L_rr
+        sm.vr[tid] = ((int64_t)j * DB + tid < P.n) ? log(df_to_double(d)) : 0.0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double s = 0.0;
+        for (int r = 0; r < DB; ++r) s += sm.vr[r];
+        *logpart = s;
+    }
+    // W = L^{-1}: with Y = I and M_lc = L_lc / L_ll, for l descending,
+    // Y_c -= Y_l M_lc (c < l); then W_c = Y_c / L_cc (columns).
+    for (int e = tid; e < DB * DB; e += DAG_THREADS) {
+        const int r = e & (DB - 1), c = e >> 6;
+        if (r > c) S[c * DLD + r] = df_mul(S[c * DLD + r], lj[r]);
+        Y[c * DLD + r] = dfl{(r == c) ? 1.0f : 0.0f, 0.0f};
+    }
+    __syncthreads();
+    for (int l = DB - 1; l > 0; --l) {
+        const int nr = DB - l;
+        for (int e = tid; e < l * nr; e += DAG_THREADS) {
+            const int c = e / nr, r = l + (e - c * nr);
+            Y[c * DLD + r] = df_fms(Y[c * DLD + r], Y[l * DLD + r], S[c * DLD + l]);
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < DB * DB; e += DAG_THREADS) {
+        const int r = e & (DB - 1), c = e >> 6;
+        Wg[e] = (r >= c) ? df_to_double(df_mul(Y[c * DLD + r], lj[c])) : 0.0;
+    }
+}
+
+// Factor and inverse of the diagonal tile held in the FP64 scratch (blocks
+// 0 = A11, 1 = A21, 3 = A22), in double-float: L11, W11; L21 = A21 W11^T;
+// L22, W22 from A22 - L21 L21^T (lower half); W21 = -W22 (L21 W11).
+// Returns the tile's log-det share.
 __device__ double diag_factor(TcCtx &c, const DagProb &P, int j) {
     DagSmem &dsm = *reinterpret_cast<DagSmem *>(c.opA);
+    dfl *sA = reinterpret_cast<dfl *>(dsm.sA), *sB = reinterpret_cast<dfl *>(dsm.sB);
     double *B = c.scr;
     const int D = 64 * 64;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     double *ld = c.red;  // two shares
-    double acc[4][4];
+    float ah[4][4], al[4][4];
     __syncthreads();
-    stage_a<0>(B + 0 * D, dsm.sA);
+    stage_a_df<0>(B + 0 * D, sA);
     __syncthreads();
-    potrf_inv_tile(P, 2 * j, B + 0 * D, B + 4 * D, ld + 0, dsm);
+    potrf_inv_tile_df(P, 2 * j, B + 0 * D, B + 4 * D, ld + 0, dsm);
     cta_gsync();
     // L21 = A21 W11^T: W11(c, t) = 0 for t > c
-    stage_a<0>(B + 1 * D, dsm.sA);
-    stage_b<1>(B + 4 * D, dsm.sB);
+    stage_a_df<0>(B + 1 * D, sA);
+    stage_b_df<1>(B + 4 * D, sB);
     __syncthreads();
-    acc_zero(acc);
-    blk_mma<false>(acc, dsm.sA, dsm.sB, 0, 4 * ty + 4);
-    blk_store(acc, B + 1 * D);
+    acc_zero_df(ah, al);
+    blk_mma_df<false>(ah, al, sA, sB, 0, 4 * ty + 4);
+    blk_store_df(ah, al, B + 1 * D);
     cta_gsync();
     // A22 - L21 L21^T on the blocks that touch the lower half
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = __ldcg(B + 3 * D + (4 * tx + a) + 64 * (4 * ty + b));
-    stage_a<0>(B + 1 * D, dsm.sA);
-    stage_b<1>(B + 1 * D, dsm.sB);
+        for (int b = 0; b < 4; ++b) {
+            const dfl v = ld_df(B + 3 * D + (4 * tx + a) + 64 * (4 * ty + b));
+            ah[a][b] = v.h;
+            al[a][b] = v.l;
+        }
+    stage_a_df<0>(B + 1 * D, sA);
+    stage_b_df<1>(B + 1 * D, sB);
     __syncthreads();
-    if (tx >= ty) blk_mma<true>(acc, dsm.sA, dsm.sB, 0, DB);
+    if (tx >= ty) blk_mma_df<true>(ah, al, sA, sB, 0, DB);
     __syncthreads();
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) dsm.sA[(4 * ty + b) * DLD + 4 * tx + a] = acc[a][b];
+        for (int b = 0; b < 4; ++b)
+            sA[(4 * ty + b) * DLD + 4 * tx + a] = df_quick_sum(ah[a][b], al[a][b]);
     __syncthreads();
-    potrf_inv_tile(P, 2 * j + 1, B + 3 * D, B + 6 * D, ld + 1, dsm);
+    potrf_inv_tile_df(P, 2 * j + 1, B + 3 * D, B + 6 * D, ld + 1, dsm);
     cta_gsync();
     // L21 W11: W11(t, c) = 0 for t < c
-    stage_a<0>(B + 1 * D, dsm.sA);
-    stage_b<0>(B + 4 * D, dsm.sB);
+    stage_a_df<0>(B + 1 * D, sA);
+    stage_b_df<0>(B + 4 * D, sB);
     __syncthreads();
-    acc_zero(acc);
-    blk_mma<false>(acc, dsm.sA, dsm.sB, 4 * ty, DB);
-    blk_store(acc, B + 2 * D);
+    acc_zero_df(ah, al);
+    blk_mma_df<false>(ah, al, sA, sB, 4 * ty, DB);
+    blk_store_df(ah, al, B + 2 * D);
     cta_gsync();
     // W21 = -W22 (L21 W11): W22(r, t) = 0 for t > r
-    stage_a<0>(B + 6 * D, dsm.sA);
-    stage_b<0>(B + 2 * D, dsm.sB);
+    stage_a_df<0>(B + 6 * D, sA);
+    stage_b_df<0>(B + 2 * D, sB);
     __syncthreads();
-    acc_zero(acc);
-    blk_mma<true>(acc, dsm.sA, dsm.sB, 0, 4 * tx + 4);
-    blk_store(acc, B + 5 * D);
+    acc_zero_df(ah, al);
+    blk_mma_df<true>(ah, al, sA, sB, 0, 4 * tx + 4);
+    blk_store_df(ah, al, B + 5 * D);
     cta_gsync();
     return ld[0] + ld[1];
 }
