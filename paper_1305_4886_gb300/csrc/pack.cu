@@ -304,26 +304,29 @@ __global__ void __launch_bounds__(256) split3_vec_kernel(SplitArgs a) {
     }
 }
 
-// The trans = 0 case in one pass over the source: 512
-// threads keep their 16 entry pairs in registers between the row-bound
-// reduction and the split, where the two-pass form read the panel twice
-// (the second time often from DRAM again) and waited on each 64-column
-// step's loads in turn.  Same bounds, slices and layout.
-constexpr int SPP_THREADS = 512;
+// The trans = 0 case in one pass over the source: each thread keeps its 16
+// entry pairs in registers between the row-bound reduction and the split,
+// where the two-pass form read the panel twice (the second time often from
+// DRAM again) and waited on each 64-column step's loads in turn.  One CTA of
+// 256 threads covers 16 rows x one 512-deep chunk, so that two CTAs share an
+// SM and one's loads overlap the other's split and stores.  Same bounds,
+// slices and layout.
+constexpr int SPP_THREADS = 256;
+constexpr int SPP_ROWS = 16;
 
-__global__ void __launch_bounds__(SPP_THREADS) split3_panel_kernel(SplitArgs a) {
-    __shared__ unsigned long long pm[SPP_THREADS / 32][32];
-    __shared__ float sc_s[32];
-    __shared__ __align__(16) uint16_t tile[2][3][32][SPV_LD];
+__global__ void __launch_bounds__(SPP_THREADS, 2) split3_panel_kernel(SplitArgs a) {
+    __shared__ unsigned long long pm[SPP_THREADS / 32][SPP_ROWS];
+    __shared__ float sc_s[SPP_ROWS];
+    __shared__ __align__(16) uint16_t tile[2][3][SPP_ROWS][SPV_LD];
     constexpr unsigned long long ABS = 0x7FFFFFFFFFFFFFFFull;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t r0 = (int64_t)blockIdx.x * 32;
+    const int64_t r0 = (int64_t)blockIdx.x * SPP_ROWS;
     const int64_t kb = (int64_t)blockIdx.y * SPLIT_KCH;
     const int64_t ke = min(a.K, kb + SPLIT_KCH);
     const int64_t slice = a.dst_rows * a.dst_kld;
     uint16_t *d0 = a.dst + (a.dst_row_off + r0) * a.dst_kld + a.dst_k_off;
-    // lane: rows rp and rp + 1; columns kb + kc + 32 i (i < 16), kc = 2 warp + co
-    const int rp = 2 * (lane & 15), kc = 2 * warp + (lane >> 4);
+    // lane: rows rp and rp + 1; columns kb + kc + 32 i (i < 16), kc = 4 warp + (lane / 8)
+    const int rp = 2 * (lane & 7), kc = 4 * warp + (lane >> 3);
     unsigned long long u[16][2];
     unsigned long long m0 = 0ull, m1 = 0ull;
 #pragma unroll
@@ -337,14 +340,17 @@ __global__ void __launch_bounds__(SPP_THREADS) split3_panel_kernel(SplitArgs a) 
         m0 = max(m0, u[i][0] & ABS);
         m1 = max(m1, u[i][1] & ABS);
     }
+    // lanes l, l + 8, l + 16, l + 24 hold the same rows
+    m0 = max(m0, __shfl_xor_sync(0xffffffffu, m0, 8));
+    m1 = max(m1, __shfl_xor_sync(0xffffffffu, m1, 8));
     m0 = max(m0, __shfl_xor_sync(0xffffffffu, m0, 16));
     m1 = max(m1, __shfl_xor_sync(0xffffffffu, m1, 16));
-    if (lane < 16) {
+    if (lane < 8) {
         pm[warp][rp] = m0;
         pm[warp][rp + 1] = m1;
     }
     __syncthreads();
-    if (threadIdx.x < 32) {
+    if (threadIdx.x < SPP_ROWS) {
         unsigned long long m = 0ull;
         for (int w = 0; w < SPP_THREADS / 32; ++w) m = max(m, pm[w][threadIdx.x]);
         int e = 0;
@@ -364,7 +370,7 @@ __global__ void __launch_bounds__(SPP_THREADS) split3_panel_kernel(SplitArgs a) 
 #pragma unroll
     for (int c = 0; c < SPLIT_KCH / 64; ++c) {
         if (kb + 64 * c >= ke) break;  // uniform
-        uint16_t(*t)[32][SPV_LD] = tile[c & 1];
+        uint16_t(*t)[SPP_ROWS][SPV_LD] = tile[c & 1];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int kk = kc + 32 * h;
@@ -379,8 +385,8 @@ __global__ void __launch_bounds__(SPP_THREADS) split3_panel_kernel(SplitArgs a) 
             t[2][rp + 1][kk] = s3[2];
         }
         __syncthreads();
-        for (int idx = threadIdx.x; idx < 3 * 32 * 8; idx += SPP_THREADS) {
-            const int p = idx >> 8, row = (idx >> 3) & 31, ch = idx & 7;
+        for (int idx = threadIdx.x; idx < 3 * SPP_ROWS * 8; idx += SPP_THREADS) {
+            const int p = idx / (SPP_ROWS * 8), row = (idx >> 3) % SPP_ROWS, ch = idx & 7;
             if (r0 + row < a.R)
                 *reinterpret_cast<uint4 *>(d0 + p * slice + (int64_t)row * a.dst_kld + kb + 64 * c + 8 * ch) =
                     *reinterpret_cast<const uint4 *>(&t[p][row][8 * ch]);
@@ -407,7 +413,7 @@ int split_rows(const double *src, int64_t ld, int64_t R, int64_t K, int64_t Kval
                      reinterpret_cast<uintptr_t>(dst) % 16 == 0 && dst_kld % 64 == 0;
     // the one-pass panel kernel holds one 512-column chunk in registers
     if (vec && !trans && kch == SPLIT_KCH)
-        split3_panel_kernel<<<g, SPP_THREADS, 0, s>>>(a);
+        split3_panel_kernel<<<dim3((unsigned)ceil_div(R, SPP_ROWS), g.y), SPP_THREADS, 0, s>>>(a);
     else if (vec && trans)
         split3_vec_kernel<<<g, 256, 0, s>>>(a);
     else
