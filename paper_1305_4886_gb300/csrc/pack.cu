@@ -308,30 +308,35 @@ __global__ void __launch_bounds__(256) split3_vec_kernel(SplitArgs a) {
 // entry pairs in registers between the row-bound reduction and the split,
 // where the two-pass form read the panel twice (the second time often from
 // DRAM again) and waited on each 64-column step's loads in turn.  One CTA of
-// 256 threads covers 16 rows x one 512-deep chunk, so that two CTAs share an
-// SM and one's loads overlap the other's split and stores.  Same bounds,
-// slices and layout.
-constexpr int SPP_THREADS = 256;
+// 256 R threads covers 16 rows x one 512 R-deep chunk (R = 1, or 2 for the
+// three-slice stores bounded over 1024 columns); with R = 1 two CTAs share
+// an SM, so that one's loads overlap the other's split and stores.  Same
+// bounds, slices and layout.
 constexpr int SPP_ROWS = 16;
 
-__global__ void __launch_bounds__(SPP_THREADS, 2) split3_panel_kernel(SplitArgs a) {
-    __shared__ unsigned long long pm[SPP_THREADS / 32][SPP_ROWS];
+template <int R>
+__global__ void __launch_bounds__(256 * R, 2 / R) split3_panel_kernel(SplitArgs a) {
+    constexpr int NT = 256 * R;       // threads
+    constexpr int KCH = 512 * R;      // chunk (and row bound) width
+    constexpr int CS = 32 * R;        // column stride of a thread's pairs
+    constexpr int PPS = 2 / R;        // a thread's pairs per 64-column step
+    __shared__ unsigned long long pm[NT / 32][SPP_ROWS];
     __shared__ float sc_s[SPP_ROWS];
     __shared__ __align__(16) uint16_t tile[2][3][SPP_ROWS][SPV_LD];
     constexpr unsigned long long ABS = 0x7FFFFFFFFFFFFFFFull;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t r0 = (int64_t)blockIdx.x * SPP_ROWS;
-    const int64_t kb = (int64_t)blockIdx.y * SPLIT_KCH;
-    const int64_t ke = min(a.K, kb + SPLIT_KCH);
+    const int64_t kb = (int64_t)blockIdx.y * KCH;
+    const int64_t ke = min(a.K, kb + KCH);
     const int64_t slice = a.dst_rows * a.dst_kld;
     uint16_t *d0 = a.dst + (a.dst_row_off + r0) * a.dst_kld + a.dst_k_off;
-    // lane: rows rp and rp + 1; columns kb + kc + 32 i (i < 16), kc = 4 warp + (lane / 8)
+    // lane: rows rp and rp + 1; columns kb + kc + CS i (i < 16), kc = 4 warp + (lane / 8)
     const int rp = 2 * (lane & 7), kc = 4 * warp + (lane >> 3);
     unsigned long long u[16][2];
     unsigned long long m0 = 0ull, m1 = 0ull;
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-        const int64_t k = kb + kc + 32 * i;
+        const int64_t k = kb + kc + CS * i;
         if (k < ke) {
             split_pair(a, r0 + rp, k, false, u[i][0], u[i][1]);
         } else {
@@ -352,40 +357,40 @@ __global__ void __launch_bounds__(SPP_THREADS, 2) split3_panel_kernel(SplitArgs 
     __syncthreads();
     if (threadIdx.x < SPP_ROWS) {
         unsigned long long m = 0ull;
-        for (int w = 0; w < SPP_THREADS / 32; ++w) m = max(m, pm[w][threadIdx.x]);
+        for (int w = 0; w < NT / 32; ++w) m = max(m, pm[w][threadIdx.x]);
         int e = 0;
         const int E = static_cast<int>(m >> 52);
         if (E > 0) e = E - 1022;
         e = max(-100, min(e, 120));
         sc_s[threadIdx.x] = ldexpf(1.0f, 7 - e);
         if (r0 + threadIdx.x < a.R)
-            a.dst_ex[(a.dst_row_off + r0 + threadIdx.x) * a.ex_ld + (a.dst_k_off + kb) / SPLIT_KCH] = e;
+            a.dst_ex[(a.dst_row_off + r0 + threadIdx.x) * a.ex_ld + (a.dst_k_off + kb) / KCH] = e;
     }
     __syncthreads();
     const float sc0 = sc_s[rp], sc1 = sc_s[rp + 1];
-    // 64-column steps: this thread's columns kc and kc + 32 of step c are its
-    // pairs 2c and 2c + 1; the transpose tile is double-buffered (one barrier
-    // per step: a buffer is rewritten only after the barrier that follows its
-    // stores)
+    // 64-column steps: this thread's pairs PPS c + h (h < PPS) lie in step c,
+    // at its columns kc + CS h; the transpose tile is double-buffered (one
+    // barrier per step: a buffer is rewritten only after the barrier that
+    // follows its stores)
 #pragma unroll
-    for (int c = 0; c < SPLIT_KCH / 64; ++c) {
+    for (int c = 0; c < KCH / 64; ++c) {
         if (kb + 64 * c >= ke) break;  // uniform
         uint16_t(*t)[SPP_ROWS][SPV_LD] = tile[c & 1];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int kk = kc + 32 * h;
+        for (int h = 0; h < PPS; ++h) {
+            const int kk = kc + CS * h;
             uint16_t s3[3];
-            split3_norm(u[2 * c + h][0], sc0, s3);
+            split3_norm(u[PPS * c + h][0], sc0, s3);
             t[0][rp][kk] = s3[0];
             t[1][rp][kk] = s3[1];
             t[2][rp][kk] = s3[2];
-            split3_norm(u[2 * c + h][1], sc1, s3);
+            split3_norm(u[PPS * c + h][1], sc1, s3);
             t[0][rp + 1][kk] = s3[0];
             t[1][rp + 1][kk] = s3[1];
             t[2][rp + 1][kk] = s3[2];
         }
         __syncthreads();
-        for (int idx = threadIdx.x; idx < 3 * SPP_ROWS * 8; idx += SPP_THREADS) {
+        for (int idx = threadIdx.x; idx < 3 * SPP_ROWS * 8; idx += NT) {
             const int p = idx / (SPP_ROWS * 8), row = (idx >> 3) % SPP_ROWS, ch = idx & 7;
             if (r0 + row < a.R)
                 *reinterpret_cast<uint4 *>(d0 + p * slice + (int64_t)row * a.dst_kld + kb + 64 * c + 8 * ch) =
@@ -411,9 +416,11 @@ int split_rows(const double *src, int64_t ld, int64_t R, int64_t K, int64_t Kval
     const bool vec = S == 3 && K % 64 == 0 && ld % 2 == 0 &&
                      reinterpret_cast<uintptr_t>(src) % 16 == 0 &&
                      reinterpret_cast<uintptr_t>(dst) % 16 == 0 && dst_kld % 64 == 0;
-    // the one-pass panel kernel holds one 512-column chunk in registers
+    // the one-pass panel kernel holds one chunk (512 or 1024 columns) in registers
     if (vec && !trans && kch == SPLIT_KCH)
-        split3_panel_kernel<<<dim3((unsigned)ceil_div(R, SPP_ROWS), g.y), SPP_THREADS, 0, s>>>(a);
+        split3_panel_kernel<1><<<dim3((unsigned)ceil_div(R, SPP_ROWS), g.y), 256, 0, s>>>(a);
+    else if (vec && !trans)
+        split3_panel_kernel<2><<<dim3((unsigned)ceil_div(R, SPP_ROWS), g.y), 512, 0, s>>>(a);
     else if (vec && trans)
         split3_vec_kernel<<<g, 256, 0, s>>>(a);
     else
