@@ -33,8 +33,13 @@ def libgp():
 
 def test_header_declares_the_path(libgp):
     names = declared_symbols()
-    for must in ["gp_cov_fill", "gp_chol", "gp_backsolve", "gp_loglik"]:
-        assert must in names
+    # the path's entry points, the workspace query, and the next rows'
+    # entry points (prediction, simulation, the paper's example covariance)
+    for must in ["gp_cov_fill", "gp_chol", "gp_backsolve", "gp_loglik", "gp_loglik_grad",
+                 "gp_loglik_grad_batched", "gp_workspace_bytes", "gp_mult_chol",
+                 "gp_predict", "gp_simulate", "gp_simulate_conditional", "gp_rng_normal",
+                 "gp_loglik_product"]:
+        assert must in names, must
 
 
 def test_exports_every_declared_symbol(libgp):
